@@ -1,0 +1,43 @@
+"""The oracle's pins must catch plausible mistakes.  Each case plants one
+mistake in a copy of the oracle's C source (on the CPU), builds it, and runs
+the pin suite against that build in a subprocess; the suite must fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "cs_oracle.c")
+
+MUTATIONS = {
+    "eq8_sign": ("t.raw = t.s2 - nsigma * sqrt(t.var);", "t.raw = t.s2 + nsigma * sqrt(t.var);"),
+    "eq2_transposed": ("s += R[a][k] * dg[k] * R[b][k];", "s += R[k][a] * dg[k] * R[k][b];"),
+    "eq7_dropped_factor": ("double g[3] = {2.0 * Ad[0], 2.0 * Ad[1], 2.0 * Ad[2]};",
+                           "double g[3] = {Ad[0], Ad[1], Ad[2]};"),
+    "eq11_no_offset": ("double e = st2 - prm->s_min;", "double e = st2;"),
+    "quat_order": ("double w = qf[0], x = qf[1], y = qf[2], z = qf[3];",
+                   "double w = qf[3], x = qf[0], y = qf[1], z = qf[2];"),
+    "filter_or": ("return !(opacity[i] < prm->opacity_min && smax > prm->extent_max);",
+                  "return !(opacity[i] < prm->opacity_min || smax > prm->extent_max);"),
+    "grad_sign": ("gvec[a] = -2.0 * w[a];", "gvec[a] = 2.0 * w[a];"),
+    "eq6_not_inverse": ("double P[3] = {1.0 / (ax * ax), 1.0 / (bx * bx), 1.0 / (cx * cx)};",
+                        "double P[3] = {ax * ax, bx * bx, cx * cx};"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutated = tmp_path / "cs_oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libcs_oracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-o", str(lib),
+                           str(mutated), "-lm"])
+    env = dict(os.environ, CS_ORACLE_LIB=str(lib))
+    proc = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert proc.returncode != 0, f"pins did not catch {name}:\n{proc.stdout[-2000:]}"
