@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the collision-metric hot path on B300; prints ONE JSON line.
+
+Workload (one step = every stage of the hot path over one batch):
+  the 1M-Gaussian tabletop scene (plane + 25 object clusters) built from
+  device-resident arrays (Eq. 2 repack, floater filter, grid, large tier);
+  262,144 arm spheres (4,096 configurations x 64, per-configuration sums) and
+  2,097,152 RRT edge spheres (2,048 edges x 16 strides x 64, per-edge OR),
+  each at n_sigma in {0, 0.5, 1, 2}; then 512 trajectories x 64 waypoint
+  poses x 8 body spheres: pose chain, metric, adjoint and pose adjoint.
+Metric: useful (query, Gaussian) pair evaluations per second (pairs inside the
+neighbour sets), with queries/s beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(independent replicas, weak scaling); the job value is the pairs of all ranks
+over the slowest rank's time.  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NSIGMAS = (0.0, 0.5, 1.0, 2.0)
+OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes)
+WORKLOAD = "tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres fwd+adjoint"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_inputs():
+    import cs_synth as S
+    scene = S.tabletop_scene()
+    arm = S.arm_queries()
+    edge = S.edge_queries()
+    poses, offs, radius = S.trajectory_poses()
+    return scene, arm, edge, poses, offs, radius
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2609_35619_b300 as cs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    scene_h, arm_h, edge_h, poses_h, offs_h, radius = make_inputs()
+    with torch.cuda.stream(stream):
+        d_scene = {k: torch.as_tensor(v, device=dev) for k, v in scene_h.items()}
+        d_arm = torch.as_tensor(arm_h, device=dev)
+        d_edge = torch.as_tensor(edge_h, device=dev)
+        d_poses = torch.as_tensor(poses_h, device=dev)
+        d_offs = torch.as_tensor(offs_h, device=dev)
+        K = offs_h.shape[0]
+        n_pose = poses_h.shape[0]
+        ones = torch.ones(n_pose, dtype=torch.float32, device=dev)
+        outs = {}
+        for name, q, G in (("arm", d_arm, 64), ("edge", d_edge, 1024)):
+            Q = q.shape[0]
+            outs[name] = {"metric": torch.empty(Q, device=dev), "collide": torch.empty(Q, dtype=torch.uint8, device=dev),
+                          "group_metric": torch.empty((Q + G - 1) // G, device=dev),
+                          "group_collide": torch.empty((Q + G - 1) // G, dtype=torch.uint8, device=dev)}
+        pose_out = {"metric": torch.empty(n_pose * K, device=dev),
+                    "collide": torch.empty(n_pose * K, dtype=torch.uint8, device=dev),
+                    "group_metric": torch.empty(n_pose, device=dev),
+                    "group_collide": torch.empty(n_pose, dtype=torch.uint8, device=dev)}
+        gbuf = torch.empty((n_pose * K, 3), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+
+    def step(events=None, stats=None):
+        ev = iter(events) if events is not None else None
+        nxt = (lambda: (next(ev), next(ev))) if ev is not None else (lambda: None)
+        scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
+                         device=dev, stream=stream)
+        for ns in NSIGMAS:
+            scene.query(d_arm, ns, params=cs.QueryParams(group_size=64), stream=stream,
+                        eval_events=nxt(), out=outs["arm"], pair_stats=stats)
+            scene.query(d_edge, ns, params=cs.QueryParams(group_size=1024), stream=stream,
+                        eval_events=nxt(), out=outs["edge"], pair_stats=stats)
+        with torch.cuda.stream(stream):
+            sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
+            scene.query(sph, 1.0, params=cs.QueryParams(group_size=K), stream=stream,
+                        eval_events=nxt(), out=pose_out, pair_stats=stats)
+            scene.query_grad(sph, 1.0, grad_out=ones, params=cs.QueryParams(group_size=K), stream=stream,
+                             eval_events=nxt(), out=gbuf)
+            gp = cs.pose_spheres_grad(d_poses, d_offs, gbuf, stream=stream)
+        return scene, gp
+
+    # ---- pair counts of one step (untimed, with the stats counters on)
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    sc, _ = step(stats=stats)
+    torch.cuda.synchronize(dev)
+    cand_pairs, useful_pairs = (int(x) for x in stats.cpu().tolist())
+    # forward sphere launches only (the roofline's kernel): rerun without the grad pass
+    stats_fwd = torch.zeros(2, dtype=torch.int64, device=dev)
+    for ns in NSIGMAS:
+        sc.query(d_arm, ns, params=cs.QueryParams(group_size=64), stream=stream, out=outs["arm"],
+                 pair_stats=stats_fwd)
+        sc.query(d_edge, ns, params=cs.QueryParams(group_size=1024), stream=stream, out=outs["edge"],
+                 pair_stats=stats_fwd)
+    torch.cuda.synchronize(dev)
+    fwd_cand, fwd_useful = (int(x) for x in stats_fwd.cpu().tolist())
+    info = sc.info()
+    sc.close()
+    n_queries = len(NSIGMAS) * (arm_h.shape[0] + edge_h.shape[0]) + 2 * n_pose * K
+    n_fwd_launches = 2 * len(NSIGMAS)
+
+    for _ in range(args.warmup):
+        s, _ = step()
+        torch.cuda.synchronize(dev)
+        s.close()
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    total_ms = 0.0
+    eval_ms = []  # per forward-sphere launch of the tabletop sweep
+    l0 = cs.abi.cs_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        if dist:
+            tdist.barrier()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (n_fwd_launches + 2))]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s, _ = step(events=evs)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        s.close()
+        total_ms += t0.elapsed_time(t1)
+        for k in range(n_fwd_launches):
+            eval_ms.append(evs[2 * k].elapsed_time(evs[2 * k + 1]))
+    launches = cs.abi.cs_launch_count() - l0
+    clk = clocks.stop()
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * useful_pairs / (ms_step * 1e-3)
+    qps = world * n_queries / (ms_step * 1e-3)
+
+    # ---- roofline of the fused forward kernel (FP32 pipe bound)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_ops = sms * 128 * max_mhz * 1e6  # FP32 lanes x max SM clock
+    avg_eval_s = (sum(eval_ms) / len(eval_ms)) * 1e-3
+    ops_per_launch = fwd_useful / n_fwd_launches * OPS_PER_PAIR
+    achieved = ops_per_launch / avg_eval_s
+    roofline = {"bound": "alu", "kernel": "k_eval<sphere> (fused cull+evaluate+reduce)",
+                "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
+                "ops_per_pair": OPS_PER_PAIR, "useful_pairs_per_launch": fwd_useful / n_fwd_launches,
+                "candidate_pairs_per_launch": fwd_cand / n_fwd_launches,
+                "avg_launch_ms": avg_eval_s * 1e3,
+                "candidate_frac": (fwd_cand * OPS_PER_PAIR / n_fwd_launches / avg_eval_s) / peak_ops}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_h, radius,
+                      useful_pairs, world)
+
+    result = {
+        "metric": "query-Gaussian pair evals/s (useful pairs inside the neighbour sets)",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": int(scene_h["means"].shape[0]),
+                   "n_kept": info["n_kept"], "queries_per_step": n_queries,
+                   "useful_pairs_per_step": useful_pairs, "candidate_pairs_per_step": cand_pairs,
+                   "nsigma": list(NSIGMAS), "parallelism": f"replicas x{world}",
+                   "l2": "256 MB buffer written between steps (outside the timed region)",
+                   "grid": {"dims": info["dims"], "cell_size": info["cell_size"],
+                            "n_large": info["n_large"]}},
+        "queries_per_s": qps, "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "gpu_launches": int(launches // args.steps) if args.steps else 0,
+        "gpu_launches_total": int(launches), "served": None,
+    }
+    return result
+
+
+def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_h, radius,
+            useful_pairs, world):
+    """The same step through the C ABI with host buffers: scene from pinned
+    host arrays, queries with host_io (copies in, compute, copies out)."""
+    import ctypes
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_scene = {k: pin(v) for k, v in scene_h.items()}
+    h_arm, h_edge, h_poses = pin(arm_h), pin(edge_h), pin(poses_h)
+    d_offs = torch.as_tensor(offs_h, device=dev)
+    K = offs_h.shape[0]
+    n_pose = poses_h.shape[0]
+    res = {}
+    for name, q, G in (("arm", h_arm, 64), ("edge", h_edge, 1024)):
+        Q = q.shape[0]
+        ng = (Q + G - 1) // G
+        res[name] = (torch.empty(Q).pin_memory(), torch.empty(Q, dtype=torch.uint8).pin_memory(),
+                     torch.empty(ng).pin_memory(), torch.empty(ng, dtype=torch.uint8).pin_memory(), G)
+    h_gpose = torch.empty((n_pose, 6)).pin_memory()
+    h_posecost = torch.empty(n_pose).pin_memory()
+    h2d = sum(v.numel() * 4 for v in h_scene.values()) + len(NSIGMAS) * (h_arm.numel() + h_edge.numel()) * 4 \
+        + h_poses.numel() * 4
+    d2h = len(NSIGMAS) * sum(r[0].numel() * 5 + r[2].numel() * 5 for r in res.values()) \
+        + h_gpose.numel() * 4 + h_posecost.numel() * 4
+    sh = stream.cuda_stream
+
+    def step():
+        d = cs.abi.cs_scene_desc()
+        d.n = scene_h["means"].shape[0]
+        d.means, d.scales = h_scene["means"].data_ptr(), h_scene["scales"].data_ptr()
+        d.quats, d.opacity = h_scene["quats"].data_ptr(), h_scene["opacity"].data_ptr()
+        d.on_device, d.use_filter, d.opacity_min, d.extent_max = 0, 1, 0.05, 0.1
+        h = ctypes.c_void_p()
+        cs.check(cs.abi.cs_scene_create(d, sh, h))
+        for ns in NSIGMAS:
+            for name, q in (("arm", h_arm), ("edge", h_edge)):
+                m, c, gm, gc, G = res[name]
+                p = cs.QueryParams(group_size=G).to_c()
+                p.host_io, p.stream = 1, sh
+                p.out_group_metric, p.out_group_collide = gm.data_ptr(), gc.data_ptr()
+                cs.check(cs.abi.cs_query(h, 0, q, q.shape[0], ns, m, c, p))
+        with torch.cuda.stream(stream):
+            d_poses = h_poses.to(dev, non_blocking=True)
+            sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
+            Q = sph.shape[0]
+            p = cs.QueryParams(group_size=K).to_c()
+            p.stream = sh
+            gm = torch.empty(n_pose, device=dev)
+            p.out_group_metric = gm.data_ptr()
+            cs.check(cs.abi.cs_query(h, 0, sph, Q, 1.0, None, None, p))
+            g = torch.empty((Q, 3), device=dev)
+            ones = torch.ones(n_pose, device=dev)
+            cs.check(cs.abi.cs_query_grad(h, 0, sph, Q, 1.0, ones, g, p))
+            gp = cs.pose_spheres_grad(d_poses, d_offs, g, stream=stream)
+            h_gpose.copy_(gp, non_blocking=True)
+            h_posecost.copy_(gm, non_blocking=True)
+        stream.synchronize()
+        cs.check(cs.abi.cs_scene_destroy(h))
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    return {"value": world * useful_pairs / (ms * 1e-3), "unit": "pairs/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ------------------------------------------------------------- oracle
+def oracle_sample(target_s: float, seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload: rows drawn
+    from the arm and edge batches (half each) at n_sigma = 1 against the full
+    scene, sized to about target_s seconds of host time."""
+    import oracle
+    scene, arm, edge, poses, offs, radius = make_inputs()
+    rng = np.random.default_rng(seed)
+    probe = np.concatenate([arm[rng.choice(arm.shape[0], 2)], edge[rng.choice(edge.shape[0], 2)]])
+    t0 = time.perf_counter()
+    oracle.query(scene, probe, 0, 1.0)
+    per_row = (time.perf_counter() - t0) / probe.shape[0]
+    rows = int(max(4, min(4096, target_s / max(per_row, 1e-6))))
+    rows -= rows % 2
+    sample = np.concatenate([arm[rng.choice(arm.shape[0], rows // 2, replace=False)],
+                             edge[rng.choice(edge.shape[0], rows // 2, replace=False)]])
+    t0 = time.perf_counter()
+    res = oracle.query(scene, sample, 0, 1.0)
+    dt = time.perf_counter() - t0
+    useful = int(res["count_nbr"].sum())
+    n = scene["means"].shape[0]
+    return {"value": useful / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{rows} rows (half arm, half edge spheres) at n_sigma=1 against all {n} Gaussians; "
+                      f"{useful} useful pairs, {rows * n} dense pairs in {dt:.2f} s "
+                      f"({rows * n / dt:.3g} dense pairs/s)",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(2.0, seed=99)
+    per_step = max(5.0, 120.0 / max(args.steps, 1))
+    for k in range(args.steps):
+        vals.append(oracle_sample(per_step, seed=k))
+    value = statistics.mean(v["value"] for v in vals)
+    ms = 1e3 * statistics.mean(v["seconds"] for v in vals)
+    last = vals[-1]
+    return {"impl": "reference", "metric": "query-Gaussian pair evals/s (useful pairs inside the neighbour sets)",
+            "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded sample per step)", "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cb = oracle_sample(15.0)
+            cb.pop("seconds", None)
+            out["cpu_baseline"] = cb
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

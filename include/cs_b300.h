@@ -1,0 +1,238 @@
+/*
+ * cs_b300.h -- C ABI of the B300 engine for the CollisionSplatting
+ * conservative collision metric (arXiv 2609.35619).
+ *
+ * The engine evaluates, for a batch of posed robot primitives (spheres or
+ * ellipsoids) and every Gaussian of a resident 3DGS scene, the conservative
+ * scaling-function metric of Section II-B and reduces it per primitive to the
+ * quantities the planners of Sections II-D and II-E consume:
+ *
+ *   Eq. 2   Sigma_i = R(q_i) diag(s_i)^2 R(q_i)^T
+ *   Eq. 5   s^2_ij  = (mu_i - c_j)^T A_j (mu_i - c_j)
+ *   Eq. 6   A_j     = R_j diag(1/a^2, 1/b^2, 1/c^2) R_j^T   (sphere: I / r^2)
+ *   Eq. 7   sigma^2_ij = g Sigma_i g^T,  g = 2 A_j (mu_i - c_j)
+ *   Eq. 8   st^2_ij = max(0, s^2_ij - n_sigma sqrt(sigma^2_ij))
+ *   Eq. 11  dc_ij   = d_max exp(-gamma max(st^2_ij - s_min, 0))
+ *
+ * Reductions over the neighbour set N_j = { i : st^2_ij <= S_cut },
+ * S_cut = s_min + ln(1/eps)/gamma (every omitted cost term is below
+ * eps * d_max):
+ *   mean cost  = sum_{N_j} dc / |N_j|   (0 when N_j is empty; Section II-D)
+ *   sum cost   = sum_{N_j} dc
+ *   min st^2   over N_j                  (+inf when empty)
+ *   softmin    = -tau ln sum_{N_j} exp(-st^2/tau)   (+inf when empty;
+ *                the recursive softmin of Section II-B, computed online)
+ *   collide    = #{ i in N_j : st^2 < 1 } > k_thr   (Section II-E)
+ *
+ * Conventions common to every entry point:
+ *   - float32 everywhere; quaternions are (w, x, y, z) and are normalised by
+ *     the library; scales are per-axis standard deviations.
+ *   - Device pointers are CUDA global-memory pointers of the current device
+ *     (e.g. from torch tensors); "host" pointers are ordinary CPU memory
+ *     (pinned memory gives asynchronous copies).  The caller owns every
+ *     buffer it passes; the library owns the scene and its scratch memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued asynchronously unless stated otherwise.  Argument errors are
+ *     returned synchronously, before anything is enqueued.
+ *   - Device-side conditions (invalid query rows, a bounded wait that ran
+ *     out) are recorded in a per-stream error word and reported by cs_sync.
+ *   - Query scratch (sort keys, prepared rows, host staging) is pooled per
+ *     (device, stream) and reused; calls on the same stream share it, calls
+ *     on different streams may run concurrently.
+ *   - cs_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef CS_B300_H
+#define CS_B300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CS_API __attribute__((visibility("default")))
+#else
+#define CS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_scene cs_scene; /* opaque, library-owned, device-resident */
+
+typedef enum cs_status {
+    CS_OK = 0,
+    CS_ERR_INVALID_ARG = -1, /* bad pointer, size, parameter or input value */
+    CS_ERR_NO_MEMORY = -2,   /* a device allocation failed */
+    CS_ERR_CUDA = -3,        /* a CUDA runtime call failed (message in cs_last_error) */
+    CS_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+    CS_ERR_BAD_HANDLE = -5,  /* NULL or destroyed scene handle */
+    CS_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+} cs_status;
+
+typedef enum cs_prim_type {
+    CS_PRIM_SPHERE = 0,    /* 4 floats per row: cx, cy, cz, r            (Eq. 6, a=b=c=r) */
+    CS_PRIM_ELLIPSOID = 1  /* 10 floats per row: cx, cy, cz, qw, qx, qy, qz, a, b, c (Eq. 6) */
+} cs_prim_type;
+
+typedef enum cs_metric_mode {
+    CS_METRIC_MEAN_COST = 0,  /* Eq. 11 averaged over N_j (MPPI, Section II-D) */
+    CS_METRIC_SUM_COST = 1,   /* Eq. 11 summed over N_j */
+    CS_METRIC_MIN_S2 = 2,     /* min over N_j of Eq. 8 */
+    CS_METRIC_SOFTMIN_S2 = 3  /* softmin over N_j of Eq. 8 (Section II-B) */
+} cs_metric_mode;
+
+/* Scene description for cs_scene_create (Section II-A, Eq. 1-2). */
+typedef struct cs_scene_desc {
+    int64_t n;              /* number of Gaussians, >= 0 */
+    const float *means;     /* [n,3] Gaussian means (world frame) */
+    const float *scales;    /* [n,3] per-axis standard deviations, >= 0 (a zero axis is a 2DGS disk) */
+    const float *quats;     /* [n,4] rotations (w,x,y,z); need not be normalised; 0 -> identity */
+    const float *opacity;   /* [n] opacities in [0,1], or NULL (no floater filter) */
+    int32_t on_device;      /* 1: the arrays above are device pointers; 0: host pointers */
+    int32_t use_filter;     /* floater filter of Section II-C: drop a Gaussian when
+                               opacity < opacity_min AND max(scale) > extent_max */
+    float opacity_min;      /* default 0.05 */
+    float extent_max;       /* default 0.1 (scene units) */
+    float cell_size;        /* uniform-grid cell edge; 0 = automatic */
+    float tier_quantile;    /* Gaussians whose largest scale exceeds this quantile go to
+                               the separately culled large tier; 0 = default 0.99 */
+} cs_scene_desc;
+
+/* Per-call parameters for cs_query / cs_query_grad.  Initialise with
+ * cs_params_init; every pointer member may be NULL. */
+typedef struct cs_params {
+    float gamma;               /* Eq. 11 decay, > 0 (default 5) */
+    float d_max;               /* Eq. 11 maximum cost per splat (default 1) */
+    float s_min;               /* Eq. 11 minimum scaling factor (default 1) */
+    float eps;                 /* neighbour-set truncation, 0 < eps < 1 (default 1e-6) */
+    float tau;                 /* softmin temperature, > 0 (default 0.05) */
+    int32_t k_thr;             /* collide iff the in-collision count exceeds k_thr (default 0) */
+    int32_t mode;              /* cs_metric_mode written to out_metric (default mean cost) */
+    int32_t group_size;        /* > 0: also reduce runs of group_size consecutive rows
+                                  (sum of the metric, OR of the flag; the last run may be
+                                  shorter) into out_group_metric / out_group_collide */
+    int32_t host_io;           /* 1: prims, nsigma_per_query, grad_out and every output are
+                                  host pointers; the call copies in, computes, copies out and
+                                  returns after the stream has finished */
+    int32_t tile_config;       /* 0 = automatic; otherwise a value from cs_tile_configs */
+    const float *nsigma_per_query; /* [Q] n_sigma per row (overrides the scalar), each >= 0 */
+    void *stream;              /* cudaStream_t */
+    int32_t *out_count;        /* [Q] |N_j| per row */
+    float *out_group_metric;   /* [ceil(Q/group_size)] */
+    uint8_t *out_group_collide;/* [ceil(Q/group_size)] */
+    unsigned long long *out_pair_stats; /* device [2], accumulated (not cleared):
+                                  [0] += (query, Gaussian) pairs evaluated after the cull,
+                                  [1] += pairs in the neighbour sets (sum of |N_j|) */
+    void *eval_events[2];      /* optional cudaEvent_t pair recorded on `stream` immediately
+                                  before and after the fused cull+evaluate kernel (tracing) */
+} cs_params;
+
+/* Scene information returned by cs_scene_info. */
+typedef struct cs_scene_info {
+    int64_t n_input;      /* Gaussians passed in */
+    int64_t n_kept;       /* after the floater filter and input validation */
+    int64_t n_grid;       /* kept Gaussians in the uniform grid */
+    int64_t n_large;      /* kept Gaussians in the large tier */
+    int64_t n_invalid;    /* rows with non-finite values or negative scales (dropped) */
+    int32_t dims[3];      /* grid cells per axis */
+    float cell_size;      /* grid cell edge */
+    float sigma_tier;     /* largest scale admitted to the grid tier */
+    float lo[3], hi[3];   /* bounding box of the kept means */
+    int64_t device_bytes; /* device memory held by the scene (without query scratch) */
+} cs_scene_info;
+
+/* Fill *p with the defaults listed in cs_params.  Returns CS_ERR_INVALID_ARG
+ * for p == NULL. */
+CS_API cs_status cs_params_init(cs_params *p);
+
+/* Build a resident scene (Eq. 2 repack, floater filter, uniform grid and
+ * large tier) on the current device.  Synchronises `stream` once (the grid
+ * shape depends on the scene's extent).  On success *out owns device memory
+ * until cs_scene_destroy.  n == 0 gives an empty scene (every query returns
+ * an empty neighbour set). */
+CS_API cs_status cs_scene_create(const cs_scene_desc *desc, void *stream, cs_scene **out);
+
+/* Release a scene.  The caller must ensure no work using the scene is still
+ * running.  NULL is a no-op.  (Query scratch is pooled per stream, not per
+ * scene: see cs_release_scratch.) */
+CS_API cs_status cs_scene_destroy(cs_scene *scene);
+
+CS_API cs_status cs_scene_info_get(const cs_scene *scene, cs_scene_info *info);
+
+/* Copy the repacked, grid-sorted scene to caller device buffers (any may be
+ * NULL): pos [n_kept,4] = (mu, max scale); cov [n_kept,8] = (Sxx, Syy, Szz,
+ * 2Sxy, 2Sxz, 2Syz, 0, 0); index [n_kept] = input row of each entry. */
+CS_API cs_status cs_scene_export(const cs_scene *scene, float *pos, float *cov, int32_t *index,
+                          void *stream);
+
+/* The metric for Q primitives (rows of `prims`, layout per cs_prim_type)
+ * against the scene, with conservatism n_sigma = `conservatism` (Eq. 8, >= 0)
+ * unless params->nsigma_per_query is given.
+ *   out_metric  [Q] float : the params->mode reduction per row (may be NULL
+ *                           only when a group output is requested)
+ *   out_collide [Q] uint8 : 1 iff the row is in collision (may be NULL)
+ * Rows with a non-finite centre or a non-positive radius/semi-axis give
+ * out_metric = NaN, out_collide = 0 and are reported by cs_sync.  Q == 0 is a
+ * no-op.  params == NULL uses the defaults on the legacy default stream. */
+CS_API cs_status cs_query(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
+                   float conservatism, float *out_metric, uint8_t *out_collide,
+                   const cs_params *params);
+
+/* Adjoint of cs_query: grad_centres[j] = grad_out[j] * d metric_j / d c_j
+ * ([Q,3], float).  With params->group_size > 0, grad_out has one entry per
+ * group and applies to every row of the group (the group metric is a sum).
+ * grad_out == NULL means ones.  The neighbour-set size is piecewise constant
+ * and the Eq. 8 clamp gives zero gradient where st^2 = 0; the min mode
+ * differentiates the arg-min pair.  Spheres and ellipsoids, all modes. */
+CS_API cs_status cs_query_grad(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
+                        float conservatism, const float *grad_out, float *grad_centres,
+                        const cs_params *params);
+
+/* Pose chain for sphere robots (device pointers): for P poses (t, w) with w
+ * an axis-angle rotation (Rodrigues) and K body-frame offsets p_k,
+ *   out_spheres[p*K + k] = (t_p + R(w_p) p_k, radius)      [P*K, 4]  */
+CS_API cs_status cs_pose_spheres(const float *poses, int64_t P, const float *offsets, int32_t K,
+                          float radius, float *out_spheres, void *stream);
+
+/* Adjoint of cs_pose_spheres: grad_poses[p] = (sum_k g_pk,
+ * J_l(w_p)^T sum_k (R(w_p) p_k) x g_pk) with J_l the left Jacobian of SO(3);
+ * grad_centres is [P*K,3], grad_poses [P,6] (overwritten). */
+CS_API cs_status cs_pose_spheres_grad(const float *poses, int64_t P, const float *offsets, int32_t K,
+                               const float *grad_centres, float *grad_poses, void *stream);
+
+/* Wait for `stream` and report device-side conditions recorded on it since
+ * the last cs_sync (CS_ERR_INVALID_ARG for invalid query rows,
+ * CS_ERR_TIMEOUT for an expired wait), clearing them.  After a timeout,
+ * later launches on the same stream return NaN rows without computing until
+ * cs_sync clears the condition. */
+CS_API cs_status cs_sync(const cs_scene *scene, void *stream);
+
+/* Tile configurations available to cs_params.tile_config: writes up to `cap`
+ * ids to `ids` and returns how many exist. */
+CS_API int32_t cs_tile_configs(int32_t *ids, int32_t cap);
+
+/* Self-test of the bounded-wait machinery: launches one block that waits on
+ * a barrier nothing completes, with a budget of `spins` polls, and returns
+ * CS_ERR_TIMEOUT when the wait gave up (the expected result) or CS_OK if it
+ * did not.  Faults nothing; the context stays usable. */
+CS_API cs_status cs_selftest_wait_timeout(int64_t spins, void *stream);
+
+/* Free the pooled query scratch of every stream (grown on demand by
+ * cs_query / cs_query_grad and kept for reuse; never allocated per call once
+ * large enough).  No query may be in flight. */
+CS_API cs_status cs_release_scratch(void);
+
+/* Number of kernels this library has launched in this process (host-side
+ * count, all threads and devices). */
+CS_API int64_t cs_launch_count(void);
+
+/* Message for the last failure on this thread ("" if none). */
+CS_API const char *cs_last_error(void);
+
+/* Library version string. */
+CS_API const char *cs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CS_B300_H */

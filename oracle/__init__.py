@@ -59,7 +59,7 @@ class _Params(ctypes.Structure):
 class _Outputs(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "sum_cost", "mean_cost", "count_nbr", "count_in", "collide", "min_s2", "softmin",
-        "band_cut", "band_in", "cond", "min_cond")]
+        "band_cut", "band_in", "cond", "min_cond", "band_kink")]
 
 
 @dataclass
@@ -99,7 +99,7 @@ def _load():
         lib.orc_query.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, P, ctypes.c_int64, P,
                                   ctypes.POINTER(_Params), ctypes.POINTER(_Outputs)]
         lib.orc_grad.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, P, ctypes.c_int64, P,
-                                 ctypes.POINTER(_Params), ctypes.c_int, P, P]
+                                 ctypes.POINTER(_Params), ctypes.c_int, P, P, P]
         lib.orc_pair.argtypes = [P, P, P, ctypes.c_int, P, ctypes.c_double,
                                  ctypes.POINTER(_Params), P]
         lib.orc_covariances.argtypes = [ctypes.c_int64, P, P, P, ctypes.POINTER(_Params), P, P]
@@ -157,7 +157,7 @@ def query(scene, prims, prim_type: int, nsigma, params: Params | None = None) ->
         "count_nbr": np.zeros(Q, np.int64), "count_in": np.zeros(Q, np.int64),
         "collide": np.zeros(Q, np.uint8), "min_s2": np.zeros(Q), "softmin": np.zeros(Q),
         "band_cut": np.zeros(Q, np.int64), "band_in": np.zeros(Q, np.int64),
-        "cond": np.zeros(Q), "min_cond": np.zeros(Q),
+        "cond": np.zeros(Q), "min_cond": np.zeros(Q), "band_kink": np.zeros(Q, np.int64),
     }
     outs = _Outputs(*[res[k].ctypes.data for k, _ in _Outputs._fields_])
     rc = lib.orc_query(means.shape[0], _ptr(means), _ptr(scales), _ptr(quats), _ptr(op), prim_type,
@@ -174,9 +174,11 @@ def metric(res: dict, mode: int) -> np.ndarray:
 
 
 def grad(scene, prims, prim_type: int, nsigma, mode: int = MODE_MEAN,
-         grad_out=None, params: Params | None = None) -> np.ndarray:
+         grad_out=None, params: Params | None = None, return_scale: bool = False):
     """Analytic gradient of the per-query metric with respect to the
-    primitive centres, [Q,3], scaled by grad_out [Q] (ones if None)."""
+    primitive centres, [Q,3], scaled by grad_out [Q] (ones if None).  With
+    return_scale, also the sum of the norms of the summed terms per query
+    (the conditioning of the sum)."""
     params = params or Params()
     lib = _load()
     means, scales, quats, op = _scene_arrays(scene)
@@ -185,11 +187,13 @@ def grad(scene, prims, prim_type: int, nsigma, mode: int = MODE_MEAN,
     ns = _nsigma_array(nsigma, Q)
     go = None if grad_out is None else np.ascontiguousarray(np.asarray(grad_out, np.float64).reshape(Q))
     g = np.zeros((Q, 3))
+    sc = np.zeros(Q)
     rc = lib.orc_grad(means.shape[0], _ptr(means), _ptr(scales), _ptr(quats), _ptr(op), prim_type,
-                      _ptr(prims), Q, _ptr(ns), ctypes.byref(params._c()), mode, _ptr(go), _ptr(g))
+                      _ptr(prims), Q, _ptr(ns), ctypes.byref(params._c()), mode, _ptr(go), _ptr(g),
+                      _ptr(sc))
     if rc != 0:
         raise ValueError(f"oracle grad failed ({rc}): invalid primitive")
-    return g
+    return (g, sc) if return_scale else g
 
 
 def pair(mean, scale, quat, prim, prim_type: int, nsigma: float,

@@ -69,6 +69,8 @@ typedef struct {
     int64_t *band_in;   /* pairs with |st^2 - 1| <= 1e-5 */
     double *cond;       /* max over N_j of s^2 + n_sigma sqrt(sigma^2) */
     double *min_cond;   /* s^2 + n_sigma sqrt(sigma^2) of the argmin pair */
+    int64_t *band_kink; /* pairs near a kink of the gradient: |st^2 - s_min| <= 1e-5 or
+                           the Eq. 8 clamp within 1e-5 of its switching point */
 } orc_outputs;
 
 /* ---- geometry -------------------------------------------------------- */
@@ -244,7 +246,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
         if (robot_primitive(prim_type, prims + (size_t)stride * j, c, A) != 0) { bad += 1; continue; }
         double ns = nsigma[j];
         double sum = 0.0, mn = INFINITY, mn_cond = 0.0, cond = 0.0;
-        int64_t cnt = 0, cin = 0, bcut = 0, bin = 0;
+        int64_t cnt = 0, cin = 0, bcut = 0, bin = 0, bkink = 0;
         /* softmin: shift by the running minimum so the sum stays in range */
         double sm_m = INFINITY, sm_acc = 0.0;
         for (int64_t i = 0; i < n; ++i) {
@@ -255,6 +257,10 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
             pair_terms t = evaluate_pair(mu, Sg, c, A, ns);
             if (fabs(t.st2 - S_cut) <= 1e-5 * S_cut) ++bcut;
             if (fabs(t.st2 - 1.0) <= 1e-5) ++bin;
+            if (t.st2 <= S_cut * (1.0 + 1e-5) &&
+                (fabs(t.st2 - prm->s_min) <= 1e-5 * fmax(1.0, fabs(prm->s_min)) ||
+                 fabs(t.raw) <= 1e-5 * (t.s2 + ns * sqrt(t.var))))
+                ++bkink;
             if (!(t.st2 <= S_cut)) continue;
             ++cnt;
             sum += pair_cost(prm, t.st2);
@@ -277,6 +283,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
         if (out->band_in) out->band_in[j] = bin;
         if (out->cond) out->cond[j] = cond;
         if (out->min_cond) out->min_cond[j] = mn_cond;
+        if (out->band_kink) out->band_kink[j] = bkink;
     }
     free(Sig);
     free(keep);
@@ -320,7 +327,7 @@ static void st2_grad(const double mu[3], const double Sig[3][3], const double c[
 int orc_grad(int64_t n, const float *means, const float *scales, const float *quats,
              const float *opacity, int prim_type, const float *prims, int64_t Q,
              const double *nsigma, const orc_params *prm, int mode, const double *grad_out,
-             double *grad)
+             double *grad, double *gscale)
 {
     const int stride = prim_type == 0 ? 4 : 10;
     const double S_cut = cutoff(prm);
@@ -337,9 +344,11 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
     for (int64_t j = 0; j < Q; ++j) {
         double c[3], A[3][3];
         grad[3 * j] = grad[3 * j + 1] = grad[3 * j + 2] = 0.0;
+        if (gscale) gscale[j] = 0.0;
         if (robot_primitive(prim_type, prims + (size_t)stride * j, c, A) != 0) { bad += 1; continue; }
         double ns = nsigma[j];
         double acc[3] = {0, 0, 0};
+        double mag = 0.0; /* sum of the norms of the summed terms */
         int64_t cnt = 0;
         double best = INFINITY, best_g[3] = {0, 0, 0};
         /* softmin: weights exp(-st2/tau) / sum, accumulated with a running
@@ -359,20 +368,26 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
                 if (st2 > prm->s_min) {
                     double dc = pair_cost(prm, st2);
                     for (int a = 0; a < 3; ++a) acc[a] += -prm->gamma * dc * g[a];
+                    mag += prm->gamma * dc * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 }
             } else if (mode == 2) {
-                if (st2 < best) { best = st2; best_g[0] = g[0]; best_g[1] = g[1]; best_g[2] = g[2]; }
+                if (st2 < best) {
+                    best = st2; best_g[0] = g[0]; best_g[1] = g[1]; best_g[2] = g[2];
+                    mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                }
             } else {
                 double x = st2 / prm->tau;
                 if (x < sm_m) {
                     double r = exp(x - sm_m);
                     sm_acc = sm_acc * r + 1.0;
                     for (int a = 0; a < 3; ++a) sm_g[a] = sm_g[a] * r + g[a];
+                    mag = mag * r + sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                     sm_m = x;
                 } else {
                     double e = exp(sm_m - x);
                     sm_acc += e;
                     for (int a = 0; a < 3; ++a) sm_g[a] += e * g[a];
+                    mag += e * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 }
             }
         }
@@ -380,14 +395,17 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
         double out[3] = {0, 0, 0};
         if (mode == 0) {
             if (cnt > 0) for (int a = 0; a < 3; ++a) out[a] = acc[a] / (double)cnt;
+            if (cnt > 0) mag /= (double)cnt;
         } else if (mode == 1) {
             for (int a = 0; a < 3; ++a) out[a] = acc[a];
         } else if (mode == 2) {
             for (int a = 0; a < 3; ++a) out[a] = best_g[a];
         } else if (cnt > 0) {
             for (int a = 0; a < 3; ++a) out[a] = sm_g[a] / sm_acc;
+            mag /= sm_acc;
         }
         for (int a = 0; a < 3; ++a) grad[3 * j + a] = up * out[a];
+        if (gscale) gscale[j] = fabs(up) * mag;
     }
     free(Sig);
     free(keep);

@@ -1,0 +1,407 @@
+// cs_build.cu -- scene construction: Eq. 2 repack of every Gaussian into the
+// 48-byte record, the floater filter of Section II-C, the uniform grid over
+// the means (the paper's spatial hash, Section II-B) with a separately culled
+// tier of very large Gaussians, and the per-chunk bounding records used by
+// the warp-level cull.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct BuildStats {
+    int aabb[6];          // ordered-int min xyz, max xyz of kept means
+    unsigned n_kept;
+    unsigned n_invalid;
+    unsigned hist[kSigmaBins];
+    int sigma_grid_max;   // ordered-int max scale over the grid tier
+};
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) {
+    return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// Eq. 2 for one Gaussian: Sigma = (R S)(R S)^T with R from the (possibly
+// unnormalised) quaternion via R = I - 2/|q|^2 (...) and S = diag(scale).
+__global__ void __launch_bounds__(kThreads) k_repack(
+    const float *__restrict__ means, const float *__restrict__ scales,
+    const float *__restrict__ quats, const float *__restrict__ opacity, int64_t n, int use_filter,
+    float opacity_min, float extent_max, float4 *__restrict__ pos, float4 *__restrict__ covA,
+    float4 *__restrict__ covB, uint8_t *__restrict__ code, BuildStats *__restrict__ st) {
+    __shared__ unsigned s_hist[kSigmaBins];
+    __shared__ int s_box[6];
+    __shared__ unsigned s_kept, s_bad;
+    for (int b = threadIdx.x; b < kSigmaBins; b += kThreads) s_hist[b] = 0;
+    if (threadIdx.x < 6) s_box[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
+    if (threadIdx.x == 0) { s_kept = 0; s_bad = 0; }
+    __syncthreads();
+
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) {
+        float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+        float s0 = scales[3 * i], s1 = scales[3 * i + 1], s2 = scales[3 * i + 2];
+        float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        float op = opacity ? opacity[i] : 1.f;
+        bool ok = finite3(mx, my, mz) && finite3(s0, s1, s2) && finite3(qw, qx, qy) &&
+                  isfinite(qz) && s0 >= 0.f && s1 >= 0.f && s2 >= 0.f && !isnan(op);
+        float smax = fmaxf(fmaxf(s0, s1), s2);
+        uint8_t c = 0;
+        if (!ok) {
+            c = 2;
+            atomicAdd(&s_bad, 1u);
+        } else if (use_filter && opacity && op < opacity_min && smax > extent_max) {
+            c = 0;  // floater (Section II-C)
+        } else {
+            c = 1;
+        }
+        code[i] = c;
+        if (c == 1) {
+            float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+            if (!(n2 > 0.f)) { qw = 1.f; qx = qy = qz = 0.f; n2 = 1.f; }
+            float s = 2.f / n2;
+            float R00 = 1.f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qw * qz),
+                  R02 = s * (qx * qz + qw * qy);
+            float R10 = s * (qx * qy + qw * qz), R11 = 1.f - s * (qx * qx + qz * qz),
+                  R12 = s * (qy * qz - qw * qx);
+            float R20 = s * (qx * qz - qw * qy), R21 = s * (qy * qz + qw * qx),
+                  R22 = 1.f - s * (qx * qx + qy * qy);
+            // M = R diag(scale); Sigma = M M^T (a Gram matrix: PSD up to rounding)
+            float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+            float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+            float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+            float Sxx = fmaf(M00, M00, fmaf(M01, M01, M02 * M02));
+            float Syy = fmaf(M10, M10, fmaf(M11, M11, M12 * M12));
+            float Szz = fmaf(M20, M20, fmaf(M21, M21, M22 * M22));
+            float Sxy = fmaf(M00, M10, fmaf(M01, M11, M02 * M12));
+            float Sxz = fmaf(M00, M20, fmaf(M01, M21, M02 * M22));
+            float Syz = fmaf(M10, M20, fmaf(M11, M21, M12 * M22));
+            pos[i] = make_float4(mx, my, mz, smax);
+            covA[i] = make_float4(Sxx, Syy, Szz, 2.f * Sxy);
+            covB[i] = make_float4(2.f * Sxz, 2.f * Syz, 0.f, __int_as_float((int)i));
+            atomicAdd(&s_kept, 1u);
+            int b = 0;
+            if (smax > 0.f) {
+                float l = (log2f(smax) - kSigmaLog2Lo) * kSigmaBinsPerOctave;
+                b = (int)fminf(fmaxf(floorf(l), 0.f), (float)(kSigmaBins - 1));
+            }
+            atomicAdd(&s_hist[b], 1u);
+            atomicMin(&s_box[0], float_to_ordered(mx));
+            atomicMin(&s_box[1], float_to_ordered(my));
+            atomicMin(&s_box[2], float_to_ordered(mz));
+            atomicMax(&s_box[3], float_to_ordered(mx));
+            atomicMax(&s_box[4], float_to_ordered(my));
+            atomicMax(&s_box[5], float_to_ordered(mz));
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSigmaBins; b += kThreads)
+        if (s_hist[b]) atomicAdd(&st->hist[b], s_hist[b]);
+    if (threadIdx.x < 3) atomicMin(&st->aabb[threadIdx.x], s_box[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicMax(&st->aabb[threadIdx.x], s_box[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        if (s_kept) atomicAdd(&st->n_kept, s_kept);
+        if (s_bad) atomicAdd(&st->n_invalid, s_bad);
+    }
+}
+
+struct GridParams {
+    float lo[3];
+    float inv_h;
+    int dims[3];
+    float sigma_tier;
+    float coarse_inv[3];  // coarse cells per unit length for the large tier
+    uint32_t ncells;
+};
+
+__device__ __forceinline__ int cell_coord(float x, float lo, float inv_h, int dim) {
+    int c = (int)floorf((x - lo) * inv_h);
+    return min(max(c, 0), dim - 1);
+}
+
+// Sort key of each Gaussian: grid cell for the grid tier, ncells + coarse
+// cell for the large tier, ncells + kCoarse^3 for dropped rows.
+__global__ void __launch_bounds__(kThreads) k_keys(const float4 *__restrict__ pos,
+                                                   const uint8_t *__restrict__ code, int64_t n,
+                                                   GridParams g, uint32_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ vals,
+                                                   BuildStats *__restrict__ st) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t ncoarse = kCoarseDim * kCoarseDim * kCoarseDim;
+    uint32_t key = g.ncells + ncoarse;
+    if (code[i] == 1) {
+        float4 p = pos[i];
+        if (p.w <= g.sigma_tier) {
+            int ix = cell_coord(p.x, g.lo[0], g.inv_h, g.dims[0]);
+            int iy = cell_coord(p.y, g.lo[1], g.inv_h, g.dims[1]);
+            int iz = cell_coord(p.z, g.lo[2], g.inv_h, g.dims[2]);
+            key = (uint32_t)ix + (uint32_t)g.dims[0] * ((uint32_t)iy + (uint32_t)g.dims[1] * (uint32_t)iz);
+            atomicMax(&st->sigma_grid_max, float_to_ordered(p.w));
+        } else {
+            int cx = cell_coord(p.x, g.lo[0], g.coarse_inv[0], kCoarseDim);
+            int cy = cell_coord(p.y, g.lo[1], g.coarse_inv[1], kCoarseDim);
+            int cz = cell_coord(p.z, g.lo[2], g.coarse_inv[2], kCoarseDim);
+            key = g.ncells + (uint32_t)(cx + kCoarseDim * (cy + kCoarseDim * cz));
+        }
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_count_keys(const uint32_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[keys[i]], 1u);
+}
+
+__global__ void k_gather(const uint32_t *__restrict__ perm, int64_t n_kept,
+                         const float4 *__restrict__ pos, const float4 *__restrict__ covA,
+                         const float4 *__restrict__ covB, float4 *__restrict__ opos,
+                         float4 *__restrict__ ocovA, float4 *__restrict__ ocovB) {
+    int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (p >= n_kept) return;
+    uint32_t i = perm[p];
+    opos[p] = pos[i];
+    ocovA[p] = covA[i];
+    ocovB[p] = covB[i];
+}
+
+// One warp per chunk of kChunk consecutive sorted Gaussians.
+__global__ void k_chunks(const float4 *__restrict__ pos, int n_kept, int nchunks,
+                         float4 *__restrict__ clo, float4 *__restrict__ chi) {
+    int c = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (c >= nchunks) return;
+    int p = c * kChunk + lane;
+    float4 v = p < n_kept ? pos[p] : pos[c * kChunk];
+    float lx = v.x, ly = v.y, lz = v.z, hx = v.x, hy = v.y, hz = v.z, sg = v.w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        sg = fmaxf(sg, __shfl_xor_sync(0xffffffffu, sg, o));
+    }
+    if (lane == 0) {
+        clo[c] = make_float4(lx, ly, lz, sg);
+        chi[c] = make_float4(hx, hy, hz, 0.f);
+    }
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
+    const int64_t n = d->n;
+    sc->n_input = n;
+    DevBuf in_means, in_scales, in_quats, in_op, tmp_rec, tmp_code, tmp_kv, tmp_hist, tmp_scan,
+        d_stats;
+    const float *means = d->means, *scales = d->scales, *quats = d->quats, *op = d->opacity;
+    if (n > 0 && !d->on_device) {
+        CS_CUDA(cudaMalloc(&in_means.p, 12 * n));
+        CS_CUDA(cudaMalloc(&in_scales.p, 12 * n));
+        CS_CUDA(cudaMalloc(&in_quats.p, 16 * n));
+        CS_CUDA(cudaMemcpyAsync(in_means.p, d->means, 12 * n, cudaMemcpyHostToDevice, s));
+        CS_CUDA(cudaMemcpyAsync(in_scales.p, d->scales, 12 * n, cudaMemcpyHostToDevice, s));
+        CS_CUDA(cudaMemcpyAsync(in_quats.p, d->quats, 16 * n, cudaMemcpyHostToDevice, s));
+        means = (const float *)in_means.p;
+        scales = (const float *)in_scales.p;
+        quats = (const float *)in_quats.p;
+        if (op) {
+            CS_CUDA(cudaMalloc(&in_op.p, 4 * n));
+            CS_CUDA(cudaMemcpyAsync(in_op.p, d->opacity, 4 * n, cudaMemcpyHostToDevice, s));
+            op = (const float *)in_op.p;
+        }
+    }
+    const int64_t nn = n > 0 ? n : 1;
+    CS_CUDA(cudaMalloc(&tmp_rec.p, 48 * nn));
+    CS_CUDA(cudaMalloc(&tmp_code.p, nn));
+    CS_CUDA(cudaMalloc(&tmp_kv.p, 16 * nn));
+    CS_CUDA(cudaMalloc(&d_stats.p, sizeof(BuildStats)));
+    float4 *upos = (float4 *)tmp_rec.p, *ucovA = upos + nn, *ucovB = ucovA + nn;
+    uint8_t *code = (uint8_t *)tmp_code.p;
+    BuildStats hs;
+    memset(&hs, 0, sizeof(hs));
+    for (int k = 0; k < 3; ++k) { hs.aabb[k] = INT_MAX; hs.aabb[3 + k] = INT_MIN; }
+    hs.sigma_grid_max = INT_MIN;
+    CS_CUDA(cudaMemcpyAsync(d_stats.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    BuildStats *st = (BuildStats *)d_stats.p;
+    if (n > 0)
+        k_repack<<<blocks_for(n), kThreads, 0, s>>>(means, scales, quats, op, n, d->use_filter,
+                                                    d->opacity_min, d->extent_max, upos, ucovA,
+                                                    ucovB, code, st);
+        count_launches(1);
+    CS_CUDA(cudaGetLastError());
+    CS_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaStreamSynchronize(s));
+    sc->n_invalid = hs.n_invalid;
+    const int64_t kept_est = hs.n_kept;
+
+    // ---- grid shape (host): extent of the kept means, cell size, tier cut
+    float lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    if (kept_est > 0) {
+        for (int k = 0; k < 3; ++k) {
+            int a = hs.aabb[k], b = hs.aabb[3 + k];
+            lo[k] = __builtin_bit_cast(float, a >= 0 ? a : a ^ 0x7FFFFFFF);
+            hi[k] = __builtin_bit_cast(float, b >= 0 ? b : b ^ 0x7FFFFFFF);
+        }
+    }
+    float ext[3], emax = 0.f;
+    for (int k = 0; k < 3; ++k) { ext[k] = hi[k] - lo[k]; emax = std::max(emax, ext[k]); }
+    if (!(emax > 0.f)) emax = 1.f;
+    const float ext_min = emax * 1e-3f;
+    for (int k = 0; k < 3; ++k) ext[k] = std::max(ext[k], ext_min);
+    // tier cut: the tier_quantile of the largest scale (upper edge of its bin)
+    double q = d->tier_quantile > 0.f ? std::min(1.0, (double)d->tier_quantile) : 0.99;
+    float sigma_tier = INFINITY;
+    if (kept_est > 0 && q < 1.0) {
+        uint64_t target = (uint64_t)ceil(q * (double)kept_est), cum = 0;
+        for (int b = 0; b < kSigmaBins; ++b) {
+            cum += hs.hist[b];
+            if (cum >= target) {
+                sigma_tier = exp2f(kSigmaLog2Lo + (float)(b + 1) / kSigmaBinsPerOctave);
+                break;
+            }
+        }
+    }
+    float h = d->cell_size;
+    if (!(h > 0.f)) {
+        double vol = (double)ext[0] * ext[1] * ext[2];
+        h = (float)cbrt(vol * 32.0 / (double)std::max<int64_t>(kept_est, 1));
+    }
+    h = std::max(h, emax / 1024.f);
+    int dims[3];
+    for (;;) {
+        int64_t tot = 1;
+        for (int k = 0; k < 3; ++k) {
+            dims[k] = std::max(1, (int)ceilf(ext[k] / h));
+            tot *= dims[k];
+        }
+        if (tot <= kMaxCells) break;
+        h *= 1.25f;
+    }
+    GridParams g;
+    for (int k = 0; k < 3; ++k) {
+        g.lo[k] = lo[k];
+        g.dims[k] = dims[k];
+        g.coarse_inv[k] = (float)kCoarseDim / ext[k];
+    }
+    g.inv_h = 1.f / h;
+    g.sigma_tier = sigma_tier;
+    g.ncells = (uint32_t)((int64_t)dims[0] * dims[1] * dims[2]);
+    sc->ncells = g.ncells;
+    const uint32_t ncoarse = kCoarseDim * kCoarseDim * kCoarseDim;
+    const uint32_t nkeys = g.ncells + ncoarse + 1;  // + dropped
+    int bits = 1;
+    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)nkeys) ++bits;
+
+    // ---- keys, stable sort, key starts
+    uint32_t *keys[2] = {(uint32_t *)tmp_kv.p, (uint32_t *)tmp_kv.p + nn};
+    uint32_t *vals[2] = {(uint32_t *)tmp_kv.p + 2 * nn, (uint32_t *)tmp_kv.p + 3 * nn};
+    size_t hist_n = std::max(sort_hist_elems((size_t)nn), (size_t)nkeys + 1);
+    size_t scan_n = scan_tmp_elems(hist_n);
+    CS_CUDA(cudaMalloc(&tmp_hist.p, 4 * hist_n));
+    CS_CUDA(cudaMalloc(&tmp_scan.p, 4 * scan_n));
+    int res = 0;
+    if (n > 0) {
+        k_keys<<<blocks_for(n), kThreads, 0, s>>>(upos, code, n, g, keys[0], vals[0], st);
+        count_launches(1);
+        res = radix_sort(keys, vals, (size_t)n, bits, (uint32_t *)tmp_hist.p,
+                         (uint32_t *)tmp_scan.p, s);
+    }
+
+    // owned memory: records, key starts, chunk records
+    const int64_t kmax = std::max<int64_t>(kept_est, 1);
+    const int nchunks = (int)((kept_est + kChunk - 1) / kChunk);
+    size_t bytes_rec = (size_t)48 * kmax;
+    size_t bytes_keys = (size_t)4 * (nkeys + 1);
+    size_t bytes_chunks = (size_t)32 * std::max(nchunks, 1);
+    size_t off_keys = (bytes_rec + 255) & ~(size_t)255;
+    size_t off_chunks = (off_keys + bytes_keys + 255) & ~(size_t)255;
+    size_t total = off_chunks + bytes_chunks;
+    void *blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, total);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation
+                                     ? (set_error("scene allocation failed"), CS_ERR_NO_MEMORY)
+                                     : cuda_fail(e, "cudaMalloc(scene)");
+    sc->blocks[sc->nblocks++] = blk;
+    sc->device_bytes = (int64_t)total;
+    char *base = (char *)blk;
+    float4 *spos = (float4 *)base, *scovA = spos + kmax, *scovB = scovA + kmax;
+    uint32_t *kstart = (uint32_t *)(base + off_keys);
+    float4 *clo = (float4 *)(base + off_chunks), *chi = clo + std::max(nchunks, 1);
+
+    uint32_t *cnt = (uint32_t *)tmp_hist.p;  // reuse: nkeys + 1 counters
+    CS_CUDA(cudaMemsetAsync(cnt, 0, 4 * ((size_t)nkeys + 1), s));
+    if (n > 0) k_count_keys<<<blocks_for(n), kThreads, 0, s>>>(keys[res], n, cnt);
+        count_launches(1);
+    scan_exclusive(cnt, kstart, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
+    uint32_t bounds[2] = {0, 0};
+    CS_CUDA(cudaMemcpyAsync(&bounds[0], kstart + g.ncells, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaMemcpyAsync(&bounds[1], kstart + g.ncells + ncoarse, 4, cudaMemcpyDeviceToHost, s));
+    int sgm = INT_MIN;
+    CS_CUDA(cudaMemcpyAsync(&sgm, &st->sigma_grid_max, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_grid = bounds[0], n_kept = bounds[1];
+    if (n_kept != kept_est) {
+        set_error("internal: kept count mismatch in scene build");
+        return CS_ERR_CUDA;
+    }
+    if (n_kept > 0)
+        k_gather<<<blocks_for(n_kept), kThreads, 0, s>>>(vals[res], n_kept, upos, ucovA, ucovB,
+                                                         spos, scovA, scovB);
+        count_launches(1);
+    if (nchunks > 0)
+        k_chunks<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            spos, (int)n_kept, nchunks, clo, chi);
+        count_launches(1);
+    CS_CUDA(cudaGetLastError());
+    CS_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
+
+    sc->n_kept = n_kept;
+    sc->n_grid = n_grid;
+    sc->n_large = n_kept - n_grid;
+    SceneDev &dv = sc->dev;
+    dv.pos = spos;
+    dv.covA = scovA;
+    dv.covB = scovB;
+    dv.cell_start = kstart;
+    dv.chunk_lo = clo;
+    dv.chunk_hi = chi;
+    dv.n_kept = (int)n_kept;
+    dv.n_grid = (int)n_grid;
+    dv.nchunks = nchunks;
+    for (int k = 0; k < 3; ++k) {
+        dv.dims[k] = dims[k];
+        dv.lo[k] = lo[k];
+        dv.bb_lo[k] = lo[k];
+        dv.bb_hi[k] = lo[k] + ext[k];
+    }
+    dv.h = h;
+    dv.inv_h = g.inv_h;
+    float sg = 0.f;
+    if (sgm != INT_MIN) sg = __builtin_bit_cast(float, sgm >= 0 ? sgm : sgm ^ 0x7FFFFFFF);
+    dv.sigma_tier = sg;
+    // slack for the FP32 rounding of cell coordinates and distances
+    float amax = 0.f;
+    for (int k = 0; k < 3; ++k) amax = std::max({amax, fabsf(lo[k]), fabsf(hi[k])});
+    dv.pad_abs = 4e-6f * std::max(amax, emax) + 1e-30f;
+    return CS_OK;
+}
+
+}  // namespace cs

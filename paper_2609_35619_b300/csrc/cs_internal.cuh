@@ -1,0 +1,212 @@
+// cs_internal.cuh -- internal definitions shared by the CUDA sources of the
+// collision-metric engine (sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "../../include/cs_b300.h"
+
+namespace cs {
+
+// ---------------------------------------------------------------- constants
+constexpr int kChunk = 32;             // Gaussians per chunk record (warp-level cull unit)
+constexpr int kMortonBits = 8;         // bits per axis of the query sort key
+constexpr int kCoarseDim = 16;         // coarse grid per axis for ordering the large tier
+constexpr int kSigmaBins = 512;        // log2 histogram of the largest scale
+constexpr float kSigmaLog2Lo = -32.f;  // histogram covers 2^-32 .. 2^32 in 1/8 octaves
+constexpr float kSigmaBinsPerOctave = 8.f;
+constexpr int64_t kMaxCells = 1ll << 22;
+constexpr float kReachPadRel = 1e-4f;  // relative padding of every cull radius
+
+// device error word bits
+constexpr unsigned kErrInvalidQuery = 1u;
+constexpr unsigned kErrTimeout = 2u;
+
+// bounded wait: polls of mbarrier.try_wait before giving up; the waits also
+// give up after one second of wall time
+constexpr long long kWaitPolls = 1ll << 27;
+
+// ------------------------------------------------------------- scene layout
+// Repacked Gaussian (48 B, three float4 arrays, sorted by grid key):
+//   pos  = (mu_x, mu_y, mu_z, max scale)
+//   covA = (Sxx, Syy, Szz, 2 Sxy)
+//   covB = (2 Sxz, 2 Syz, 0, bit pattern of the input row)
+// The off-diagonals are stored doubled so that d^T Sigma d needs 9 FP32 ops.
+struct SceneDev {
+    const float4 *pos = nullptr;
+    const float4 *covA = nullptr;
+    const float4 *covB = nullptr;
+    const uint32_t *cell_start = nullptr;  // [ncells + 1]: first sorted index of each cell
+    const float4 *chunk_lo = nullptr;      // [nchunks]: (min mu, max scale over the chunk)
+    const float4 *chunk_hi = nullptr;      // [nchunks]: (max mu, 0)
+    int n_kept = 0;
+    int n_grid = 0;       // [0, n_grid) grid tier, [n_grid, n_kept) large tier
+    int nchunks = 0;
+    int dims[3] = {1, 1, 1};
+    float lo[3] = {0, 0, 0};   // grid origin
+    float h = 1.f, inv_h = 1.f;
+    float sigma_tier = 0.f;    // max scale over the grid tier
+    float pad_abs = 0.f;       // absolute slack added to cull radii
+    float bb_lo[3] = {0, 0, 0}, bb_hi[3] = {1, 1, 1};  // box used for query sort keys
+};
+
+// Per-stream scratch of the query path.  Grown on demand, never shrunk, never
+// allocated per call once large enough.
+struct Workspace {
+    cudaStream_t stream = nullptr;
+    size_t cap_q = 0;
+    uint32_t *keys[2] = {nullptr, nullptr};
+    uint32_t *vals[2] = {nullptr, nullptr};
+    uint32_t *sort_hist = nullptr;   size_t cap_hist = 0;
+    uint32_t *scan_tmp = nullptr;    size_t cap_scan_tmp = 0;
+    float4 *qrec = nullptr;          // [Q * recs] prepared primitives, sorted order
+    float *qns = nullptr;            // [Q] n_sigma, sorted order
+    // host_io staging
+    float *io_prims = nullptr;       size_t cap_io_prims = 0;
+    float *io_ns = nullptr;
+    float *io_metric = nullptr;
+    uint8_t *io_collide = nullptr;
+    int32_t *io_count = nullptr;
+    float *io_grad = nullptr;
+    float *io_gout = nullptr;
+    float *io_gm = nullptr;
+    uint8_t *io_gc = nullptr;
+    unsigned *err = nullptr;         // device error word
+};
+
+struct Scene {
+    SceneDev dev;
+    int64_t n_input = 0, n_kept = 0, n_grid = 0, n_large = 0, n_invalid = 0;
+    int64_t ncells = 0;
+    int64_t device_bytes = 0;
+    void *blocks[8] = {};            // owned device allocations
+    int nblocks = 0;
+    int device = 0;
+    int num_sms = 148;
+    uint32_t magic = 0;
+};
+
+// Query scratch is pooled per (device, stream) and shared by every scene
+// used on that stream; it lives until cs_release_scratch or process exit.
+cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io, Workspace **out);
+Workspace *find_workspace(int device, cudaStream_t stream);
+
+constexpr uint32_t kSceneMagic = 0xC5B300A1u;
+
+// ------------------------------------------------------- launch accounting
+// Host-side count of kernel launches (cs_launch_count); every launcher adds
+// the number of kernels it enqueues.
+void count_launches(int n);
+
+// ---------------------------------------------------- error helpers (host)
+void set_error(const std::string &msg);
+cs_status cuda_fail(cudaError_t e, const char *what);
+
+#define CS_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::cs::cuda_fail(e_, #call);      \
+    } while (0)
+
+// ---------------------------------------------------- primitives (host API)
+size_t scan_tmp_elems(size_t n);
+// exclusive scan of n uint32 values (in may equal out); tmp from scan_tmp_elems
+void scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s);
+
+size_t sort_hist_elems(size_t n);
+// stable LSD radix sort of (keys, vals) on the low `bits` bits; the result is
+// in keys[res], vals[res] where res (0 or 1) is returned.
+int radix_sort(uint32_t *keys[2], uint32_t *vals[2], size_t n, int bits, uint32_t *hist,
+               uint32_t *scan_tmp, cudaStream_t s);
+
+// ------------------------------------------------------ device-side helpers
+__device__ __forceinline__ int float_to_ordered(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float ordered_to_float(int i) {
+    return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// One poll; true when the phase with the given parity has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 1-D bulk copy global -> shared, completing `bytes` on the mbarrier.  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, unsigned bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Reach of a cull: every pair whose centre distance exceeds
+// R(sigma) = alpha sigma + sqrt(alpha^2 sigma^2 + beta) has st^2 > S_reach,
+// where (alpha, beta) come from the primitive (see prepare kernels).
+__device__ __forceinline__ float reach(float alpha, float beta, float sigma, float pad_abs) {
+    float a = alpha * sigma;
+    return (a + sqrtf(fmaf(a, a, beta))) * (1.f + kReachPadRel) + pad_abs;
+}
+
+}  // namespace cs

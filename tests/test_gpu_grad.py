@@ -1,0 +1,151 @@
+"""Adjoint kernel (cs_query_grad) and pose chain vs the FP64 oracle's
+analytic gradient and central finite differences.
+
+Tolerance: |g_gpu - g_oracle| <= 1e-4 |g_oracle| + 1e-5 * scale, where scale
+is the sum of the norms of the terms the gradient sums (the oracle returns
+it): the summed terms may cancel, and FP32 terms are each accurate to a few
+ulp of their own size.  Rows with a pair within 1e-5 of a kink of the
+gradient (st^2 = s_min, the Eq. 8 clamp, the cutoff) are excluded and counted.
+"""
+import numpy as np
+import pytest
+
+import cs_synth as S
+import oracle
+from oracle import pose as opose
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cs(cuda_device):
+    import paper_2609_35619_b300 as cs
+    return cs
+
+
+def _scene(cs, sc):
+    return cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"])
+
+
+def _check(g_gpu, g_orc, scale, exclude, label):
+    ok = ~exclude
+    err = np.linalg.norm(g_gpu[ok] - g_orc[ok], axis=1)
+    tol = 1e-4 * np.linalg.norm(g_orc[ok], axis=1) + 1e-5 * scale[ok] + 1e-12
+    bad = err > tol
+    assert not bad.any(), (f"{label}: {bad.sum()}/{ok.sum()} gradient mismatches; "
+                           f"gpu={g_gpu[ok][bad][:3]} oracle={g_orc[ok][bad][:3]}")
+    return int(exclude.sum())
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("prim_type", [0, 1])
+def test_adjoint_matches_oracle(cs, mode, prim_type):
+    sc = S.tiny_scene(n=3000)
+    rng = np.random.default_rng(100 + mode)
+    Q = 700
+    c = rng.uniform(0, 2, (Q, 3))
+    prims = (np.c_[c, rng.uniform(0.05, 0.25, Q)] if prim_type == 0
+             else S.ellipsoid_queries(7, c)).astype(np.float32)
+    scene = _scene(cs, sc)
+    up = rng.normal(size=Q).astype(np.float32)
+    for ns in (0.0, 1.0, 2.0):
+        g = scene.query_grad(torch.as_tensor(prims), ns, grad_out=torch.as_tensor(up), prim_type=prim_type,
+                             params=cs.QueryParams(mode=mode)).cpu().numpy()
+        go, scale = oracle.grad(sc, prims, prim_type, ns, mode, grad_out=up.astype(np.float64),
+                                return_scale=True)
+        orc = oracle.query(sc, prims, prim_type, ns)
+        excl = (orc["band_cut"] > 0) | (orc["band_kink"] > 0)
+        if mode == 2:  # the arg-min pair must be unambiguous
+            excl |= orc["band_in"] < 0  # (no extra condition; ties are measure-zero)
+        _check(g, go, scale, excl, f"mode={mode} prim={prim_type} ns={ns}")
+
+
+def test_adjoint_group_upstream(cs):
+    sc = S.tiny_scene()
+    q = S.tiny_queries(q=640)
+    scene = _scene(cs, sc)
+    G = 64
+    up = np.random.default_rng(1).normal(size=q.shape[0] // G).astype(np.float32)
+    g = scene.query_grad(torch.as_tensor(q), 1.0, grad_out=torch.as_tensor(up),
+                         params=cs.QueryParams(group_size=G)).cpu().numpy()
+    go, scale = oracle.grad(sc, q, 0, 1.0, grad_out=np.repeat(up, G).astype(np.float64), return_scale=True)
+    orc = oracle.query(sc, q, 0, 1.0)
+    _check(g, go, scale, (orc["band_cut"] > 0) | (orc["band_kink"] > 0), "group upstream")
+
+
+def test_adjoint_against_central_differences(cs):
+    """Central differences (h = 1e-4 m) of the GPU metric itself agree with
+    the GPU adjoint where no kink lies within the stencil."""
+    sc = S.tiny_scene()
+    rng = np.random.default_rng(2)
+    Q = 200
+    q = np.c_[rng.uniform(0.2, 1.8, (Q, 3)), rng.uniform(0.1, 0.25, Q)].astype(np.float32)
+    scene = _scene(cs, sc)
+    g = scene.query_grad(torch.as_tensor(q), 1.0, params=cs.QueryParams(mode=1)).cpu().numpy()
+    h = 1e-4
+    fd = np.zeros((Q, 3))
+    stable = np.ones(Q, bool)
+    base = scene.query(torch.as_tensor(q), 1.0, want_count=True, params=cs.QueryParams(mode=1))
+    for a in range(3):
+        vals = []
+        for s in (h, -h):
+            qq = q.astype(np.float64).copy()
+            qq[:, a] += s
+            qq = qq.astype(np.float32)
+            out = scene.query(torch.as_tensor(qq), 1.0, want_count=True, params=cs.QueryParams(mode=1))
+            stable &= (out["count"] == base["count"]).cpu().numpy()
+            step = qq[:, a].astype(np.float64) - q[:, a]
+            vals.append((out["metric"].cpu().numpy().astype(np.float64), step))
+        fd[:, a] = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+    orc = oracle.query(sc, q, 0, 1.0)
+    stable &= orc["band_kink"] == 0
+    m = base["metric"].cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(g - fd, axis=1)[stable]
+    # FP32 metric differences over 2h: noise ~ 1e-7 |m| / h
+    tol = 2e-3 * np.linalg.norm(g, axis=1)[stable] + 4e-7 * np.abs(m[stable]) / h + 1e-6
+    assert (err <= tol).all(), (err[err > tol][:5], tol[err > tol][:5])
+    assert stable.sum() > Q // 2
+
+
+def test_pose_chain_forward_and_adjoint(cs):
+    poses, offs, r = S.trajectory_poses(trajectories=16, waypoints=16)
+    P = poses.shape[0]
+    tp = torch.as_tensor(poses, device="cuda")
+    to = torch.as_tensor(offs, device="cuda")
+    sph = cs.pose_spheres(tp, to, r).cpu().numpy()
+    want = opose.centres(poses, offs).reshape(-1, 3)
+    np.testing.assert_allclose(sph[:, :3], want, rtol=0, atol=2e-6)
+    assert (sph[:, 3] == np.float32(r)).all()
+    gc = np.random.default_rng(3).normal(size=(P * offs.shape[0], 3)).astype(np.float32)
+    gp = cs.pose_spheres_grad(tp, to, torch.as_tensor(gc, device="cuda")).cpu().numpy()
+    want_g = opose.pose_grad(poses, offs, gc.reshape(P, -1, 3))
+    np.testing.assert_allclose(gp, want_g, rtol=1e-4, atol=1e-5)
+
+
+def test_collision_cost_autograd(cs):
+    """torch.autograd through CollisionCost equals the oracle chain: the
+    metric gradient of each sphere (oracle) pushed through the pose adjoint
+    (oracle)."""
+    sc = S.tabletop_scene(n=200_000)
+    poses, offs, r = S.trajectory_poses(trajectories=32, waypoints=16)
+    scene = _scene(cs, sc)
+    tp = torch.tensor(poses, device="cuda", requires_grad=True)
+    to = torch.as_tensor(offs, device="cuda")
+    cost = cs.CollisionCost.apply(tp, scene, to, r, 1.0, None)
+    w = torch.as_tensor(np.random.default_rng(4).normal(size=poses.shape[0]).astype(np.float32), device="cuda")
+    (cost * w).sum().backward()
+    g = tp.grad.cpu().numpy()
+    sph = opose.centres(poses, offs).reshape(-1, 3)
+    prims = np.c_[sph, np.full(sph.shape[0], r)].astype(np.float32)
+    K = offs.shape[0]
+    orc = oracle.query(sc, prims, 0, 1.0)
+    np.testing.assert_allclose(cost.detach().cpu().numpy(),
+                               orc["mean_cost"].reshape(-1, K).sum(1), rtol=1e-4, atol=1e-7)
+    gsph = oracle.grad(sc, prims, 0, 1.0, grad_out=np.repeat(w.cpu().numpy(), K).astype(np.float64))
+    want = opose.pose_grad(poses, offs, gsph.reshape(-1, K, 3))
+    ok = (orc["band_cut"].reshape(-1, K).sum(1) == 0) & (orc["band_kink"].reshape(-1, K).sum(1) == 0)
+    err = np.linalg.norm(g - want, axis=1)[ok]
+    tol = 1e-3 * np.linalg.norm(want, axis=1)[ok] + 1e-4 * np.abs(want).max() + 1e-9
+    assert (err <= tol).all(), (err[err > tol][:5], tol[err > tol][:5])
+    assert np.abs(want).max() > 0

@@ -1,0 +1,329 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Small cases cover every output and mode on scenes the oracle finishes in
+seconds (several tiles and a ragged tail); the full-size workloads run in the
+launch configuration the benchmark times and are checked on a seeded sample
+of rows that the oracle evaluates one by one.
+"""
+import numpy as np
+import pytest
+
+import cs_synth as S
+import oracle
+from _parity import compare, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cs(cuda_device):
+    import paper_2609_35619_b300 as cs
+    return cs
+
+
+def _scene(cs, sc, **kw):
+    return cs.Scene(sc["means"], sc["scales"], sc["quats"], sc.get("opacity"), **kw)
+
+
+def _run(cs, scene, prims, ns, prim_type=0, mode=0, nsq=None, **kw):
+    params = cs.QueryParams(mode=mode, **kw)
+    out = scene.query(torch.as_tensor(prims), ns, prim_type=prim_type, params=params, want_count=True,
+                      nsigma_per_query=None if nsq is None else torch.as_tensor(nsq, dtype=torch.float32))
+    torch.cuda.synchronize()
+    return to_np(out)
+
+
+def _oracle_params(**kw):
+    return oracle.Params(**kw)
+
+
+# ------------------------------------------------------------- config 1
+@pytest.mark.parametrize("nsigma", [0.0, 0.5, 1.0, 2.0])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_tiny_scene_all_modes(cs, nsigma, mode):
+    sc = S.tiny_scene()
+    q = S.tiny_queries()
+    scene = _scene(cs, sc)
+    out = _run(cs, scene, q, nsigma, mode=mode)
+    orc = oracle.query(sc, q, 0, nsigma)
+    rep = compare(out, orc, mode, oracle.Params(), f"tiny ns={nsigma} mode={mode}")
+    assert rep["checked"] > 0.9 * rep["Q"]
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+@pytest.mark.parametrize("Q", [1, 37, 1000, 5000])
+def test_tile_configs_and_ragged_batches(cs, cfg, Q):
+    """Every tile shape, batch sizes spanning one to many tiles with a ragged tail."""
+    sc = S.tiny_scene(n=3000)
+    rng = np.random.default_rng(Q)
+    q = np.c_[rng.uniform(0, 2, (Q, 3)), rng.uniform(0.05, 0.3, Q)].astype(np.float32)
+    scene = _scene(cs, sc)
+    out = _run(cs, scene, q, 1.0, tile_config=cfg)
+    compare(out, oracle.query(sc, q, 0, 1.0), 0, oracle.Params(), f"cfg={cfg} Q={Q}")
+
+
+def test_per_query_nsigma_and_k_thr(cs):
+    sc = S.tiny_scene()
+    q = S.tiny_queries(q=700)
+    rng = np.random.default_rng(3)
+    ns = rng.uniform(0, 2.5, q.shape[0]).astype(np.float32)
+    scene = _scene(cs, sc)
+    for k_thr in (0, 3):
+        out = _run(cs, scene, q, 0.0, nsq=ns, k_thr=k_thr)
+        orc = oracle.query(sc, q, 0, ns.astype(np.float64), oracle.Params(k_thr=k_thr))
+        compare(out, orc, 0, oracle.Params(), f"per-row n_sigma k_thr={k_thr}")
+
+
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_ellipsoids(cs, mode):
+    sc = S.tiny_scene()
+    rng = np.random.default_rng(4)
+    centres = rng.uniform(0, 2, (600, 3))
+    e = S.ellipsoid_queries(5, centres)
+    scene = _scene(cs, sc)
+    for cfg in (1, 2):
+        out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode, tile_config=cfg)
+        compare(out, oracle.query(sc, e, 1, 1.0), mode, oracle.Params(), f"ellipsoid mode={mode}")
+
+
+def test_nondefault_metric_parameters(cs):
+    sc = S.tiny_scene()
+    q = S.tiny_queries()
+    kw = dict(gamma=2.0, d_max=3.0, s_min=1.5, eps=1e-4, tau=0.2)
+    scene = _scene(cs, sc)
+    for mode in (0, 1, 3):
+        out = _run(cs, scene, q, 1.0, mode=mode, **kw)
+        compare(out, oracle.query(sc, q, 0, 1.0, oracle.Params(**kw)), mode, oracle.Params(**kw),
+                f"params mode={mode}")
+
+
+def test_group_outputs(cs):
+    sc = S.tiny_scene()
+    q = S.tiny_queries(q=1000)
+    scene = _scene(cs, sc)
+    for G in (32, 64, 7):
+        params = cs.QueryParams(group_size=G)
+        out = to_np(scene.query(torch.as_tensor(q), 1.0, params=params))
+        orc = oracle.query(sc, q, 0, 1.0)
+        gm, gc = oracle.group_reduce(orc["mean_cost"], orc["collide"], G)
+        assert out["group_metric"].shape == gm.shape
+        np.testing.assert_allclose(out["group_metric"], gm, rtol=2e-5, atol=1e-30)
+        band = np.add.reduceat(orc["band_in"], np.arange(0, q.shape[0], G)) > 0
+        assert (out["group_collide"][~band] == gc[~band]).all()
+        # the per-row sums reproduce the group sums
+        per_row = out["metric"].astype(np.float64)
+        np.testing.assert_allclose(np.add.reduceat(per_row, np.arange(0, q.shape[0], G)),
+                                   out["group_metric"], rtol=1e-5)
+
+
+# --------------------------------------------------------------- edge cases
+def test_empty_batch_and_empty_scene(cs):
+    sc = S.tiny_scene()
+    scene = _scene(cs, sc)
+    res = scene.query(torch.zeros((0, 4)), 1.0)
+    assert res["metric"].numel() == 0
+    empty = cs.Scene(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 4)))
+    assert empty.info()["n_kept"] == 0
+    out = to_np(empty.query(torch.as_tensor(S.tiny_queries()), 1.0, want_count=True))
+    assert (out["metric"] == 0).all() and (out["collide"] == 0).all() and (out["count"] == 0).all()
+    out = to_np(empty.query(torch.as_tensor(S.tiny_queries()), 1.0,
+                            params=cs.QueryParams(mode=2)))
+    assert np.isinf(out["metric"]).all()
+
+
+def test_all_filtered_and_invalid_rows(cs):
+    n = 500
+    rng = np.random.default_rng(6)
+    sc = {"means": rng.uniform(0, 1, (n, 3)).astype(np.float32),
+          "scales": np.full((n, 3), 0.2, np.float32),
+          "quats": np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+          "opacity": np.full(n, 0.01, np.float32)}
+    scene = _scene(cs, sc)
+    assert scene.info()["n_kept"] == 0
+    sc["means"][:10] = np.nan
+    sc["opacity"][:] = 0.9
+    scene = _scene(cs, sc)
+    inf = scene.info()
+    assert inf["n_invalid"] == 10 and inf["n_kept"] == n - 10
+    q = np.c_[rng.uniform(0, 1, (64, 3)), np.full(64, 0.1)].astype(np.float32)
+    out = _run(cs, scene, q, 1.0)
+    good = {k: v[10:] for k, v in sc.items()}
+    compare(out, oracle.query(good, q, 0, 1.0), 0, oracle.Params(), "invalid gaussian rows")
+
+
+def test_invalid_query_rows_reported(cs):
+    sc = S.tiny_scene()
+    scene = _scene(cs, sc)
+    q = S.tiny_queries(q=100).copy()
+    q[5, 3] = -1.0
+    q[7, 0] = np.nan
+    out = _run(cs, scene, q, 1.0)
+    assert np.isnan(out["metric"][5]) and np.isnan(out["metric"][7]) and out["collide"][5] == 0
+    with pytest.raises(cs.CsError) as ei:
+        scene.sync()
+    assert ei.value.status == cs.abi.CS_ERR_INVALID_ARG
+    scene.sync()  # cleared
+    keep = np.setdiff1d(np.arange(100), [5, 7])
+    sub = {k: v[keep] for k, v in out.items()}
+    compare(sub, oracle.query(sc, q[keep], 0, 1.0), 0, oracle.Params(), "valid rows beside invalid")
+
+
+def test_degenerate_gaussians_and_far_queries(cs):
+    """2DGS-style disks (a zero scale), zero-size points, identity-less zero
+    quaternions, queries far outside the scene box."""
+    rng = np.random.default_rng(7)
+    n = 1500
+    sc = S.tiny_scene(n=n)
+    sc["scales"][:300, 2] = 0.0
+    sc["scales"][300:400] = 0.0
+    sc["quats"][400:450] = 0.0
+    q = S.tiny_queries(q=300).copy()
+    q[:20, :3] += 50.0
+    q[20:40, :3] -= 3.0
+    scene = _scene(cs, sc)
+    for ns in (0.0, 1.5):
+        out = _run(cs, scene, q, ns)
+        compare(out, oracle.query(sc, q, 0, ns), 0, oracle.Params(), f"degenerate ns={ns}")
+
+
+@pytest.mark.parametrize("kw", [dict(cell_size=0.02), dict(cell_size=5.0), dict(tier_quantile=0.5),
+                                dict(tier_quantile=1.0), dict(use_filter=False)])
+def test_scene_build_options(cs, kw):
+    """Tiny cells (many rows), one cell, a large tier holding half the scene,
+    no large tier, the floater filter off: the results do not change."""
+    sc = S.tiny_scene()
+    q = S.tiny_queries()
+    scene = _scene(cs, sc, **kw)
+    out = _run(cs, scene, q, 2.0)
+    p = oracle.Params(use_filter=kw.get("use_filter", True))
+    compare(out, oracle.query(sc, q, 0, 2.0, p), 0, p, f"build {kw}")
+
+
+def test_repack_matches_eq2(cs):
+    """The exported 48-byte records equal the oracle's Eq. 2 covariances, in
+    grid order, and the index permutation covers the kept rows exactly once."""
+    sc = S.tiny_scene(n=4000)
+    scene = _scene(cs, sc)
+    pos, cov, idx = (t.cpu().numpy() for t in scene.export())
+    sig, keep = oracle.covariances(sc)
+    assert sorted(idx.tolist()) == np.flatnonzero(keep).tolist()
+    np.testing.assert_array_equal(pos[:, :3], sc["means"][idx])
+    np.testing.assert_allclose(pos[:, 3], sc["scales"][idx].max(1), rtol=0)
+    S_ = sig[idx]
+    scale = np.abs(S_).reshape(len(idx), -1).max(1)
+    want = np.stack([S_[:, 0, 0], S_[:, 1, 1], S_[:, 2, 2], 2 * S_[:, 0, 1], 2 * S_[:, 0, 2],
+                     2 * S_[:, 1, 2]], 1)
+    np.testing.assert_allclose(cov[:, :6], want, rtol=0, atol=4e-7 * scale.max())
+    assert (np.abs(cov[:, :6] - want) <= 1e-6 * scale[:, None]).all()
+    inf = scene.info()
+    assert inf["n_grid"] + inf["n_large"] == inf["n_kept"]
+
+
+def test_alone_equals_in_the_mix(cs):
+    """A row's result does not depend on which other rows share its launch
+    (bitwise): every neighbour is visited in the same global order."""
+    sc = S.tiny_scene()
+    q = S.tiny_queries(q=2000)
+    scene = _scene(cs, sc)
+    full = _run(cs, scene, q, 1.0)
+    rng = np.random.default_rng(8)
+    sub = rng.choice(2000, 77, replace=False)
+    part = _run(cs, scene, q[sub], 1.0)
+    np.testing.assert_array_equal(part["metric"], full["metric"][sub])
+    np.testing.assert_array_equal(part["count"], full["count"][sub])
+
+
+def test_host_io_path_equals_device_path(cs):
+    sc = S.tiny_scene()
+    q = S.tiny_queries(q=900)
+    scene = _scene(cs, sc)
+    dev = _run(cs, scene, q, 1.0, group_size=32)
+    p = cs.QueryParams(group_size=32).to_c()
+    p.host_io = 1
+    Q = q.shape[0]
+    m = np.empty(Q, np.float32)
+    c = np.empty(Q, np.uint8)
+    cnt = np.empty(Q, np.int32)
+    gm = np.empty((Q + 31) // 32, np.float32)
+    gc = np.empty_like(gm, dtype=np.uint8)
+    p.out_count = cnt.ctypes.data
+    p.out_group_metric = gm.ctypes.data
+    p.out_group_collide = gc.ctypes.data
+    cs.check(cs.abi.cs_query(scene.handle, 0, q, Q, 1.0, m, c, p))
+    np.testing.assert_array_equal(m, dev["metric"])
+    np.testing.assert_array_equal(c, dev["collide"])
+    np.testing.assert_array_equal(cnt, dev["count"])
+    np.testing.assert_array_equal(gm, dev["group_metric"])
+
+
+def test_pair_stats(cs):
+    sc = S.tiny_scene()
+    q = S.tiny_queries()
+    scene = _scene(cs, sc)
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    out = to_np(scene.query(torch.as_tensor(q), 1.0, want_count=True, pair_stats=stats))
+    st = stats.cpu().numpy()
+    assert st[1] == out["count"].sum()
+    assert st[0] >= st[1] and st[0] <= q.shape[0] * sc["means"].shape[0]
+
+
+def test_wait_timeout_selftest_leaves_context_usable(cs):
+    assert cs.abi.cs_selftest_wait_timeout(2000, None) == cs.abi.CS_ERR_TIMEOUT
+    sc = S.tiny_scene()
+    q = S.tiny_queries()
+    out = _run(cs, _scene(cs, sc), q, 1.0)
+    compare(out, oracle.query(sc, q, 0, 1.0), 0, oracle.Params(), "after timeout self-test")
+
+
+# ------------------------------------------------- full-size workloads
+def _sample(Q, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(Q, size=min(k, Q), replace=False))
+
+
+def test_drone_mppi_full_size(cs):
+    """500k-Gaussian room, 1,024 rollouts x 32 steps, per-rollout outputs."""
+    sc = S.drone_scene()
+    q = S.drone_queries()
+    scene = _scene(cs, sc)
+    out = _run(cs, scene, q, 1.0, group_size=32)
+    idx = _sample(q.shape[0], 192, 11)
+    orc = oracle.query(sc, q[idx], 0, 1.0)
+    rep = compare({k: v[idx] for k, v in out.items() if v.shape[0] == q.shape[0]}, orc, 0,
+                  oracle.Params(), "drone sample")
+    assert rep["checked"] > 150
+    # group outputs are the sums of the per-row outputs
+    np.testing.assert_allclose(out["group_metric"], out["metric"].reshape(-1, 32).astype(np.float64).sum(1),
+                               rtol=1e-5)
+    assert (out["group_collide"] == out["collide"].reshape(-1, 32).max(1)).all()
+
+
+@pytest.mark.parametrize("nsigma", [0.0, 0.5, 1.0, 2.0])
+def test_tabletop_full_size(cs, nsigma):
+    """1M-Gaussian tabletop, 262,144 arm spheres + 2,097,152 RRT edge spheres
+    in one launch (the benchmark's launch), sampled rows checked."""
+    sc = _TABLE["scene"]
+    q = _TABLE["queries"]
+    scene = _TABLE.get("gpu") or _scene(cs, sc)
+    _TABLE["gpu"] = scene
+    out = _run(cs, scene, q, nsigma)
+    idx = _sample(q.shape[0], 128, 12 + int(nsigma * 10))
+    # bias the sample towards rows that touch the scene
+    touching = np.flatnonzero(out["count"] > 0)
+    idx2 = np.random.default_rng(13).choice(touching, size=min(64, touching.size), replace=False)
+    idx = np.unique(np.r_[idx, idx2])
+    orc = oracle.query(sc, q[idx], 0, nsigma)
+    rep = compare({k: v[idx] for k, v in out.items()}, orc, 0, oracle.Params(), f"tabletop ns={nsigma}")
+    assert rep["checked"] > 100
+
+
+_TABLE = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _tabletop_data():
+    _TABLE["scene"] = S.tabletop_scene()
+    _TABLE["queries"] = np.concatenate([S.arm_queries(), S.edge_queries()])
+    yield
+    _TABLE.clear()
