@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="step", choices=["step", "eval"],
+                    help="eval: the profiling case -- build the tabletop scene, then one warm-up "
+                         "and one measured query of the 262,144 arm spheres at n_sigma=1 "
+                         "(two fused-kernel launches); prints a short JSON summary")
     return ap.parse_args()
 
 
@@ -394,8 +398,34 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_eval_case(args):
+    """Small case for kernel profiles: one scene build and two launches of the
+    fused kernel over the 262,144 arm spheres (the second is the measured one)."""
+    import torch
+
+    import cs_synth as S
+    import paper_2609_35619_b300 as cs
+    dev = torch.device("cuda", 0)
+    sc = S.tabletop_scene()
+    arm = torch.as_tensor(S.arm_queries(), device=dev)
+    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    scene.query(arm, 1.0, params=cs.QueryParams(group_size=64))
+    scene.query(arm, 1.0, params=cs.QueryParams(group_size=64), pair_stats=stats, eval_events=ev)
+    torch.cuda.synchronize()
+    scene.sync()
+    cand, useful = stats.cpu().tolist()
+    ms = ev[0].elapsed_time(ev[1])
+    print(json.dumps({"case": "eval", "queries": arm.shape[0], "useful_pairs": useful,
+                      "candidate_pairs": cand, "eval_ms": ms, "info": scene.info()}))
+
+
 def main():
     args = parse()
+    if args.case == "eval":
+        run_eval_case(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if world > 1 and args.impl == "ours":

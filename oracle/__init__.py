@@ -178,7 +178,8 @@ def grad(scene, prims, prim_type: int, nsigma, mode: int = MODE_MEAN,
     """Analytic gradient of the per-query metric with respect to the
     primitive centres, [Q,3], scaled by grad_out [Q] (ones if None).  With
     return_scale, also the sum of the norms of the summed terms per query
-    (the conditioning of the sum)."""
+    (each term's size counted as the sum of the sizes of its two parts, which
+    may cancel: the conditioning of the sum)."""
     params = params or Params()
     lib = _load()
     means, scales, quats, op = _scene_arrays(scene)

@@ -298,7 +298,8 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
  *   sqrt(sigma^2)          = 2 sqrt(w^T Sigma w)
  *   d sqrt(sigma^2) / d c  = -2 A Sigma w / sqrt(w^T Sigma w)               */
 static void st2_grad(const double mu[3], const double Sig[3][3], const double c[3],
-                     const double A[3][3], double nsigma, double *st2_out, double gvec[3])
+                     const double A[3][3], double nsigma, double *st2_out, double gvec[3],
+                     double *gmag)
 {
     double d[3] = {mu[0] - c[0], mu[1] - c[1], mu[2] - c[2]};
     double w[3];
@@ -312,13 +313,19 @@ static void st2_grad(const double mu[3], const double Sig[3][3], const double c[
     double raw = s2 - nsigma * 2.0 * root;
     *st2_out = raw > 0.0 ? raw : 0.0;
     for (int a = 0; a < 3; ++a) gvec[a] = 0.0;
+    *gmag = 0.0;
     if (!(raw > 0.0)) return;
     double ASw[3];
     for (int a = 0; a < 3; ++a) ASw[a] = A[a][0] * Sw[0] + A[a][1] * Sw[1] + A[a][2] * Sw[2];
+    double m1 = 0.0, m2 = 0.0;
     for (int a = 0; a < 3; ++a) {
-        gvec[a] = -2.0 * w[a];
-        if (root > 0.0) gvec[a] += nsigma * 2.0 * ASw[a] / root;
+        double p1 = -2.0 * w[a], p2 = root > 0.0 ? nsigma * 2.0 * ASw[a] / root : 0.0;
+        gvec[a] = p1 + p2;
+        m1 += p1 * p1;
+        m2 += p2 * p2;
     }
+    /* size of the two parts, which may cancel: the conditioning of the term */
+    *gmag = sqrt(m1) + sqrt(m2);
 }
 
 /* Gradient of the per-query metric with respect to the primitive centre.
@@ -359,8 +366,8 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
             const double *S = Sig + 9 * i;
             double Sg[3][3] = {{S[0], S[1], S[2]}, {S[3], S[4], S[5]}, {S[6], S[7], S[8]}};
             double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-            double st2, g[3];
-            st2_grad(mu, Sg, c, A, ns, &st2, g);
+            double st2, g[3], gm;
+            st2_grad(mu, Sg, c, A, ns, &st2, g, &gm);
             if (!(st2 <= S_cut)) continue;
             ++cnt;
             if (mode == 0 || mode == 1) {
@@ -368,12 +375,12 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
                 if (st2 > prm->s_min) {
                     double dc = pair_cost(prm, st2);
                     for (int a = 0; a < 3; ++a) acc[a] += -prm->gamma * dc * g[a];
-                    mag += prm->gamma * dc * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                    mag += prm->gamma * dc * gm;
                 }
             } else if (mode == 2) {
                 if (st2 < best) {
                     best = st2; best_g[0] = g[0]; best_g[1] = g[1]; best_g[2] = g[2];
-                    mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                    mag = gm;
                 }
             } else {
                 double x = st2 / prm->tau;
@@ -381,13 +388,13 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
                     double r = exp(x - sm_m);
                     sm_acc = sm_acc * r + 1.0;
                     for (int a = 0; a < 3; ++a) sm_g[a] = sm_g[a] * r + g[a];
-                    mag = mag * r + sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                    mag = mag * r + gm;
                     sm_m = x;
                 } else {
                     double e = exp(sm_m - x);
                     sm_acc += e;
                     for (int a = 0; a < 3; ++a) sm_g[a] += e * g[a];
-                    mag += e * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                    mag += e * gm;
                 }
             }
         }

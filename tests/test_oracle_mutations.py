@@ -20,7 +20,7 @@ MUTATIONS = {
                    "double w = qf[3], x = qf[0], y = qf[1], z = qf[2];"),
     "filter_or": ("return !(opacity[i] < prm->opacity_min && smax > prm->extent_max);",
                   "return !(opacity[i] < prm->opacity_min || smax > prm->extent_max);"),
-    "grad_sign": ("gvec[a] = -2.0 * w[a];", "gvec[a] = 2.0 * w[a];"),
+    "grad_sign": ("double p1 = -2.0 * w[a], p2", "double p1 = 2.0 * w[a], p2"),
     "eq6_not_inverse": ("double P[3] = {1.0 / (ax * ax), 1.0 / (bx * bx), 1.0 / (cx * cx)};",
                         "double P[3] = {ax * ax, bx * bx, cx * cx};"),
 }
