@@ -29,6 +29,7 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
                      float *grad_centres, unsigned *err, int num_sms, long long polls,
                      cudaStream_t s);
 cudaError_t run_wait_selftest(long long polls, unsigned *err, cudaStream_t s);
+void launch_export(const SceneDev &sc, float *pos, float *cov, int32_t *index, cudaStream_t s);
 
 static thread_local std::string g_err;
 static std::atomic<int64_t> g_launches{0};
@@ -242,16 +243,8 @@ cs_status cs_scene_export(const cs_scene *s, float *pos, float *cov, int32_t *in
     cudaStream_t cs_ = (cudaStream_t)stream;
     const int64_t n = sc->n_kept;
     if (n == 0) return CS_OK;
-    if (pos) CS_CUDA(cudaMemcpyAsync(pos, sc->dev.pos, 16 * n, cudaMemcpyDeviceToDevice, cs_));
-    if (cov) {
-        CS_CUDA(cudaMemcpy2DAsync(cov, 32, sc->dev.covA, 16, 16, n, cudaMemcpyDeviceToDevice, cs_));
-        CS_CUDA(cudaMemcpy2DAsync((char *)cov + 16, 32, sc->dev.covB, 16, 8, n,
-                                  cudaMemcpyDeviceToDevice, cs_));
-        CS_CUDA(cudaMemset2DAsync((char *)cov + 24, 32, 0, 8, n, cs_));
-    }
-    if (index)
-        CS_CUDA(cudaMemcpy2DAsync(index, 4, (const char *)sc->dev.covB + 12, 16, 4, n,
-                                  cudaMemcpyDeviceToDevice, cs_));
+    launch_export(sc->dev, pos, cov, index, cs_);
+    CS_CUDA(cudaGetLastError());
     return CS_OK;
 }
 

@@ -125,8 +125,27 @@ __device__ __forceinline__ int cell_coord(float x, float lo, float inv_h, int di
     return min(max(c, 0), dim - 1);
 }
 
-// Sort key of each Gaussian: grid cell for the grid tier, ncells + coarse
-// cell for the large tier, ncells + kCoarse^3 for dropped rows.
+// Position of x inside its cell on a 2^kFineBits grid (orders Gaussians inside
+// a cell so that chunks of 32 consecutive ones are spatially compact).
+__device__ __forceinline__ uint32_t fine_coord(float x, float lo, float inv_h, int c) {
+    float f = ((x - lo) * inv_h - (float)c) * (float)(1 << kFineBits);
+    return (uint32_t)min(max((int)floorf(f), 0), (1 << kFineBits) - 1);
+}
+
+__device__ __forceinline__ uint32_t fine_morton(uint32_t fx, uint32_t fy, uint32_t fz) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < kFineBits; ++b)
+        m |= (((fx >> b) & 1u) << (3 * b)) | (((fy >> b) & 1u) << (3 * b + 1)) |
+             (((fz >> b) & 1u) << (3 * b + 2));
+    return m;
+}
+
+constexpr int kFineKeyBits = 3 * kFineBits;
+
+// Sort key of each Gaussian: (grid cell, fine position) for the grid tier,
+// (ncells + coarse cell, fine position) for the large tier, and
+// ncells + kCoarse^3 for dropped rows.
 __global__ void __launch_bounds__(kThreads) k_keys(const float4 *__restrict__ pos,
                                                    const uint8_t *__restrict__ code, int64_t n,
                                                    GridParams g, uint32_t *__restrict__ keys,
@@ -135,20 +154,26 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float4 *__restrict__ po
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
     const uint32_t ncoarse = kCoarseDim * kCoarseDim * kCoarseDim;
-    uint32_t key = g.ncells + ncoarse;
+    uint32_t key = (g.ncells + ncoarse) << kFineKeyBits;
     if (code[i] == 1) {
         float4 p = pos[i];
         if (p.w <= g.sigma_tier) {
             int ix = cell_coord(p.x, g.lo[0], g.inv_h, g.dims[0]);
             int iy = cell_coord(p.y, g.lo[1], g.inv_h, g.dims[1]);
             int iz = cell_coord(p.z, g.lo[2], g.inv_h, g.dims[2]);
-            key = (uint32_t)ix + (uint32_t)g.dims[0] * ((uint32_t)iy + (uint32_t)g.dims[1] * (uint32_t)iz);
+            uint32_t cell = (uint32_t)ix + (uint32_t)g.dims[0] * ((uint32_t)iy + (uint32_t)g.dims[1] * (uint32_t)iz);
+            uint32_t f = fine_morton(fine_coord(p.x, g.lo[0], g.inv_h, ix), fine_coord(p.y, g.lo[1], g.inv_h, iy),
+                                     fine_coord(p.z, g.lo[2], g.inv_h, iz));
+            key = (cell << kFineKeyBits) | f;
             atomicMax(&st->sigma_grid_max, float_to_ordered(p.w));
         } else {
             int cx = cell_coord(p.x, g.lo[0], g.coarse_inv[0], kCoarseDim);
             int cy = cell_coord(p.y, g.lo[1], g.coarse_inv[1], kCoarseDim);
             int cz = cell_coord(p.z, g.lo[2], g.coarse_inv[2], kCoarseDim);
-            key = g.ncells + (uint32_t)(cx + kCoarseDim * (cy + kCoarseDim * cz));
+            uint32_t f = fine_morton(fine_coord(p.x, g.lo[0], g.coarse_inv[0], cx),
+                                     fine_coord(p.y, g.lo[1], g.coarse_inv[1], cy),
+                                     fine_coord(p.z, g.lo[2], g.coarse_inv[2], cz));
+            key = ((g.ncells + (uint32_t)(cx + kCoarseDim * (cy + kCoarseDim * cz))) << kFineKeyBits) | f;
         }
     }
     keys[i] = key;
@@ -157,30 +182,37 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float4 *__restrict__ po
 
 __global__ void k_count_keys(const uint32_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ cnt) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[keys[i]], 1u);
+    if (i < n) atomicAdd(&cnt[keys[i] >> kFineKeyBits], 1u);
 }
 
-__global__ void k_gather(const uint32_t *__restrict__ perm, int64_t n_kept,
+// One warp per chunk block: lane l fills Gaussian 32c + l (sorted order) and
+// the warp reduces the block's bounding box and largest scale.
+__global__ void k_blocks(const uint32_t *__restrict__ perm, int n_kept, int nchunks,
                          const float4 *__restrict__ pos, const float4 *__restrict__ covA,
-                         const float4 *__restrict__ covB, float4 *__restrict__ opos,
-                         float4 *__restrict__ ocovA, float4 *__restrict__ ocovB) {
-    int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (p >= n_kept) return;
-    uint32_t i = perm[p];
-    opos[p] = pos[i];
-    ocovA[p] = covA[i];
-    ocovB[p] = covB[i];
-}
-
-// One warp per chunk of kChunk consecutive sorted Gaussians.
-__global__ void k_chunks(const float4 *__restrict__ pos, int n_kept, int nchunks,
-                         float4 *__restrict__ clo, float4 *__restrict__ chi) {
+                         const float4 *__restrict__ covB, ChunkBlock *__restrict__ blocks,
+                         float *__restrict__ smax, int32_t *__restrict__ index) {
     int c = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (c >= nchunks) return;
     int p = c * kChunk + lane;
-    float4 v = p < n_kept ? pos[p] : pos[c * kChunk];
-    float lx = v.x, ly = v.y, lz = v.z, hx = v.x, hy = v.y, hz = v.z, sg = v.w;
+    ChunkBlock &b = blocks[c];
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+    float sg = 0.f;
+    if (p < n_kept) {
+        uint32_t i = perm[p];
+        float4 P = pos[i], A = covA[i], B = covB[i];
+        b.x[lane] = P.x; b.y[lane] = P.y; b.z[lane] = P.z;
+        b.sxx[lane] = A.x; b.syy[lane] = A.y; b.szz[lane] = A.z; b.sxy2[lane] = A.w;
+        b.sxz2[lane] = B.x; b.syz2[lane] = B.y;
+        smax[p] = P.w;
+        index[p] = (int32_t)i;
+        lx = hx = P.x; ly = hy = P.y; lz = hz = P.z; sg = P.w;
+    } else {
+        b.x[lane] = __int_as_float(0x7fc00000);  // never a neighbour
+        b.y[lane] = 0.f; b.z[lane] = 0.f;
+        b.sxx[lane] = 0.f; b.syy[lane] = 0.f; b.szz[lane] = 0.f;
+        b.sxy2[lane] = 0.f; b.sxz2[lane] = 0.f; b.syz2[lane] = 0.f;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
@@ -192,8 +224,8 @@ __global__ void k_chunks(const float4 *__restrict__ pos, int n_kept, int nchunks
         sg = fmaxf(sg, __shfl_xor_sync(0xffffffffu, sg, o));
     }
     if (lane == 0) {
-        clo[c] = make_float4(lx, ly, lz, sg);
-        chi[c] = make_float4(hx, hy, hz, 0.f);
+        b.lo = make_float4(lx, ly, lz, sg);
+        b.hi = make_float4(hx, hy, hz, 0.f);
     }
 }
 
@@ -241,11 +273,12 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     hs.sigma_grid_max = INT_MIN;
     CS_CUDA(cudaMemcpyAsync(d_stats.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     BuildStats *st = (BuildStats *)d_stats.p;
-    if (n > 0)
+    if (n > 0) {
         k_repack<<<blocks_for(n), kThreads, 0, s>>>(means, scales, quats, op, n, d->use_filter,
                                                     d->opacity_min, d->extent_max, upos, ucovA,
                                                     ucovB, code, st);
         count_launches(1);
+    }
     CS_CUDA(cudaGetLastError());
     CS_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     CS_CUDA(cudaStreamSynchronize(s));
@@ -309,6 +342,11 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     const uint32_t nkeys = g.ncells + ncoarse + 1;  // + dropped
     int bits = 1;
     while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)nkeys) ++bits;
+    bits += kFineKeyBits;
+    if (bits > 32) {
+        set_error("internal: grid too large for 32-bit sort keys");
+        return CS_ERR_CUDA;
+    }
 
     // ---- keys, stable sort, key starts
     uint32_t *keys[2] = {(uint32_t *)tmp_kv.p, (uint32_t *)tmp_kv.p + nn};
@@ -325,15 +363,15 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
                          (uint32_t *)tmp_scan.p, s);
     }
 
-    // owned memory: records, key starts, chunk records
+    // owned memory: chunk blocks, key starts, per-Gaussian largest scale and input row
     const int64_t kmax = std::max<int64_t>(kept_est, 1);
     const int nchunks = (int)((kept_est + kChunk - 1) / kChunk);
-    size_t bytes_rec = (size_t)48 * kmax;
+    size_t bytes_blocks = sizeof(ChunkBlock) * (size_t)std::max(nchunks, 1);
     size_t bytes_keys = (size_t)4 * (nkeys + 1);
-    size_t bytes_chunks = (size_t)32 * std::max(nchunks, 1);
-    size_t off_keys = (bytes_rec + 255) & ~(size_t)255;
-    size_t off_chunks = (off_keys + bytes_keys + 255) & ~(size_t)255;
-    size_t total = off_chunks + bytes_chunks;
+    size_t off_keys = (bytes_blocks + 255) & ~(size_t)255;
+    size_t off_smax = (off_keys + bytes_keys + 255) & ~(size_t)255;
+    size_t off_index = (off_smax + 4 * (size_t)kmax + 255) & ~(size_t)255;
+    size_t total = off_index + 4 * (size_t)kmax;
     void *blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, total);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation
@@ -342,14 +380,17 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     sc->blocks[sc->nblocks++] = blk;
     sc->device_bytes = (int64_t)total;
     char *base = (char *)blk;
-    float4 *spos = (float4 *)base, *scovA = spos + kmax, *scovB = scovA + kmax;
+    ChunkBlock *blocks = (ChunkBlock *)base;
     uint32_t *kstart = (uint32_t *)(base + off_keys);
-    float4 *clo = (float4 *)(base + off_chunks), *chi = clo + std::max(nchunks, 1);
+    float *smax = (float *)(base + off_smax);
+    int32_t *index = (int32_t *)(base + off_index);
 
     uint32_t *cnt = (uint32_t *)tmp_hist.p;  // reuse: nkeys + 1 counters
     CS_CUDA(cudaMemsetAsync(cnt, 0, 4 * ((size_t)nkeys + 1), s));
-    if (n > 0) k_count_keys<<<blocks_for(n), kThreads, 0, s>>>(keys[res], n, cnt);
+    if (n > 0) {
+        k_count_keys<<<blocks_for(n), kThreads, 0, s>>>(keys[res], n, cnt);
         count_launches(1);
+    }
     scan_exclusive(cnt, kstart, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
     uint32_t bounds[2] = {0, 0};
     CS_CUDA(cudaMemcpyAsync(&bounds[0], kstart + g.ncells, 4, cudaMemcpyDeviceToHost, s));
@@ -362,14 +403,11 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
         set_error("internal: kept count mismatch in scene build");
         return CS_ERR_CUDA;
     }
-    if (n_kept > 0)
-        k_gather<<<blocks_for(n_kept), kThreads, 0, s>>>(vals[res], n_kept, upos, ucovA, ucovB,
-                                                         spos, scovA, scovB);
+    if (nchunks > 0) {
+        k_blocks<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            vals[res], (int)n_kept, nchunks, upos, ucovA, ucovB, blocks, smax, index);
         count_launches(1);
-    if (nchunks > 0)
-        k_chunks<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            spos, (int)n_kept, nchunks, clo, chi);
-        count_launches(1);
+    }
     CS_CUDA(cudaGetLastError());
     CS_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
 
@@ -377,12 +415,10 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     sc->n_grid = n_grid;
     sc->n_large = n_kept - n_grid;
     SceneDev &dv = sc->dev;
-    dv.pos = spos;
-    dv.covA = scovA;
-    dv.covB = scovB;
+    dv.blocks = blocks;
     dv.cell_start = kstart;
-    dv.chunk_lo = clo;
-    dv.chunk_hi = chi;
+    dv.smax = smax;
+    dv.index = index;
     dv.n_kept = (int)n_kept;
     dv.n_grid = (int)n_grid;
     dv.nchunks = nchunks;
@@ -402,6 +438,35 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     for (int k = 0; k < 3; ++k) amax = std::max({amax, fabsf(lo[k]), fabsf(hi[k])});
     dv.pad_abs = 4e-6f * std::max(amax, emax) + 1e-30f;
     return CS_OK;
+}
+
+namespace {
+// Unpack the chunk blocks into row-major arrays (cs_scene_export).
+__global__ void k_export(const ChunkBlock *__restrict__ blocks, const float *__restrict__ smax,
+                         const int32_t *__restrict__ index, int n, float *__restrict__ pos,
+                         float *__restrict__ cov, int32_t *__restrict__ oidx) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const ChunkBlock &b = blocks[p / kChunk];
+    int l = p % kChunk;
+    if (pos) {
+        pos[4 * p + 0] = b.x[l]; pos[4 * p + 1] = b.y[l]; pos[4 * p + 2] = b.z[l];
+        pos[4 * p + 3] = smax[p];
+    }
+    if (cov) {
+        float *c = cov + 8 * (size_t)p;
+        c[0] = b.sxx[l]; c[1] = b.syy[l]; c[2] = b.szz[l];
+        c[3] = b.sxy2[l]; c[4] = b.sxz2[l]; c[5] = b.syz2[l];
+        c[6] = 0.f; c[7] = 0.f;
+    }
+    if (oidx) oidx[p] = index[p];
+}
+}  // namespace
+
+void launch_export(const SceneDev &sc, float *pos, float *cov, int32_t *index, cudaStream_t s) {
+    k_export<<<(sc.n_kept + 255) / 256, 256, 0, s>>>(sc.blocks, sc.smax, sc.index, sc.n_kept, pos, cov,
+                                                     index);
+    count_launches(1);
 }
 
 }  // namespace cs

@@ -16,6 +16,7 @@ namespace cs {
 // ---------------------------------------------------------------- constants
 constexpr int kChunk = 32;             // Gaussians per chunk record (warp-level cull unit)
 constexpr int kMortonBits = 8;         // bits per axis of the query sort key
+constexpr int kFineBits = 3;           // bits per axis of the order inside a grid cell
 constexpr int kCoarseDim = 16;         // coarse grid per axis for ordering the large tier
 constexpr int kSigmaBins = 512;        // log2 histogram of the largest scale
 constexpr float kSigmaLog2Lo = -32.f;  // histogram covers 2^-32 .. 2^32 in 1/8 octaves
@@ -32,18 +33,31 @@ constexpr unsigned kErrTimeout = 2u;
 constexpr long long kWaitPolls = 1ll << 27;
 
 // ------------------------------------------------------------- scene layout
-// Repacked Gaussian (48 B, three float4 arrays, sorted by grid key):
-//   pos  = (mu_x, mu_y, mu_z, max scale)
-//   covA = (Sxx, Syy, Szz, 2 Sxy)
-//   covB = (2 Sxz, 2 Syz, 0, bit pattern of the input row)
-// The off-diagonals are stored doubled so that d^T Sigma d needs 9 FP32 ops.
+// Repacked Gaussians are stored in chunk blocks of kChunk = 32 consecutive
+// (grid-sorted) Gaussians, one 1184-byte block each, so that a run of chunks
+// is one contiguous 1-D bulk copy and lane l of a warp reads Gaussian l of a
+// chunk with conflict-free 4-byte shared-memory loads:
+//   lo  = (min mu over the chunk, max scale over the chunk)
+//   hi  = (max mu over the chunk, 0)
+//   x, y, z          the means
+//   sxx, syy, szz    the covariance diagonal (Eq. 2)
+//   sxy2, sxz2, syz2 the off-diagonals, doubled so d^T Sigma d takes 9 FP32 ops
+// Slots past the last Gaussian hold x = NaN (never a neighbour).
+struct __align__(16) ChunkBlock {
+    float4 lo;
+    float4 hi;
+    float x[kChunk], y[kChunk], z[kChunk];
+    float sxx[kChunk], syy[kChunk], szz[kChunk];
+    float sxy2[kChunk], sxz2[kChunk], syz2[kChunk];
+};
+static_assert(sizeof(ChunkBlock) == 1184, "chunk block layout");
+static_assert(sizeof(ChunkBlock) % 16 == 0, "bulk copies move whole 16-byte units");
+
 struct SceneDev {
-    const float4 *pos = nullptr;
-    const float4 *covA = nullptr;
-    const float4 *covB = nullptr;
+    const ChunkBlock *blocks = nullptr;    // [nchunks]
     const uint32_t *cell_start = nullptr;  // [ncells + 1]: first sorted index of each cell
-    const float4 *chunk_lo = nullptr;      // [nchunks]: (min mu, max scale over the chunk)
-    const float4 *chunk_hi = nullptr;      // [nchunks]: (max mu, 0)
+    const float *smax = nullptr;           // [n_kept] largest scale per Gaussian (export only)
+    const int32_t *index = nullptr;        // [n_kept] input row per sorted Gaussian (export only)
     int n_kept = 0;
     int n_grid = 0;       // [0, n_grid) grid tier, [n_grid, n_kept) large tier
     int nchunks = 0;

@@ -55,35 +55,47 @@ struct EvalArgs {
     long long wait_polls;
 };
 
+// Kernel shape: NCW consumer warps, each owning QW primitives of the tile,
+// plus one producer warp.  Stages hold kCHB chunk blocks.
+constexpr int kNCW = 8;
 constexpr int kNS = 4;      // pipeline stages
-constexpr int kCH = 128;    // Gaussians per stage
-constexpr int kMaxP = 32;   // pieces (contiguous spans) per stage
+constexpr int kCHB = 8;     // chunk blocks per stage (256 Gaussians)
 
-struct StageMeta {
-    int count;
-    int npieces;
-    int pad[2];
-    int4 piece[kMaxP];  // (offset in stage, first sorted index, count, 0)
+struct SlotMeta {
+    int chunk;  // global chunk id
+    int lo;     // first valid lane of the chunk in this slot
+    int hi;     // one past the last valid lane
+    int pad;
 };
 
+// Per-primitive data in shared memory, 4 float4 (QREC) per primitive:
+//   sphere:    (c, 1/r^2) (2n, alpha, beta, live) - -
+//   ellipsoid: (c, 2n) (Axx, Ayy, Azz, Axy) (Axz, Ayz, alpha, beta) (live, - - -)
+constexpr int kQRec = 4;
+
+template <int QW>
 struct __align__(16) EvalSmem {
-    float4 pos[kNS][kCH];
-    float4 covA[kNS][kCH];
-    float4 covB[kNS][kCH];
-    StageMeta meta[kNS];
+    ChunkBlock blk[kNS][kCHB];
+    SlotMeta meta[kNS][kCHB];
+    int count[kNS];
+    int abort;  // an earlier launch on this stream timed out: skip the work
+    int pad[3];
     uint64_t full[kNS];
     uint64_t empty[kNS];
-    int abort;  // an earlier launch on this stream timed out: skip the work
+    float4 q[kNCW * QW][kQRec];
 };
 
 template <int PRIM> struct PrimTraits;
 template <> struct PrimTraits<0> { static constexpr int RECS = 1; };  // sphere: (c, r)
 template <> struct PrimTraits<1> { static constexpr int RECS = 3; };  // ellipsoid
 
-// Cull parameters of one prepared primitive: every pair farther than
-// alpha*s + sqrt(alpha^2 s^2 + beta) (s = the Gaussian's largest scale) has
-// st2 > S_reach.  Sphere: alpha = n, beta = S r^2.  Ellipsoid (semi-axes
-// a_max >= ... >= a_min): alpha = n a_max^2/a_min^2, beta = S a_max^2.
+// Cull parameters of one prepared primitive: every pair whose centre distance
+// exceeds alpha*s + sqrt(alpha^2 s^2 + beta) (s = the Gaussian's largest
+// scale) has st2 > S_reach.  With d the centre offset, s^2 >= |d|^2/a_max^2
+// and sqrt(sigma^2) <= 2 s |d| / a_min^2, so st2 <= S requires
+// |d|^2 - 2 n s |d| a_max^2/a_min^2 - S a_max^2 <= 0:
+//   sphere:    alpha = n,                 beta = S r^2
+//   ellipsoid: alpha = n a_max^2/a_min^2, beta = S a_max^2.
 template <int PRIM>
 __device__ __forceinline__ void prim_reach(const float4 *rec, float ns, float S, float &alpha,
                                            float &beta) {
@@ -131,13 +143,14 @@ __device__ __forceinline__ int cell_of(float x, float lo, float inv_h, int dim) 
 }
 
 // ------------------------------------------------------------- producer
+template <int QW>
 struct Producer {
-    EvalSmem *sm;
+    EvalSmem<QW> *sm;
     const SceneDev *sc;
     long long polls;
+    float lx, ly, lz, hx, hy, hz, al, be;  // tile box and reach parameters
     int k = 0;       // stage sequence number
-    int fill = 0;    // Gaussians in the open stage
-    int np = 0;      // pieces in the open stage
+    int nslot = 0;   // chunk slots filled in the open stage
     bool failed = false;
     int lane;
 
@@ -149,48 +162,69 @@ struct Producer {
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) failed = true;
         }
-        fill = 0;
-        np = 0;
+        nslot = 0;
     }
     __device__ void close_stage() {
         int s = k % kNS;
+        __syncwarp();  // slot metadata written by other lanes before the release
         if (lane == 0) {
-            sm->meta[s].count = fill;
-            sm->meta[s].npieces = np;
+            sm->count[s] = nslot;
             mbar_arrive(&sm->full[s]);
         }
         __syncwarp();
         ++k;
         open_stage();
     }
-    // Append sorted Gaussians [start, start + cnt) to the staged stream.
-    __device__ void append(int start, int cnt) {
-        while (cnt > 0 && !failed) {
-            int s = k % kNS;
-            int take = min(cnt, kCH - fill);
-            if (lane == 0) {
-                sm->meta[s].piece[np] = make_int4(fill, start, take, 0);
-                unsigned bytes = (unsigned)take * 16u;
-                mbar_expect_tx(&sm->full[s], 3u * bytes);
-                bulk_g2s(&sm->pos[s][fill], sc->pos + start, bytes, &sm->full[s]);
-                bulk_g2s(&sm->covA[s][fill], sc->covA + start, bytes, &sm->full[s]);
-                bulk_g2s(&sm->covB[s][fill], sc->covB + start, bytes, &sm->full[s]);
+    // Stage chunks [c, c + len) (contiguous blocks) covering sorted Gaussians
+    // [s, e) of the stream.
+    __device__ void emit_run(int c, int len, int s, int e) {
+        while (len > 0 && !failed) {
+            const int st = k % kNS;
+            const int take = min(len, kCHB - nslot);
+            if (lane < take) {
+                int cc = c + lane;
+                sm->meta[st][nslot + lane] = SlotMeta{cc, max(s - cc * kChunk, 0),
+                                                      min(e - cc * kChunk, kChunk), 0};
             }
-            fill += take;
-            start += take;
-            cnt -= take;
-            ++np;
-            if (fill == kCH || np == kMaxP) close_stage();
+            if (lane == 0) {
+                unsigned bytes = (unsigned)take * (unsigned)sizeof(ChunkBlock);
+                mbar_expect_tx(&sm->full[st], bytes);
+                bulk_g2s(&sm->blk[st][nslot], sc->blocks + c, bytes, &sm->full[st]);
+            }
+            nslot += take;
+            c += take;
+            len -= take;
+            if (nslot == kCHB) close_stage();
+        }
+    }
+    // The chunks overlapping [s, e) that pass the tile-level reach test.
+    __device__ void append_span(int s, int e) {
+        const int c0 = s / kChunk, c1 = (e - 1) / kChunk;
+        for (int cb = c0; cb <= c1 && !failed; cb += 32) {
+            const int c = cb + lane;
+            bool pass = false;
+            if (c <= c1) {
+                const float4 blo = __ldg(&sc->blocks[c].lo), bhi = __ldg(&sc->blocks[c].hi);
+                const float R = reach(al, be, blo.w, sc->pad_abs);
+                pass = box_gap2(lx, ly, lz, hx, hy, hz, blo, bhi) <= R * R;
+            }
+            unsigned m = __ballot_sync(0xffffffffu, pass);
+            while (m && !failed) {
+                const int first = __ffs(m) - 1;
+                const unsigned rest = ~(m >> first);
+                const int len = rest ? __ffs(rest) - 1 : 32 - first;
+                emit_run(cb + first, len, s, e);
+                m = (first + len >= 32) ? 0u : (m & ~((1u << (first + len)) - 1u));
+            }
         }
     }
     __device__ void finish() {
         if (failed) return;
-        if (fill > 0) close_stage();
+        if (nslot > 0) close_stage();
         if (failed) return;
         int s = k % kNS;
         if (lane == 0) {
-            sm->meta[s].count = 0;  // terminator
-            sm->meta[s].npieces = 0;
+            sm->count[s] = 0;  // terminator
             mbar_arrive(&sm->full[s]);
         }
         __syncwarp();
@@ -198,11 +232,11 @@ struct Producer {
     // After a failed wait: close the open stage so its copies can complete,
     // then wait (bounded) for every stage's latest phase.
     __device__ void drain() {
+        __syncwarp();
         if (lane == 0) {
             int s = k % kNS;
-            if (fill > 0) {
-                sm->meta[s].count = fill;
-                sm->meta[s].npieces = np;
+            if (nslot > 0) {
+                sm->count[s] = nslot;
                 mbar_arrive(&sm->full[s]);
                 ++k;
             }
@@ -213,13 +247,12 @@ struct Producer {
     }
 };
 
-template <int PRIM, int QB, int NCW>
-__device__ void producer_warp(const EvalArgs &a, EvalSmem *sm, int tile) {
+template <int PRIM, int QW>
+__device__ void producer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
-    constexpr int TQ = NCW * 32 * QB;
+    constexpr int TQ = kNCW * QW;
     const int lane = threadIdx.x & 31;
     const SceneDev &sc = a.sc;
-    // tile bounding box and reach parameters over its valid primitives
     float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY,
           hz = -INFINITY, al = 0.f, be = 0.f;
     const int q0 = tile * TQ;
@@ -247,7 +280,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem *sm, int tile) {
         al = fmaxf(al, __shfl_xor_sync(0xffffffffu, al, o));
         be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
     }
-    Producer pr{sm, &sc, a.wait_polls};
+    Producer<QW> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
     pr.lane = lane;
     const bool any = lx <= hx;  // at least one valid primitive
     if (any && sc.n_grid > 0) {
@@ -288,39 +321,16 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem *sm, int tile) {
                 }
             }
             unsigned m = __ballot_sync(0xffffffffu, cnt > 0);
-            while (m) {
+            while (m && !pr.failed) {
                 int src = __ffs(m) - 1;
                 m &= m - 1;
                 int s0 = __shfl_sync(0xffffffffu, start, src);
                 int c0 = __shfl_sync(0xffffffffu, cnt, src);
-                pr.append(s0, c0);
-                if (pr.failed) break;
+                pr.append_span(s0, s0 + c0);
             }
         }
     }
-    if (any && sc.n_kept > sc.n_grid && !pr.failed) {
-        // ---- large tier: chunk records tested one by one against the tile box
-        const int c_begin = sc.n_grid / kChunk;
-        for (int cb = c_begin; cb < sc.nchunks && !pr.failed; cb += 32) {
-            int c = cb + lane;
-            bool pass = false;
-            if (c < sc.nchunks) {
-                float4 clo = sc.chunk_lo[c], chi = sc.chunk_hi[c];
-                float Rc = reach(al, be, clo.w, sc.pad_abs);
-                pass = box_gap2(lx, ly, lz, hx, hy, hz, clo, chi) <= Rc * Rc;
-            }
-            unsigned m = __ballot_sync(0xffffffffu, pass);
-            while (m) {
-                int src = __ffs(m) - 1;
-                m &= m - 1;
-                int cc = cb + src;
-                int s0 = max(cc * kChunk, sc.n_grid);
-                int e0 = min(cc * kChunk + kChunk, sc.n_kept);
-                pr.append(s0, e0 - s0);
-                if (pr.failed) break;
-            }
-        }
-    }
+    if (any && sc.n_kept > sc.n_grid && !pr.failed) pr.append_span(sc.n_grid, sc.n_kept);  // large tier
     pr.finish();
     if (pr.failed) {
         if (lane == 0) atomicOr(a.err, kErrTimeout);
@@ -329,237 +339,190 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem *sm, int tile) {
 }
 
 // ------------------------------------------------------------- consumers
-template <int PRIM, int QB, bool SOFTMIN, bool GRAD>
-struct Lane;
-
-// Per-lane state for QB spheres.
-template <int QB, bool SOFTMIN, bool GRAD>
-struct Lane<0, QB, SOFTMIN, GRAD> {
-    float cx[QB], cy[QB], cz[QB], ir2[QB], ns2[QB];
-    float sum[QB], cnt[QB], cin[QB], mn[QB];
-    float sm_m[QB], sm_acc[QB];
-    float gx[QB], gy[QB], gz[QB];
-
-    __device__ void init(const float4 *rec, const float *ns, int i) {
-        float4 r = rec[0];
-        cx[i] = r.x; cy[i] = r.y; cz[i] = r.z;
-        ir2[i] = 1.f / (r.w * r.w);
-        ns2[i] = 2.f * ns[0];
-    }
-    __device__ void clear(int i) {
-        sum[i] = 0.f; cnt[i] = 0.f; cin[i] = 0.f; mn[i] = INFINITY;
-        sm_m[i] = INFINITY; sm_acc[i] = 0.f;
-        gx[i] = gy[i] = gz[i] = 0.f;
-    }
-    // a slot without a valid primitive: finite values, results never stored
-    __device__ void park(int i) { cx[i] = cy[i] = cz[i] = 0.f; ir2[i] = 0.f; ns2[i] = 0.f; }
-    // Eq. 5, 7, 8, 11 for one Gaussian against the lane's QB spheres.  In the
-    // difference form d = mu - c (no cancellation in absolute coordinates):
-    //   s^2 = |d|^2 / r^2,  sqrt(sigma^2) = 2 sqrt(d^T Sigma d) / r^2,
-    //   st^2 = max(0, |d|^2 - 2 n sqrt(d^T Sigma d)) / r^2.
-    __device__ __forceinline__ void update(const float4 P, const float4 A, const float4 B,
-                                           const QueryConsts &k) {
-#pragma unroll
-        for (int i = 0; i < QB; ++i) {
-            float dx = P.x - cx[i], dy = P.y - cy[i], dz = P.z - cz[i];
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            float q, vx = 0.f, vy = 0.f, vz = 0.f;
-            if (!GRAD) {
-                float t1 = fmaf(B.x, dz, fmaf(A.w, dy, A.x * dx));  // Sxx dx + 2Sxy dy + 2Sxz dz
-                float t2 = fmaf(B.y, dz, A.y * dy);                 // Syy dy + 2Syz dz
-                q = fmaf(dx, t1, fmaf(dy, t2, dz * (A.z * dz)));
-            } else {
-                // Sigma d with the stored doubled off-diagonals halved
-                float hxy = 0.5f * A.w, hxz = 0.5f * B.x, hyz = 0.5f * B.y;
-                vx = fmaf(hxz, dz, fmaf(hxy, dy, A.x * dx));
-                vy = fmaf(hyz, dz, fmaf(A.y, dy, hxy * dx));
-                vz = fmaf(A.z, dz, fmaf(hyz, dy, hxz * dx));
-                q = fmaf(dx, vx, fmaf(dy, vy, dz * vz));
-            }
-            q = fmaxf(q, 0.f);
-            float sq = sqrt_approx(q);
-            float raw = fmaf(-ns2[i], sq, r2);
-            float st2 = fmaxf(raw, 0.f) * ir2[i];
-            float dc = ex2_approx(fminf(fmaf(st2, -k.G, k.Gsmin), 0.f));
-            bool nb = st2 <= k.S_cut;
-            if (!GRAD) {
-                if (nb) { sum[i] += dc; cnt[i] += 1.f; }
-                if (st2 < k.T_in) cin[i] += 1.f;
-                mn[i] = fminf(mn[i], st2);
-                if (SOFTMIN && nb) {
-                    float nm = fminf(sm_m[i], st2);
-                    sm_acc[i] = fmaf(sm_acc[i], ex2_approx((nm - sm_m[i]) * k.K),
-                                     ex2_approx((nm - st2) * k.K));
-                    sm_m[i] = nm;
-                }
-            } else {
-                // d st2 / d c = (-2 d + 2 n Sigma d / sqrt(d^T Sigma d)) / r^2 where raw > 0
-                float rs = sq > 0.f ? ns2[i] / sq : 0.f;
-                float live = raw > 0.f ? ir2[i] : 0.f;
-                float ex = (fmaf(rs, vx, -2.f * dx)) * live;
-                float ey = (fmaf(rs, vy, -2.f * dy)) * live;
-                float ez = (fmaf(rs, vz, -2.f * dz)) * live;
-                if (nb) cnt[i] += 1.f;
-                if (k.mode <= CS_METRIC_SUM_COST) {
-                    // Eq. 11 is flat below s_min
-                    float w = (nb && st2 > k.s_min) ? dc : 0.f;
-                    gx[i] = fmaf(w, ex, gx[i]); gy[i] = fmaf(w, ey, gy[i]); gz[i] = fmaf(w, ez, gz[i]);
-                } else if (k.mode == CS_METRIC_MIN_S2) {
-                    if (nb && st2 < mn[i]) { mn[i] = st2; gx[i] = ex; gy[i] = ey; gz[i] = ez; }
-                } else if (nb) {
-                    float nm = fminf(sm_m[i], st2);
-                    float f = ex2_approx((nm - sm_m[i]) * k.K);
-                    float e = ex2_approx((nm - st2) * k.K);
-                    sm_acc[i] = fmaf(sm_acc[i], f, e);
-                    gx[i] = fmaf(gx[i], f, e * ex); gy[i] = fmaf(gy[i], f, e * ey); gz[i] = fmaf(gz[i], f, e * ez);
-                    sm_m[i] = nm;
-                }
-            }
-        }
-    }
+// MODE: 0 = cost (mean/sum), 1 = min, 2 = softmin.
+// A consumer warp owns QW primitives.  Lane l takes Gaussian l of every
+// staged chunk (global sorted index 32c + l), so each lane's partial
+// reductions run over a fixed subsequence of the scene in increasing order,
+// whatever the tile: results do not depend on which rows share the launch.
+template <int PRIM, int QW, int MODE, bool GRAD>
+struct Acc {
+    float sumb[(MODE == 0 && !GRAD) ? QW : 1];  // cost partial over the current chunk group
+    float sum[(MODE == 0 && !GRAD) ? QW : 1];
+    float mn[(MODE == 1) ? QW : 1];
+    float sm_m[(MODE == 2) ? QW : 1];
+    float sm_acc[(MODE == 2) ? QW : 1];
+    float gx[GRAD ? QW : 1], gy[GRAD ? QW : 1], gz[GRAD ? QW : 1];
+    int cnt[QW];
+    int cin[GRAD ? 1 : QW];
 };
 
-// Per-lane state for QB ellipsoids: centre, A (6 coefficients), 2 n.
-template <int QB, bool SOFTMIN, bool GRAD>
-struct Lane<1, QB, SOFTMIN, GRAD> {
-    float cx[QB], cy[QB], cz[QB], axx[QB], ayy[QB], azz[QB], axy[QB], axz[QB], ayz[QB], ns2[QB];
-    float sum[QB], cnt[QB], cin[QB], mn[QB];
-    float sm_m[QB], sm_acc[QB];
-    float gx[QB], gy[QB], gz[QB];
-
-    __device__ void init(const float4 *rec, const float *ns, int i) {
-        float4 r0 = rec[0], r1 = rec[1], r2 = rec[2];
-        cx[i] = r0.x; cy[i] = r0.y; cz[i] = r0.z;
-        axx[i] = r1.x; ayy[i] = r1.y; azz[i] = r1.z; axy[i] = r1.w;
-        axz[i] = r2.x; ayz[i] = r2.y;
-        ns2[i] = 2.f * ns[0];
-    }
-    __device__ void clear(int i) {
-        sum[i] = 0.f; cnt[i] = 0.f; cin[i] = 0.f; mn[i] = INFINITY;
-        sm_m[i] = INFINITY; sm_acc[i] = 0.f;
-        gx[i] = gy[i] = gz[i] = 0.f;
-    }
-    __device__ void park(int i) {
-        cx[i] = cy[i] = cz[i] = 0.f;
-        axx[i] = ayy[i] = azz[i] = axy[i] = axz[i] = ayz[i] = 0.f;
-        ns2[i] = 0.f;
-    }
-    // Eq. 5-8 for an ellipsoid: w = A d, s^2 = d^T w, sqrt(sigma^2) = 2 sqrt(w^T Sigma w).
-    __device__ __forceinline__ void update(const float4 P, const float4 A, const float4 B,
-                                           const QueryConsts &k) {
-#pragma unroll
-        for (int i = 0; i < QB; ++i) {
-            float dx = P.x - cx[i], dy = P.y - cy[i], dz = P.z - cz[i];
-            float wx = fmaf(axz[i], dz, fmaf(axy[i], dy, axx[i] * dx));
-            float wy = fmaf(ayz[i], dz, fmaf(ayy[i], dy, axy[i] * dx));
-            float wz = fmaf(azz[i], dz, fmaf(ayz[i], dy, axz[i] * dx));
-            float s2 = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
-            float u, vx = 0.f, vy = 0.f, vz = 0.f;
-            if (!GRAD) {
-                float t1 = fmaf(B.x, wz, fmaf(A.w, wy, A.x * wx));
-                float t2 = fmaf(B.y, wz, A.y * wy);
-                u = fmaf(wx, t1, fmaf(wy, t2, wz * (A.z * wz)));
-            } else {
-                float hxy = 0.5f * A.w, hxz = 0.5f * B.x, hyz = 0.5f * B.y;
-                vx = fmaf(hxz, wz, fmaf(hxy, wy, A.x * wx));   // Sigma w
-                vy = fmaf(hyz, wz, fmaf(A.y, wy, hxy * wx));
-                vz = fmaf(A.z, wz, fmaf(hyz, wy, hxz * wx));
-                u = fmaf(wx, vx, fmaf(wy, vy, wz * vz));
-            }
-            u = fmaxf(u, 0.f);
-            float sq = sqrt_approx(u);
-            float raw = fmaf(-ns2[i], sq, s2);
-            float st2 = fmaxf(raw, 0.f);
-            float dc = ex2_approx(fminf(fmaf(st2, -k.G, k.Gsmin), 0.f));
-            bool nb = st2 <= k.S_cut;
-            if (!GRAD) {
-                if (nb) { sum[i] += dc; cnt[i] += 1.f; }
-                if (st2 < k.T_in) cin[i] += 1.f;
-                mn[i] = fminf(mn[i], st2);
-                if (SOFTMIN && nb) {
-                    float nm = fminf(sm_m[i], st2);
-                    sm_acc[i] = fmaf(sm_acc[i], ex2_approx((nm - sm_m[i]) * k.K),
-                                     ex2_approx((nm - st2) * k.K));
-                    sm_m[i] = nm;
-                }
-            } else {
-                // d st2 / d c = -2 w + 2 n A Sigma w / sqrt(w^T Sigma w) where raw > 0
-                float rs = sq > 0.f ? ns2[i] / sq : 0.f;
-                float live = raw > 0.f ? 1.f : 0.f;
-                float px = fmaf(axz[i], vz, fmaf(axy[i], vy, axx[i] * vx));  // A Sigma w
-                float py = fmaf(ayz[i], vz, fmaf(ayy[i], vy, axy[i] * vx));
-                float pz = fmaf(azz[i], vz, fmaf(ayz[i], vy, axz[i] * vx));
-                float ex = fmaf(rs, px, -2.f * wx) * live;
-                float ey = fmaf(rs, py, -2.f * wy) * live;
-                float ez = fmaf(rs, pz, -2.f * wz) * live;
-                if (nb) cnt[i] += 1.f;
-                if (k.mode <= CS_METRIC_SUM_COST) {
-                    float w = (nb && st2 > k.s_min) ? dc : 0.f;
-                    gx[i] = fmaf(w, ex, gx[i]); gy[i] = fmaf(w, ey, gy[i]); gz[i] = fmaf(w, ez, gz[i]);
-                } else if (k.mode == CS_METRIC_MIN_S2) {
-                    if (nb && st2 < mn[i]) { mn[i] = st2; gx[i] = ex; gy[i] = ey; gz[i] = ez; }
-                } else if (nb) {
-                    float nm = fminf(sm_m[i], st2);
-                    float f = ex2_approx((nm - sm_m[i]) * k.K);
-                    float e = ex2_approx((nm - st2) * k.K);
-                    sm_acc[i] = fmaf(sm_acc[i], f, e);
-                    gx[i] = fmaf(gx[i], f, e * ex); gy[i] = fmaf(gy[i], f, e * ey); gz[i] = fmaf(gz[i], f, e * ez);
-                    sm_m[i] = nm;
-                }
-            }
-        }
-    }
+// Lane-local Gaussian of the current chunk slot.
+struct LaneG {
+    float x, y, z, sxx, syy, szz, sxy2, sxz2, syz2;
 };
 
-template <int PRIM, int QB, int NCW, bool SOFTMIN, bool GRAD>
-__device__ void consumer_warp(const EvalArgs &a, EvalSmem *sm, int tile, int warp, bool abort) {
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int PRIM, int QW, int MODE, bool GRAD>
+__device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j, const LaneG &g,
+                                            const float4 *qd, const QueryConsts &k) {
+    const float dx = g.x - qd[0].x, dy = g.y - qd[0].y, dz = g.z - qd[0].z;
+    float s2, u, vx = 0.f, vy = 0.f, vz = 0.f;   // s2: Eq. 5 numerator (sphere) or Eq. 5
+    float ns2, ir2;
+    float wx = dx, wy = dy, wz = dz;             // w = A d (sphere: d, scaled by 1/r^2 later)
+    if (PRIM == 0) {
+        ns2 = qd[1].x;
+        ir2 = qd[0].w;
+        s2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    } else {
+        ns2 = qd[0].w;
+        ir2 = 1.f;
+        const float axx = qd[1].x, ayy = qd[1].y, azz = qd[1].z, axy = qd[1].w, axz = qd[2].x, ayz = qd[2].y;
+        wx = fmaf(axz, dz, fmaf(axy, dy, axx * dx));
+        wy = fmaf(ayz, dz, fmaf(ayy, dy, axy * dx));
+        wz = fmaf(azz, dz, fmaf(ayz, dy, axz * dx));
+        s2 = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+    }
+    if (!GRAD) {
+        // w^T Sigma w with the doubled off-diagonals: 9 FP32 ops
+        const float t1 = fmaf(g.sxz2, wz, fmaf(g.sxy2, wy, g.sxx * wx));
+        const float t2 = fmaf(g.syz2, wz, g.syy * wy);
+        u = fmaf(wx, t1, fmaf(wy, t2, wz * (g.szz * wz)));
+    } else {
+        const float hxy = 0.5f * g.sxy2, hxz = 0.5f * g.sxz2, hyz = 0.5f * g.syz2;
+        vx = fmaf(hxz, wz, fmaf(hxy, wy, g.sxx * wx));  // Sigma w
+        vy = fmaf(hyz, wz, fmaf(g.syy, wy, hxy * wx));
+        vz = fmaf(g.szz, wz, fmaf(hyz, wy, hxz * wx));
+        u = fmaf(wx, vx, fmaf(wy, vy, wz * vz));
+    }
+    u = fmaxf(u, 0.f);
+    float sq, rsq = 0.f;
+    if (!GRAD) {
+        sq = sqrt_approx(u);
+    } else {
+        rsq = u > 0.f ? rsqrtf(u) : 0.f;
+        sq = u * rsq;
+    }
+    // Eq. 8: st2 = max(0, s^2 - n sqrt(sigma^2)); for a sphere s^2 and
+    // sqrt(sigma^2) = 2 sqrt(d^T Sigma d)/r^2 share the factor 1/r^2.
+    const float raw = fmaf(-ns2, sq, s2);
+    const float st2 = fmaxf(raw, 0.f) * ir2;
+    // Eq. 11 without d_max (applied once per primitive): 2^min(-G (st2 - s_min), 0)
+    const float dc = ex2_approx(fminf(fmaf(st2, -k.G, k.Gsmin), 0.f));
+    const bool nb = st2 <= k.S_cut;
+    A.cnt[j] += nb ? 1 : 0;
+    if (!GRAD) {
+        A.cin[j] += (st2 < k.T_in) ? 1 : 0;
+        if (MODE == 0) A.sumb[j] += nb ? dc : 0.f;
+        if (MODE == 1) A.mn[j] = fminf(A.mn[j], st2);
+        if (MODE == 2) {
+            const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
+            const float f = ex2_approx((nm - A.sm_m[j]) * k.K);
+            const float e = nb ? ex2_approx((nm - st2) * k.K) : 0.f;
+            A.sm_acc[j] = fmaf(A.sm_acc[j], f, e);
+            A.sm_m[j] = nm;
+        }
+    } else {
+        // d st2 / d c = (-2 w + 2 n A Sigma w / sqrt(w^T Sigma w)) * ir2 where raw > 0
+        float px = vx, py = vy, pz = vz;
+        if (PRIM == 1) {
+            const float axx = qd[1].x, ayy = qd[1].y, azz = qd[1].z, axy = qd[1].w, axz = qd[2].x, ayz = qd[2].y;
+            px = fmaf(axz, vz, fmaf(axy, vy, axx * vx));
+            py = fmaf(ayz, vz, fmaf(ayy, vy, axy * vx));
+            pz = fmaf(azz, vz, fmaf(ayz, vy, axz * vx));
+        }
+        const float rs = ns2 * rsq;
+        const float live = raw > 0.f ? ir2 : 0.f;
+        const float ex = fmaf(rs, px, -2.f * wx) * live;
+        const float ey = fmaf(rs, py, -2.f * wy) * live;
+        const float ez = fmaf(rs, pz, -2.f * wz) * live;
+        if (MODE == 0) {
+            // Eq. 11 is flat (zero gradient) below s_min
+            const float w = (nb && st2 > k.s_min) ? dc : 0.f;
+            A.gx[j] = fmaf(w, ex, A.gx[j]);
+            A.gy[j] = fmaf(w, ey, A.gy[j]);
+            A.gz[j] = fmaf(w, ez, A.gz[j]);
+        } else if (MODE == 1) {
+            const bool take = nb && st2 < A.mn[j];
+            A.mn[j] = take ? st2 : A.mn[j];
+            A.gx[j] = take ? ex : A.gx[j];
+            A.gy[j] = take ? ey : A.gy[j];
+            A.gz[j] = take ? ez : A.gz[j];
+        } else {
+            const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
+            const float f = ex2_approx((nm - A.sm_m[j]) * k.K);
+            const float e = nb ? ex2_approx((nm - st2) * k.K) : 0.f;
+            A.sm_acc[j] = fmaf(A.sm_acc[j], f, e);
+            A.gx[j] = fmaf(A.gx[j], f, e * ex);
+            A.gy[j] = fmaf(A.gy[j], f, e * ey);
+            A.gz[j] = fmaf(A.gz[j], f, e * ez);
+            A.sm_m[j] = nm;
+        }
+    }
+}
+
+template <int PRIM, int QW, int MODE, bool GRAD>
+__device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int warp, bool abort) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
-    constexpr int TQ = NCW * 32 * QB;
+    constexpr int TQ = kNCW * QW;
     const int lane = threadIdx.x & 31;
     const QueryConsts &k = a.k;
-    Lane<PRIM, QB, SOFTMIN, GRAD> st;
-    int qi[QB];
-    bool valid[QB];
-    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
-    float al = 0.f, be = 0.f;
+    const SceneDev &sc = a.sc;
+    float4(*wq)[kQRec] = &sm->q[warp * QW];
+    // ---- this warp's primitives into shared memory
     int nvalid = 0;
-#pragma unroll
-    for (int i = 0; i < QB; ++i) {
-        int q = tile * TQ + warp * 32 * QB + i * 32 + lane;
-        qi[i] = q;
-        valid[i] = false;
-        st.clear(i);
-        st.park(i);
+    if (lane < QW) {
+        const int q = tile * TQ + warp * QW + lane;
+        float4 d0 = make_float4(0, 0, 0, 0), d1 = d0, d2 = d0, d3 = d0;
         if (q < a.Q) {
             const float4 *rec = a.qrec + (size_t)q * RECS;
-            float4 r0 = rec[0];
+            const float4 r0 = rec[0];
             if (rec_valid(r0)) {
-                valid[i] = true;
-                st.init(rec, a.qns + q, i);
+                const float ns = a.qns[q];
                 float alpha, beta;
-                prim_reach<PRIM>(rec, a.qns[q], k.S_reach, alpha, beta);
-                lx = fminf(lx, r0.x); ly = fminf(ly, r0.y); lz = fminf(lz, r0.z);
-                hx = fmaxf(hx, r0.x); hy = fmaxf(hy, r0.y); hz = fmaxf(hz, r0.z);
-                al = fmaxf(al, alpha); be = fmaxf(be, beta);
-                ++nvalid;
+                prim_reach<PRIM>(rec, ns, k.S_reach, alpha, beta);
+                if (PRIM == 0) {
+                    d0 = make_float4(r0.x, r0.y, r0.z, 1.f / (r0.w * r0.w));
+                    d1 = make_float4(2.f * ns, alpha, beta, 1.f);
+                } else {
+                    const float4 r1 = rec[1], r2 = rec[2];
+                    d0 = make_float4(r0.x, r0.y, r0.z, 2.f * ns);
+                    d1 = r1;
+                    d2 = make_float4(r2.x, r2.y, alpha, beta);
+                    d3 = make_float4(1.f, 0.f, 0.f, 0.f);
+                }
+                nvalid = 1;
             }
         }
+        wq[lane][0] = d0;
+        wq[lane][1] = d1;
+        wq[lane][2] = d2;
+        wq[lane][3] = d3;
     }
+    nvalid = __reduce_add_sync(0xffffffffu, nvalid);
+    __syncwarp();
+
+    Acc<PRIM, QW, MODE, GRAD> A;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-        al = fmaxf(al, __shfl_xor_sync(0xffffffffu, al, o));
-        be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
-        nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
+    for (int j = 0; j < QW; ++j) {
+        A.cnt[j] = 0;
+        if (!GRAD) A.cin[j] = 0;
+        if (MODE == 0 && !GRAD) { A.sumb[j] = 0.f; A.sum[j] = 0.f; }
+        if (MODE == 1) A.mn[j] = INFINITY;
+        if (MODE == 2) { A.sm_m[j] = k.S_cut; A.sm_acc[j] = 0.f; }
+        if (GRAD) { A.gx[j] = 0.f; A.gy[j] = 0.f; A.gz[j] = 0.f; }
     }
-    const bool warp_live = nvalid > 0;
-    const SceneDev &sc = a.sc;
-    long long evaluated = 0;
+    unsigned long long cand = 0;  // (primitive, Gaussian) pairs evaluated
+    int group = -1;               // chunk group of the cost partials
     bool ok = !abort;
     for (int kk = 0; ok; ++kk) {
         const int s = kk % kNS;
@@ -567,28 +530,47 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem *sm, int tile, int war
         if (lane == 0) got = wait_phase(&sm->full[s], (unsigned)((kk / kNS) & 1), a.wait_polls);
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) { ok = false; break; }
-        const int n = sm->meta[s].count;
-        if (n == 0) break;
-        if (warp_live) {
-            const int npc = sm->meta[s].npieces;
-            for (int p = 0; p < npc; ++p) {
-                const int4 pc = sm->meta[s].piece[p];
-                int g = pc.y;
-                const int gend = pc.y + pc.z;
-                while (g < gend) {
-                    const int c = g >> 5;
-                    const int ce = min(gend, (c + 1) << 5);
-                    const float4 clo = __ldg(sc.chunk_lo + c);
-                    const float4 chi = __ldg(sc.chunk_hi + c);
-                    const float Rc = reach(al, be, clo.w, sc.pad_abs);
-                    if (box_gap2(lx, ly, lz, hx, hy, hz, clo, chi) <= Rc * Rc) {
-                        const int o0 = pc.x + (g - pc.y), o1 = pc.x + (ce - pc.y);
-                        evaluated += o1 - o0;
-#pragma unroll 2
-                        for (int o = o0; o < o1; ++o)
-                            st.update(sm->pos[s][o], sm->covA[s][o], sm->covB[s][o], k);
+        const int nslots = sm->count[s];
+        if (nslots == 0) break;
+        if (nvalid > 0) {
+            for (int slot = 0; slot < nslots; ++slot) {
+                const SlotMeta mt = sm->meta[s][slot];
+                const ChunkBlock &B = sm->blk[s][slot];
+                if (MODE == 0 && !GRAD) {
+                    // fixed grouping of the cost partials (16 chunks) keeps
+                    // the summation order independent of the tile
+                    const int grp = mt.chunk >> 4;
+                    if (grp != group) {
+#pragma unroll
+                        for (int j = 0; j < QW; ++j) { A.sum[j] += A.sumb[j]; A.sumb[j] = 0.f; }
+                        group = grp;
                     }
-                    g = ce;
+                }
+                const bool lv = lane >= mt.lo && lane < mt.hi;
+                LaneG g;
+                g.x = lv ? B.x[lane] : 1e18f;
+                g.y = lv ? B.y[lane] : 1e18f;
+                g.z = lv ? B.z[lane] : 1e18f;
+                g.sxx = lv ? B.sxx[lane] : 0.f;
+                g.syy = lv ? B.syy[lane] : 0.f;
+                g.szz = lv ? B.szz[lane] : 0.f;
+                g.sxy2 = lv ? B.sxy2[lane] : 0.f;
+                g.sxz2 = lv ? B.sxz2[lane] : 0.f;
+                g.syz2 = lv ? B.syz2[lane] : 0.f;
+                const float4 blo = B.lo, bhi = B.hi;
+                const int nlanes = mt.hi - mt.lo;
+#pragma unroll
+                for (int j = 0; j < QW; ++j) {
+                    const float4 *qd = wq[j];
+                    const float4 q0 = qd[0];
+                    float alpha, beta, live;
+                    if (PRIM == 0) { const float4 q1 = qd[1]; alpha = q1.y; beta = q1.z; live = q1.w; }
+                    else { const float4 q2 = qd[2]; alpha = q2.z; beta = q2.w; live = qd[3].x; }
+                    if (live == 0.f) continue;  // warp-uniform
+                    const float R = reach(alpha, beta, blo.w, sc.pad_abs);
+                    if (box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) > R * R) continue;  // uniform
+                    cand += (unsigned long long)nlanes;
+                    pair_update<PRIM, QW, MODE, GRAD>(A, j, g, qd, k);
                 }
             }
         }
@@ -597,79 +579,85 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem *sm, int tile, int war
     }
     if (!ok && !abort && lane == 0) atomicOr(a.err, kErrTimeout);
 
-    // ---- outputs (input row order)
-    float nb_total = 0.f;
+    // ---- reductions across lanes (fixed trees) and outputs
+    unsigned long long nb_total = 0;
 #pragma unroll
-    for (int i = 0; i < QB; ++i) {
-        const int q = qi[i];
-        if (q >= a.Q) continue;
-        const uint32_t row = a.perm[q];
+    for (int j = 0; j < QW; ++j) {
+        const int q = tile * TQ + warp * QW + j;
+        const bool vq = wq[j][PRIM == 0 ? 1 : 3].w != 0.f || (PRIM == 1 && wq[j][3].x != 0.f);
+        const int cntj = __reduce_add_sync(0xffffffffu, (unsigned)A.cnt[j]);
         if (!GRAD) {
-            float metric;
-            uint8_t col = 0;
-            int cntv = 0;
-            if (!valid[i] || !ok) {
-                metric = __int_as_float(0x7fc00000);
+            const int cinj = __reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
+            float metric = 0.f;
+            if (MODE == 0) {
+                const float tot = warp_sum(A.sum[j] + A.sumb[j]);
+                metric = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? tot * k.d_max / (float)cntj : 0.f)
+                                                         : tot * k.d_max;
+            } else if (MODE == 1) {
+                const float m = warp_min(A.mn[j]);
+                metric = cntj > 0 ? m : INFINITY;
             } else {
-                const float c = st.cnt[i];
-                cntv = (int)c;
-                nb_total += c;
-                col = st.cin[i] > (float)k.k_thr ? 1 : 0;
-                switch (k.mode) {
-                    case CS_METRIC_MEAN_COST: metric = c > 0.f ? st.sum[i] * k.d_max / c : 0.f; break;
-                    case CS_METRIC_SUM_COST: metric = st.sum[i] * k.d_max; break;
-                    case CS_METRIC_MIN_S2: metric = c > 0.f ? st.mn[i] : INFINITY; break;
-                    default:
-                        metric = c > 0.f ? st.sm_m[i] - k.tau * 0.6931471805599453f * lg2_approx(st.sm_acc[i])
-                                         : INFINITY;
-                }
+                const float M = warp_min(A.sm_m[j]);
+                const float acc = warp_sum(A.sm_acc[j] * ex2_approx((M - A.sm_m[j]) * k.K));
+                metric = cntj > 0 ? M - k.tau * 0.6931471805599453f * lg2_approx(acc) : INFINITY;
             }
-            if (a.out_metric) a.out_metric[row] = metric;
-            if (a.out_collide) a.out_collide[row] = col;
-            if (a.out_count) a.out_count[row] = cntv;
+            if (lane == 0 && q < a.Q) {
+                const uint32_t row = a.perm[q];
+                const bool good = vq && ok;
+                if (a.out_metric) a.out_metric[row] = good ? metric : __int_as_float(0x7fc00000);
+                if (a.out_collide) a.out_collide[row] = (good && cinj > k.k_thr) ? 1 : 0;
+                if (a.out_count) a.out_count[row] = good ? cntj : 0;
+            }
         } else {
-            float gxo = 0.f, gyo = 0.f, gzo = 0.f;
-            if (!valid[i] || !ok) {
-                gxo = gyo = gzo = __int_as_float(0x7fc00000);
+            float gx, gy, gz, f = 0.f;
+            if (MODE == 0) {
+                gx = warp_sum(A.gx[j]); gy = warp_sum(A.gy[j]); gz = warp_sum(A.gz[j]);
+                f = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? -k.gamma * k.d_max / (float)cntj : 0.f)
+                                                    : -k.gamma * k.d_max;
+            } else if (MODE == 1) {
+                // the arg-min pair: the lane holding the smallest st2 (lowest lane on ties)
+                const float m = warp_min(A.mn[j]);
+                const unsigned who = __ballot_sync(0xffffffffu, A.mn[j] == m);
+                const int src = who ? __ffs(who) - 1 : 0;
+                gx = __shfl_sync(0xffffffffu, A.gx[j], src);
+                gy = __shfl_sync(0xffffffffu, A.gy[j], src);
+                gz = __shfl_sync(0xffffffffu, A.gz[j], src);
+                f = cntj > 0 ? 1.f : 0.f;
             } else {
-                const float c = st.cnt[i];
-                nb_total += c;
+                const float M = warp_min(A.sm_m[j]);
+                const float sc_ = ex2_approx((M - A.sm_m[j]) * k.K);
+                const float acc = warp_sum(A.sm_acc[j] * sc_);
+                gx = warp_sum(A.gx[j] * sc_); gy = warp_sum(A.gy[j] * sc_); gz = warp_sum(A.gz[j] * sc_);
+                f = cntj > 0 ? 1.f / acc : 0.f;
+            }
+            if (lane == 0 && q < a.Q) {
+                const uint32_t row = a.perm[q];
                 float up = 1.f;
                 if (a.grad_out) up = a.grad_out[k.group_size > 0 ? row / (uint32_t)k.group_size : row];
-                float f = 0.f;
-                switch (k.mode) {
-                    case CS_METRIC_MEAN_COST: f = c > 0.f ? -k.gamma * k.d_max / c : 0.f; break;
-                    case CS_METRIC_SUM_COST: f = -k.gamma * k.d_max; break;
-                    case CS_METRIC_MIN_S2: f = c > 0.f ? 1.f : 0.f; break;
-                    default: f = c > 0.f ? 1.f / st.sm_acc[i] : 0.f;
-                }
-                f *= up;
-                gxo = st.gx[i] * f; gyo = st.gy[i] * f; gzo = st.gz[i] * f;
+                const bool good = vq && ok;
+                const float nanv = __int_as_float(0x7fc00000);
+                a.grad_centres[3 * (size_t)row + 0] = good ? gx * f * up : nanv;
+                a.grad_centres[3 * (size_t)row + 1] = good ? gy * f * up : nanv;
+                a.grad_centres[3 * (size_t)row + 2] = good ? gz * f * up : nanv;
             }
-            a.grad_centres[3 * (size_t)row + 0] = gxo;
-            a.grad_centres[3 * (size_t)row + 1] = gyo;
-            a.grad_centres[3 * (size_t)row + 2] = gzo;
         }
+        nb_total += (unsigned long long)cntj;
     }
-    if (a.stats) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nb_total += __shfl_xor_sync(0xffffffffu, nb_total, o);
-        if (lane == 0) {
-            atomicAdd(a.stats + 0, (unsigned long long)evaluated * (unsigned long long)nvalid);
-            atomicAdd(a.stats + 1, (unsigned long long)nb_total);
-        }
+    if (a.stats && lane == 0) {
+        atomicAdd(a.stats + 0, cand);
+        atomicAdd(a.stats + 1, nb_total);
     }
 }
 
-template <int PRIM, int QB, int NCW, bool SOFTMIN, bool GRAD>
-__global__ void __launch_bounds__((NCW + 1) * 32) k_eval(const EvalArgs a) {
+template <int PRIM, int QW, int MODE, bool GRAD>
+__global__ void __launch_bounds__((kNCW + 1) * 32, (GRAD || QW > 8) ? 1 : 2) k_eval(const EvalArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    EvalSmem *sm = reinterpret_cast<EvalSmem *>(smem_raw);
+    EvalSmem<QW> *sm = reinterpret_cast<EvalSmem<QW> *>(smem_raw);
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNS; ++s) {
             mbar_init(&sm->full[s], 1);
-            mbar_init(&sm->empty[s], NCW);
+            mbar_init(&sm->empty[s], kNCW);
         }
         fence_mbar_init();
         sm->abort = (*(volatile unsigned *)a.err & kErrTimeout) ? 1 : 0;
@@ -677,10 +665,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32) k_eval(const EvalArgs a) {
     __syncthreads();
     const int tile = blockIdx.x;
     const bool abort = sm->abort != 0;
-    if (warp == NCW) {
-        if (!abort) producer_warp<PRIM, QB, NCW>(a, sm, tile);
+    if (warp == kNCW) {
+        if (!abort) producer_warp<PRIM, QW>(a, sm, tile);
     } else {
-        consumer_warp<PRIM, QB, NCW, SOFTMIN, GRAD>(a, sm, tile, warp, abort);
+        consumer_warp<PRIM, QW, MODE, GRAD>(a, sm, tile, warp, abort);
     }
 }
 
@@ -693,13 +681,16 @@ __device__ __forceinline__ uint32_t spread8(uint32_t v) {
     return v;
 }
 
-// Morton key of each primitive centre over the scene box (8 bits per axis).
-__global__ void k_prep_keys(const float *__restrict__ prims, int stride, int Q, SceneDev sc,
+// Sort key of each primitive: its size class (half-octaves of the radius or
+// largest semi-axis, from 1/1024 up) above the Morton code of its centre over
+// the scene box (8 bits per axis).  Tiles of consecutive keys then hold
+// primitives of similar size and position, so their shared cull is tight.
+__global__ void k_prep_keys(const float *__restrict__ prims, int prim_type, int Q, SceneDev sc,
                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Q) return;
+    const int stride = prim_type == CS_PRIM_SPHERE ? 4 : 10;
     const float *p = prims + (size_t)j * stride;
-    uint32_t code = 0;
     uint32_t c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -707,8 +698,15 @@ __global__ void k_prep_keys(const float *__restrict__ prims, int stride, int Q, 
         u = isfinite(u) ? fminf(fmaxf(u, 0.f), 255.f) : 255.f;
         c[a] = (uint32_t)u;
     }
-    code = spread8(c[0]) | (spread8(c[1]) << 1) | (spread8(c[2]) << 2);
-    keys[j] = code;
+    const uint32_t code = spread8(c[0]) | (spread8(c[1]) << 1) | (spread8(c[2]) << 2);
+    const float size = prim_type == CS_PRIM_SPHERE ? p[3] : fmaxf(fmaxf(p[7], p[8]), p[9]);
+    uint32_t cls = 31;
+    if (size > 0.f && isfinite(size)) {
+        const int bits = __float_as_int(size);
+        const int half_oct = 2 * ((bits >> 23) & 0xFF) + ((bits >> 22) & 1) - 2 * (127 - 10);
+        cls = (uint32_t)min(max(half_oct, 0), 31);
+    }
+    keys[j] = (cls << 24) | code;
     vals[j] = (uint32_t)j;
 }
 
@@ -799,10 +797,11 @@ QueryConsts make_consts(const cs_params &p) {
 
 struct TileCfg {
     int id;
-    int qb;
+    int qw;  // primitives per consumer warp
 };
-// ids: 1 = 1 primitive per lane (128 per tile), 2 = 2 (256), 3 = 4 (512)
-static const TileCfg kTileCfgs[] = {{1, 1}, {2, 2}, {3, 4}};
+// ids: 1 = 8 primitives per warp (64 per tile, two tiles per SM),
+//      2 = 16 (128 per tile, one tile per SM)
+static const TileCfg kTileCfgs[] = {{1, 8}, {2, 16}};
 
 int tile_configs(int32_t *ids, int32_t cap) {
     int n = (int)(sizeof(kTileCfgs) / sizeof(kTileCfgs[0]));
@@ -810,49 +809,50 @@ int tile_configs(int32_t *ids, int32_t cap) {
     return n;
 }
 
-constexpr int kNCW = 4;
-
-template <int PRIM, int QB, bool SOFTMIN, bool GRAD>
+template <int PRIM, int QW, int MODE, bool GRAD>
 static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
-    constexpr int TQ = kNCW * 32 * QB;
+    constexpr int TQ = kNCW * QW;
     const int ntiles = (a.Q + TQ - 1) / TQ;
-    static_assert(sizeof(EvalSmem) <= 48 * 1024, "stage ring must fit the default smem limit");
-    k_eval<PRIM, QB, kNCW, SOFTMIN, GRAD><<<ntiles, (kNCW + 1) * 32, sizeof(EvalSmem), s>>>(a);
+    const size_t smem = sizeof(EvalSmem<QW>);
+    auto kern = k_eval<PRIM, QW, MODE, GRAD>;
+    static bool attr = false;  // once per instantiation (idempotent)
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<ntiles, (kNCW + 1) * 32, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int PRIM, int QB>
-static cudaError_t launch_eval_qb(const EvalArgs &a, bool grad, cudaStream_t s) {
-    const bool soft = a.k.mode == CS_METRIC_SOFTMIN_S2;
-    if (grad) return launch_eval_t<PRIM, QB, false, true>(a, s);
-    if (soft) return launch_eval_t<PRIM, QB, true, false>(a, s);
-    return launch_eval_t<PRIM, QB, false, false>(a, s);
+template <int PRIM, int QW>
+static cudaError_t launch_eval_qw(const EvalArgs &a, bool grad, cudaStream_t s) {
+    const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
+    if (grad) {
+        if (mode == 0) return launch_eval_t<PRIM, 8, 0, true>(a, s);
+        if (mode == 1) return launch_eval_t<PRIM, 8, 1, true>(a, s);
+        return launch_eval_t<PRIM, 8, 2, true>(a, s);
+    }
+    if (mode == 0) return launch_eval_t<PRIM, QW, 0, false>(a, s);
+    if (mode == 1) return launch_eval_t<PRIM, QW, 1, false>(a, s);
+    return launch_eval_t<PRIM, QW, 2, false>(a, s);
 }
 
-static int choose_qb(int prim_type, int Q, int tile_cfg, int num_sms) {
+static int choose_qw(int Q, int tile_cfg, int num_sms) {
     for (const TileCfg &t : kTileCfgs)
-        if (t.id == tile_cfg) return (prim_type == CS_PRIM_ELLIPSOID && t.qb > 2) ? 2 : t.qb;
-    // automatic: the largest tile that still gives every SM four tiles
-    const int cand[3] = {4, 2, 1};
-    for (int qb : cand) {
-        if (prim_type == CS_PRIM_ELLIPSOID && qb > 2) continue;
-        int ntiles = (Q + kNCW * 32 * qb - 1) / (kNCW * 32 * qb);
-        if (ntiles >= 4 * num_sms) return qb;
-    }
-    return 1;
+        if (t.id == tile_cfg) return t.qw;
+    (void)Q;
+    (void)num_sms;
+    return 8;  // automatic: two 64-primitive tiles per SM
 }
 
 cudaError_t launch_eval(int prim_type, const EvalArgs &a, bool grad, int tile_cfg, int num_sms,
                         cudaStream_t s) {
-    int qb = choose_qb(prim_type, a.Q, tile_cfg, num_sms);
-    if (prim_type == CS_PRIM_SPHERE) {
-        if (qb == 4) return launch_eval_qb<0, 4>(a, grad, s);
-        if (qb == 2) return launch_eval_qb<0, 2>(a, grad, s);
-        return launch_eval_qb<0, 1>(a, grad, s);
-    }
-    if (qb == 2) return launch_eval_qb<1, 2>(a, grad, s);
-    return launch_eval_qb<1, 1>(a, grad, s);
+    const int qw = choose_qw(a.Q, tile_cfg, num_sms);
+    if (prim_type == CS_PRIM_SPHERE)
+        return qw == 16 ? launch_eval_qw<0, 16>(a, grad, s) : launch_eval_qw<0, 8>(a, grad, s);
+    return qw == 16 ? launch_eval_qw<1, 16>(a, grad, s) : launch_eval_qw<1, 8>(a, grad, s);
 }
 
 cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, const float *qns,
@@ -901,11 +901,10 @@ cudaError_t run_wait_selftest(long long polls, unsigned *err, cudaStream_t s) {
 
 void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, float ns_scalar,
                  const float *ns_rows, Workspace &ws, uint32_t **perm_out, cudaStream_t s) {
-    const int stride = prim_type == CS_PRIM_SPHERE ? 4 : 10;
     const int thr = 256, blk = (Q + thr - 1) / thr;
-    k_prep_keys<<<blk, thr, 0, s>>>(prims, stride, Q, sc, ws.keys[0], ws.vals[0]);
+    k_prep_keys<<<blk, thr, 0, s>>>(prims, prim_type, Q, sc, ws.keys[0], ws.vals[0]);
     count_launches(1);
-    int res = radix_sort(ws.keys, ws.vals, (size_t)Q, 3 * kMortonBits, ws.sort_hist, ws.scan_tmp, s);
+    int res = radix_sort(ws.keys, ws.vals, (size_t)Q, 32, ws.sort_hist, ws.scan_tmp, s);
     uint32_t *perm = ws.vals[res];
     k_prep_recs<<<blk, thr, 0, s>>>(prims, prim_type, Q, perm, ns_scalar, ns_rows, ws.qrec,
                                     ws.qns, ws.err);

@@ -92,7 +92,10 @@ def test_adjoint_group_upstream(cs):
 
 def test_adjoint_against_central_differences(cs):
     """Central differences (h = 1e-4 m) of the GPU metric itself agree with
-    the GPU adjoint where no kink lies within the stencil."""
+    the GPU adjoint on rows where the metric is smooth across the stencil
+    (rows where the oracle's own central differences match its analytic
+    gradient; elsewhere a kink of Eq. 8/11 or of the neighbour set lies
+    within h)."""
     sc = S.tiny_scene()
     rng = np.random.default_rng(2)
     Q = 200
@@ -101,27 +104,27 @@ def test_adjoint_against_central_differences(cs):
     g = scene.query_grad(torch.as_tensor(q), 1.0, params=cs.QueryParams(mode=1)).cpu().numpy()
     h = 1e-4
     fd = np.zeros((Q, 3))
-    stable = np.ones(Q, bool)
-    base = scene.query(torch.as_tensor(q), 1.0, want_count=True, params=cs.QueryParams(mode=1))
+    fd_o = np.zeros((Q, 3))
+    base = scene.query(torch.as_tensor(q), 1.0, params=cs.QueryParams(mode=1))
     for a in range(3):
-        vals = []
-        for s in (h, -h):
-            qq = q.astype(np.float64).copy()
-            qq[:, a] += s
-            qq = qq.astype(np.float32)
-            out = scene.query(torch.as_tensor(qq), 1.0, want_count=True, params=cs.QueryParams(mode=1))
-            stable &= (out["count"] == base["count"]).cpu().numpy()
-            step = qq[:, a].astype(np.float64) - q[:, a]
-            vals.append((out["metric"].cpu().numpy().astype(np.float64), step))
-        fd[:, a] = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
-    orc = oracle.query(sc, q, 0, 1.0)
-    stable &= orc["band_kink"] == 0
+        qp = q.astype(np.float64).copy()
+        qm = q.astype(np.float64).copy()
+        qp[:, a] += h
+        qm[:, a] -= h
+        qp, qm = qp.astype(np.float32), qm.astype(np.float32)
+        step = qp[:, a].astype(np.float64) - qm[:, a].astype(np.float64)
+        mp = scene.query(torch.as_tensor(qp), 1.0, params=cs.QueryParams(mode=1))["metric"]
+        mm = scene.query(torch.as_tensor(qm), 1.0, params=cs.QueryParams(mode=1))["metric"]
+        fd[:, a] = (mp.cpu().numpy().astype(np.float64) - mm.cpu().numpy().astype(np.float64)) / step
+        fd_o[:, a] = (oracle.query(sc, qp, 0, 1.0)["sum_cost"] - oracle.query(sc, qm, 0, 1.0)["sum_cost"]) / step
+    go = oracle.grad(sc, q, 0, 1.0, oracle.MODE_SUM)
+    smooth = np.linalg.norm(fd_o - go, axis=1) <= 1e-3 * np.linalg.norm(go, axis=1) + 1e-9
     m = base["metric"].cpu().numpy().astype(np.float64)
-    err = np.linalg.norm(g - fd, axis=1)[stable]
-    # FP32 metric differences over 2h: noise ~ 1e-7 |m| / h
-    tol = 2e-3 * np.linalg.norm(g, axis=1)[stable] + 4e-7 * np.abs(m[stable]) / h + 1e-6
+    err = np.linalg.norm(g - fd, axis=1)[smooth]
+    # FP32 metric differences over 2h: noise ~ 1e-6 |m| / h
+    tol = 2e-3 * np.linalg.norm(g, axis=1)[smooth] + 1e-6 * np.abs(m[smooth]) / h + 1e-6
     assert (err <= tol).all(), (err[err > tol][:5], tol[err > tol][:5])
-    assert stable.sum() > Q // 2
+    assert smooth.sum() > Q // 2
 
 
 def test_pose_chain_forward_and_adjoint(cs):
