@@ -197,24 +197,48 @@ struct Producer {
             if (nslot == kCHB) close_stage();
         }
     }
-    // The chunks overlapping [s, e) that pass the tile-level reach test.
+    // Every chunk overlapping sorted Gaussians [s, e) (a grid row span: the
+    // row's x-range already follows the tile's reach; the consumers test each
+    // chunk against each primitive).
     __device__ void append_span(int s, int e) {
         const int c0 = s / kChunk, c1 = (e - 1) / kChunk;
-        for (int cb = c0; cb <= c1 && !failed; cb += 32) {
-            const int c = cb + lane;
-            bool pass = false;
-            if (c <= c1) {
-                const float4 blo = __ldg(&sc->blocks[c].lo), bhi = __ldg(&sc->blocks[c].hi);
-                const float R = reach(al, be, blo.w, sc->pad_abs);
-                pass = box_gap2(lx, ly, lz, hx, hy, hz, blo, bhi) <= R * R;
+        emit_run(c0, c1 - c0 + 1, s, e);
+    }
+    // The large tier [s, e): its chunks are spread over the scene, so each is
+    // tested against the tile box first (four header loads in flight per lane).
+    __device__ void append_tested(int s, int e) {
+        const int c0 = s / kChunk, c1 = (e - 1) / kChunk;
+        for (int cb = c0; cb <= c1 && !failed; cb += 128) {
+            bool pass[4];
+            float4 blo[4], bhi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = cb + 32 * u + lane;
+                if (c <= c1) {
+                    blo[u] = __ldg(&sc->blocks[c].lo);
+                    bhi[u] = __ldg(&sc->blocks[c].hi);
+                }
             }
-            unsigned m = __ballot_sync(0xffffffffu, pass);
-            while (m && !failed) {
-                const int first = __ffs(m) - 1;
-                const unsigned rest = ~(m >> first);
-                const int len = rest ? __ffs(rest) - 1 : 32 - first;
-                emit_run(cb + first, len, s, e);
-                m = (first + len >= 32) ? 0u : (m & ~((1u << (first + len)) - 1u));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = cb + 32 * u + lane;
+                pass[u] = false;
+                if (c <= c1) {
+                    const float R = reach(al, be, blo[u].w, sc->pad_abs);
+                    pass[u] = box_gap2(lx, ly, lz, hx, hy, hz, blo[u], bhi[u]) <= R * R;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                unsigned m = __ballot_sync(0xffffffffu, pass[u]);
+                const int base = cb + 32 * u;
+                while (m && !failed) {
+                    const int first = __ffs(m) - 1;
+                    const unsigned rest = ~(m >> first);
+                    const int len = rest ? __ffs(rest) - 1 : 32 - first;
+                    emit_run(base + first, len, s, e);
+                    m = (first + len >= 32) ? 0u : (m & ~((1u << (first + len)) - 1u));
+                }
             }
         }
     }
@@ -294,43 +318,63 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile) {
         const int ny = iy1 - iy0 + 1;
         const int nrows = ny * (iz1 - iz0 + 1);
         const float slack = sc.pad_abs;
-        for (int rb = 0; rb < nrows && !pr.failed; rb += 32) {
-            int r = rb + lane;
-            int start = 0, cnt = 0;
-            if (r < nrows) {
-                int iz = iz0 + r / ny, iy = iy0 + r % ny;
-                float y0 = sc.lo[1] + (float)iy * sc.h - slack, y1 = sc.lo[1] + (float)(iy + 1) * sc.h + slack;
-                float z0 = sc.lo[2] + (float)iz * sc.h - slack, z1 = sc.lo[2] + (float)(iz + 1) * sc.h + slack;
-                // first and last rows extend to infinity (clamped cell coordinates)
-                if (iy == 0) y0 = -INFINITY;
-                if (iy == sc.dims[1] - 1) y1 = INFINITY;
-                if (iz == 0) z0 = -INFINITY;
-                if (iz == sc.dims[2] - 1) z1 = INFINITY;
-                float gy = fmaxf(0.f, fmaxf(y0 - hy, ly - y1));
-                float gz = fmaxf(0.f, fmaxf(z0 - hz, lz - z1));
-                float d2 = fmaf(gy, gy, gz * gz);
-                if (d2 <= R2) {
-                    float half = sqrtf(R2 - d2);
-                    int ix0 = cell_of(lx - half, sc.lo[0], sc.inv_h, sc.dims[0]);
-                    int ix1 = cell_of(hx + half, sc.lo[0], sc.inv_h, sc.dims[0]);
-                    uint32_t rowkey = (uint32_t)sc.dims[0] * ((uint32_t)iy + (uint32_t)sc.dims[1] * (uint32_t)iz);
-                    uint32_t b = sc.cell_start[rowkey + ix0];
-                    uint32_t e = sc.cell_start[rowkey + ix1 + 1];
-                    start = (int)b;
-                    cnt = (int)(e - b);
+        for (int rb = 0; rb < nrows && !pr.failed; rb += 64) {
+            int start[2] = {0, 0}, cnt[2] = {0, 0};
+            uint32_t kb[2] = {0, 0}, ke[2] = {0, 0};
+            bool want[2] = {false, false};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int r = rb + 32 * u + lane;
+                if (r < nrows) {
+                    const int iz = iz0 + r / ny, iy = iy0 + r % ny;
+                    float y0 = sc.lo[1] + (float)iy * sc.h - slack, y1 = sc.lo[1] + (float)(iy + 1) * sc.h + slack;
+                    float z0 = sc.lo[2] + (float)iz * sc.h - slack, z1 = sc.lo[2] + (float)(iz + 1) * sc.h + slack;
+                    // first and last rows extend to infinity (clamped cell coordinates)
+                    if (iy == 0) y0 = -INFINITY;
+                    if (iy == sc.dims[1] - 1) y1 = INFINITY;
+                    if (iz == 0) z0 = -INFINITY;
+                    if (iz == sc.dims[2] - 1) z1 = INFINITY;
+                    const float gy = fmaxf(0.f, fmaxf(y0 - hy, ly - y1));
+                    const float gz = fmaxf(0.f, fmaxf(z0 - hz, lz - z1));
+                    const float d2 = fmaf(gy, gy, gz * gz);
+                    if (d2 <= R2) {
+                        const float half = sqrtf(R2 - d2);
+                        const int ix0 = cell_of(lx - half, sc.lo[0], sc.inv_h, sc.dims[0]);
+                        const int ix1 = cell_of(hx + half, sc.lo[0], sc.inv_h, sc.dims[0]);
+                        const uint32_t rowkey =
+                            (uint32_t)sc.dims[0] * ((uint32_t)iy + (uint32_t)sc.dims[1] * (uint32_t)iz);
+                        kb[u] = rowkey + ix0;
+                        ke[u] = rowkey + ix1 + 1;
+                        want[u] = true;
+                    }
                 }
             }
-            unsigned m = __ballot_sync(0xffffffffu, cnt > 0);
-            while (m && !pr.failed) {
-                int src = __ffs(m) - 1;
-                m &= m - 1;
-                int s0 = __shfl_sync(0xffffffffu, start, src);
-                int c0 = __shfl_sync(0xffffffffu, cnt, src);
-                pr.append_span(s0, s0 + c0);
+            // all four cell-start loads in flight before any is used
+            uint32_t vb[2], ve[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                vb[u] = want[u] ? __ldg(sc.cell_start + kb[u]) : 0u;
+                ve[u] = want[u] ? __ldg(sc.cell_start + ke[u]) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                start[u] = (int)vb[u];
+                cnt[u] = (int)(ve[u] - vb[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                unsigned m = __ballot_sync(0xffffffffu, cnt[u] > 0);
+                while (m && !pr.failed) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int s0 = __shfl_sync(0xffffffffu, start[u], src);
+                    const int c0 = __shfl_sync(0xffffffffu, cnt[u], src);
+                    pr.append_span(s0, s0 + c0);
+                }
             }
         }
     }
-    if (any && sc.n_kept > sc.n_grid && !pr.failed) pr.append_span(sc.n_grid, sc.n_kept);  // large tier
+    if (any && sc.n_kept > sc.n_grid && !pr.failed) pr.append_tested(sc.n_grid, sc.n_kept);  // large tier
     pr.finish();
     if (pr.failed) {
         if (lane == 0) atomicOr(a.err, kErrTimeout);
@@ -470,6 +514,24 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
     }
 }
 
+// Does the primitive (shared-memory record) reach the chunk (bounding box,
+// largest scale)?  Dead slots never do.  The same answer on every lane.
+template <int PRIM>
+__device__ __forceinline__ bool reaches(const float4 *qd, const float4 &blo, const float4 &bhi,
+                                        float pad_abs) {
+    const float4 q0 = qd[0];
+    float alpha, beta, live;
+    if (PRIM == 0) {
+        const float4 q1 = qd[1];
+        alpha = q1.y; beta = q1.z; live = q1.w;
+    } else {
+        const float4 q2 = qd[2];
+        alpha = q2.z; beta = q2.w; live = qd[3].x;
+    }
+    const float R = reach(alpha, beta, blo.w, pad_abs);
+    return live != 0.f && box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) <= R * R;
+}
+
 template <int PRIM, int QW, int MODE, bool GRAD>
 __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int warp, bool abort) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
@@ -560,17 +622,23 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
                 const float4 blo = B.lo, bhi = B.hi;
                 const int nlanes = mt.hi - mt.lo;
 #pragma unroll
-                for (int j = 0; j < QW; ++j) {
-                    const float4 *qd = wq[j];
-                    const float4 q0 = qd[0];
-                    float alpha, beta, live;
-                    if (PRIM == 0) { const float4 q1 = qd[1]; alpha = q1.y; beta = q1.z; live = q1.w; }
-                    else { const float4 q2 = qd[2]; alpha = q2.z; beta = q2.w; live = qd[3].x; }
-                    if (live == 0.f) continue;  // warp-uniform
-                    const float R = reach(alpha, beta, blo.w, sc.pad_abs);
-                    if (box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) > R * R) continue;  // uniform
-                    cand += (unsigned long long)nlanes;
-                    pair_update<PRIM, QW, MODE, GRAD>(A, j, g, qd, k);
+                for (int j = 0; j < QW; j += 2) {
+                    // two primitives per step: when both reach the chunk their
+                    // pair updates share one basic block (two independent
+                    // dependency chains for the scheduler)
+                    const bool p0 = reaches<PRIM>(wq[j], blo, bhi, sc.pad_abs);
+                    const bool p1 = reaches<PRIM>(wq[j + 1], blo, bhi, sc.pad_abs);
+                    if (p0 && p1) {
+                        cand += 2ull * (unsigned long long)nlanes;
+                        pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
+                        pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+                    } else if (p0) {
+                        cand += (unsigned long long)nlanes;
+                        pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
+                    } else if (p1) {
+                        cand += (unsigned long long)nlanes;
+                        pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+                    }
                 }
             }
         }
