@@ -59,7 +59,7 @@ struct EvalArgs {
 // plus one producer warp.  Stages hold kCHB chunk blocks.
 constexpr int kNCW = 8;
 constexpr int kNS = 4;      // pipeline stages
-constexpr int kCHB = 8;     // chunk blocks per stage (256 Gaussians)
+constexpr int kCHB = 16;    // chunk blocks per stage (512 Gaussians)
 
 struct SlotMeta {
     int chunk;  // global chunk id
@@ -572,6 +572,31 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
     }
     nvalid = __reduce_add_sync(0xffffffffu, nvalid);
     __syncwarp();
+    // the warp's box of primitive centres and its largest reach parameters:
+    // a chunk outside box + reach is out of reach of every primitive here
+    float wlx = INFINITY, wly = INFINITY, wlz = INFINITY, whx = -INFINITY, why = -INFINITY, whz = -INFINITY;
+    float wal = 0.f, wbe = 0.f;
+    if (lane < QW) {
+        const float4 q0 = wq[lane][0];
+        float alpha, beta, live;
+        if (PRIM == 0) { const float4 q1 = wq[lane][1]; alpha = q1.y; beta = q1.z; live = q1.w; }
+        else { const float4 q2 = wq[lane][2]; alpha = q2.z; beta = q2.w; live = wq[lane][3].x; }
+        if (live != 0.f) {
+            wlx = whx = q0.x; wly = why = q0.y; wlz = whz = q0.z;
+            wal = alpha; wbe = beta;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wlx = fminf(wlx, __shfl_xor_sync(0xffffffffu, wlx, o));
+        wly = fminf(wly, __shfl_xor_sync(0xffffffffu, wly, o));
+        wlz = fminf(wlz, __shfl_xor_sync(0xffffffffu, wlz, o));
+        whx = fmaxf(whx, __shfl_xor_sync(0xffffffffu, whx, o));
+        why = fmaxf(why, __shfl_xor_sync(0xffffffffu, why, o));
+        whz = fmaxf(whz, __shfl_xor_sync(0xffffffffu, whz, o));
+        wal = fmaxf(wal, __shfl_xor_sync(0xffffffffu, wal, o));
+        wbe = fmaxf(wbe, __shfl_xor_sync(0xffffffffu, wbe, o));
+    }
 
     Acc<PRIM, QW, MODE, GRAD> A;
 #pragma unroll
@@ -595,9 +620,24 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
         const int nslots = sm->count[s];
         if (nslots == 0) break;
         if (nvalid > 0) {
-            for (int slot = 0; slot < nslots; ++slot) {
+            // lane t tests chunk slot t against the warp's box + reach
+            bool wpass = false;
+            if (lane < nslots) {
+                const float4 blo = sm->blk[s][lane].lo, bhi = sm->blk[s][lane].hi;
+                const float R = reach(wal, wbe, blo.w, sc.pad_abs);
+                wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
+            }
+            unsigned cmask = __ballot_sync(0xffffffffu, wpass);
+            while (cmask) {
+                const int slot = __ffs(cmask) - 1;
+                cmask &= cmask - 1;
                 const SlotMeta mt = sm->meta[s][slot];
                 const ChunkBlock &B = sm->blk[s][slot];
+                const float4 blo = B.lo, bhi = B.hi;
+                // lane j tests primitive j against the chunk
+                const bool qp = lane < QW && reaches<PRIM>(wq[lane], blo, bhi, sc.pad_abs);
+                const unsigned qmask = __ballot_sync(0xffffffffu, qp);
+                if (qmask == 0u) continue;
                 if (MODE == 0 && !GRAD) {
                     // fixed grouping of the cost partials (16 chunks) keeps
                     // the summation order independent of the tile
@@ -619,24 +659,19 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
                 g.sxy2 = lv ? B.sxy2[lane] : 0.f;
                 g.sxz2 = lv ? B.sxz2[lane] : 0.f;
                 g.syz2 = lv ? B.syz2[lane] : 0.f;
-                const float4 blo = B.lo, bhi = B.hi;
-                const int nlanes = mt.hi - mt.lo;
+                cand += (unsigned long long)__popc(qmask) * (unsigned long long)(mt.hi - mt.lo);
 #pragma unroll
                 for (int j = 0; j < QW; j += 2) {
                     // two primitives per step: when both reach the chunk their
                     // pair updates share one basic block (two independent
                     // dependency chains for the scheduler)
-                    const bool p0 = reaches<PRIM>(wq[j], blo, bhi, sc.pad_abs);
-                    const bool p1 = reaches<PRIM>(wq[j + 1], blo, bhi, sc.pad_abs);
+                    const bool p0 = (qmask >> j) & 1u, p1 = (qmask >> (j + 1)) & 1u;
                     if (p0 && p1) {
-                        cand += 2ull * (unsigned long long)nlanes;
                         pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
                         pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
                     } else if (p0) {
-                        cand += (unsigned long long)nlanes;
                         pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
                     } else if (p1) {
-                        cand += (unsigned long long)nlanes;
                         pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
                     }
                 }
