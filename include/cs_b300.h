@@ -177,6 +177,34 @@ CS_API cs_status cs_query(const cs_scene *scene, int32_t prim_type, const float 
                    float conservatism, float *out_metric, uint8_t *out_collide,
                    const cs_params *params);
 
+/* Largest Q that cs_query_noalloc accepts. */
+#define CS_QUERY_NOALLOC_MAX_ROWS 65536
+
+/* cs_query without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc once they are
+ * running -- a receding-horizon controller with a hard period, where an
+ * allocation may block on the driver and synchronise the device, or a program
+ * whose device memory is owned by another allocator that forbids outside
+ * allocations.  Arguments, outputs and results are those of cs_query, with
+ * these limits:
+ *   - the scratch is one fixed area inside the library image (about 4.6 MB of
+ *     device memory on every GPU that loads the library, held until the
+ *     process exits), so Q <= CS_QUERY_NOALLOC_MAX_ROWS; a larger Q returns
+ *     CS_ERR_INVALID_ARG before anything is enqueued;
+ *   - device pointers only (params->host_io = 1 returns CS_ERR_INVALID_ARG);
+ *     the scene's device must be current;
+ *   - the first call on a device resolves the area's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call shares the area and it keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (other streams, other threads)
+ *     race and corrupt each other's rows, so the caller serialises them;
+ *   - invalid rows and an expired wait show as NaN rows; cs_sync does not
+ *     report them for this entry point.
+ * The caller still passes the scene and every input and output buffer. */
+CS_API cs_status cs_query_noalloc(const cs_scene *scene, int32_t prim_type, const float *prims,
+                                  int64_t Q, float conservatism, float *out_metric,
+                                  uint8_t *out_collide, const cs_params *params);
+
 /* Adjoint of cs_query: grad_centres[j] = grad_out[j] * d metric_j / d c_j
  * ([Q,3], float).  With params->group_size > 0, grad_out has one entry per
  * group and applies to every row of the group (the group metric is a sum).

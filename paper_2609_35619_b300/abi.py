@@ -89,6 +89,8 @@ _SIGNATURES = {
                                 ctypes.POINTER(cs_params)]),
     "cs_query_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P,
                                      ctypes.POINTER(cs_params)]),
+    "cs_query_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P,
+                                        ctypes.POINTER(cs_params)]),
     "cs_pose_spheres": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_float, _P, _P]),
     "cs_pose_spheres_grad": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, _P, _P, _P]),
     "cs_sync": (ctypes.c_int, [_P, _P]),
@@ -188,6 +190,15 @@ def cs_scene_export(scene, pos, cov, index, stream) -> int:
 def cs_query(scene, prim_type, prims, Q, conservatism, out_metric, out_collide, params) -> int:
     return load().cs_query(scene, prim_type, ptr(prims), int(Q), float(conservatism), ptr(out_metric),
                            ptr(out_collide), None if params is None else ctypes.byref(params))
+
+
+def cs_query_noalloc(scene, prim_type, prims, Q, conservatism, out_metric, out_collide, params) -> int:
+    return load().cs_query_noalloc(scene, prim_type, ptr(prims), int(Q), float(conservatism),
+                                   ptr(out_metric), ptr(out_collide),
+                                   None if params is None else ctypes.byref(params))
+
+
+CS_QUERY_NOALLOC_MAX_ROWS = 65536
 
 
 def cs_query_grad(scene, prim_type, prims, Q, conservatism, grad_out, grad_centres, params) -> int:

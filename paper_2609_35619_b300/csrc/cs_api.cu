@@ -43,7 +43,7 @@ cs_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? CS_ERR_NO_MEMORY : CS_ERR_CUDA;
 }
 
-static cs_status invalid(const char *msg) {
+cs_status invalid(const char *msg) {
     g_err = msg;
     return CS_ERR_INVALID_ARG;
 }
@@ -128,7 +128,7 @@ cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io,
     return CS_OK;
 }
 
-static cs_status check_scene(const cs_scene *s) {
+cs_status check_scene(const cs_scene *s) {
     const Scene *sc = reinterpret_cast<const Scene *>(s);
     if (!sc || sc->magic != kSceneMagic) {
         g_err = "invalid scene handle";
@@ -137,7 +137,7 @@ static cs_status check_scene(const cs_scene *s) {
     return CS_OK;
 }
 
-static cs_status check_params(const cs_params &p) {
+cs_status check_params(const cs_params &p) {
     if (!(p.gamma > 0.f) || !isfinite(p.gamma)) return invalid("gamma must be finite and > 0");
     if (!isfinite(p.d_max)) return invalid("d_max must be finite");
     if (!isfinite(p.s_min)) return invalid("s_min must be finite");

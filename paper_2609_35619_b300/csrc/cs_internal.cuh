@@ -120,6 +120,9 @@ void count_launches(int n);
 // ---------------------------------------------------- error helpers (host)
 void set_error(const std::string &msg);
 cs_status cuda_fail(cudaError_t e, const char *what);
+cs_status invalid(const char *msg);
+cs_status check_scene(const cs_scene *s);
+cs_status check_params(const cs_params &p);
 
 #define CS_CUDA(call)                                                  \
     do {                                                               \
