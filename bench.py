@@ -51,6 +51,9 @@ def parse():
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
                          "(two fused-kernel launches); prints a short JSON summary")
+    ap.add_argument("--tile", type=int, default=0, help="tile configuration for --case eval (0 = auto)")
+    ap.add_argument("--batch", default="arm", choices=["arm", "edge"], help="query batch for --case eval")
+    ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     return ap.parse_args()
 
 
@@ -400,25 +403,38 @@ def run_reference(args, rank, world):
 
 def run_eval_case(args):
     """Small case for kernel profiles: one scene build and two launches of the
-    fused kernel over the 262,144 arm spheres (the second is the measured one)."""
+    fused kernel over the 262,144 arm spheres (the second is the measured one;
+    a third, untimed, reads the kernel counters)."""
     import torch
 
     import cs_synth as S
     import paper_2609_35619_b300 as cs
     dev = torch.device("cuda", 0)
     sc = S.tabletop_scene()
-    arm = torch.as_tensor(S.arm_queries(), device=dev)
+    arm = torch.as_tensor(S.arm_queries() if args.batch == "arm" else S.edge_queries(), device=dev)
     scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    G = 64 if args.batch == "arm" else 1024
+    qp = cs.QueryParams(group_size=G, tile_config=args.tile)
+    ns = args.nsigma
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    kstats = torch.zeros(16, dtype=torch.int64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    scene.query(arm, 1.0, params=cs.QueryParams(group_size=64))
-    scene.query(arm, 1.0, params=cs.QueryParams(group_size=64), pair_stats=stats, eval_events=ev)
+    scene.query(arm, ns, params=qp)
+    scene.query(arm, ns, params=qp, pair_stats=stats, eval_events=ev)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    scene.query(arm, ns, params=qp, kernel_stats=kstats)
     torch.cuda.synchronize()
     scene.sync()
     cand, useful = stats.cpu().tolist()
-    ms = ev[0].elapsed_time(ev[1])
-    print(json.dumps({"case": "eval", "queries": arm.shape[0], "useful_pairs": useful,
-                      "candidate_pairs": cand, "eval_ms": ms, "info": scene.info()}))
+    names = ["stages", "chunks_tested", "chunks_pass_warp", "hits", "chunks_staged", "stages_filled",
+             "consumer_polls", "producer_polls", "consumer_cycles", "consumer_wait_cycles",
+             "producer_cycles", "producer_wait_cycles", "consumer_first_cycles", "producer_first_cycles",
+             "consumer_tail_cycles", "tiles"]
+    print(json.dumps({"case": "eval", "batch": args.batch, "tile": args.tile, "nsigma": ns,
+                      "queries": arm.shape[0], "useful_pairs": useful,
+                      "candidate_pairs": cand, "eval_ms": ms,
+                      "kernel_stats": dict(zip(names, kstats.cpu().tolist())), "info": scene.info()}))
 
 
 def main():

@@ -124,6 +124,21 @@ typedef struct cs_params {
                                   [1] += pairs in the neighbour sets (sum of |N_j|) */
     void *eval_events[2];      /* optional cudaEvent_t pair recorded on `stream` immediately
                                   before and after the fused cull+evaluate kernel (tracing) */
+    unsigned long long *out_kernel_stats; /* optional device [16], accumulated (not cleared),
+                                  counters of the fused kernel (tuning):
+                                  [0] stages consumed by consumer warps,
+                                  [1] staged chunks tested by consumer warps,
+                                  [2] chunks passing a consumer warp's box test,
+                                  [3] (primitive, chunk) hits evaluated,
+                                  [4] chunks staged by producers,
+                                  [5] stages filled by producers,
+                                  [6] polls of consumer waits, [7] polls of producer waits,
+                                  [8] consumer-warp cycles in total, [9] of which waiting,
+                                  [10] producer-warp cycles in total, [11] of which waiting,
+                                  [12] consumer cycles until the first stage was ready,
+                                  [13] producer cycles until the first stage was closed,
+                                  [14] consumer cycles after the last stage (reductions),
+                                  [15] tiles */
 } cs_params;
 
 /* Scene information returned by cs_scene_info. */

@@ -116,7 +116,7 @@ class Scene:
 
     def query(self, prims, nsigma=1.0, *, prim_type=CS_PRIM_SPHERE, params: QueryParams | None = None,
               nsigma_per_query=None, want_count=False, pair_stats=None, stream=None,
-              eval_events=None, out=None) -> dict:
+              eval_events=None, out=None, kernel_stats=None) -> dict:
         """cs_query on device tensors; returns a dict of device tensors."""
         torch = _torch()
         params = params or QueryParams()
@@ -146,6 +146,8 @@ class Scene:
             p.out_group_collide = abi.ptr(out["group_collide"])
         if pair_stats is not None:
             p.out_pair_stats = abi.ptr(pair_stats)
+        if kernel_stats is not None:
+            p.out_kernel_stats = abi.ptr(kernel_stats)
         check(abi.cs_query(self._h, prim_type, prims, Q, float(nsigma), out["metric"], out["collide"], p))
         out.pop("_ns", None)
         return out

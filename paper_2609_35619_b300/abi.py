@@ -59,6 +59,7 @@ class cs_params(ctypes.Structure):
         ("out_group_collide", ctypes.c_void_p),
         ("out_pair_stats", ctypes.c_void_p),
         ("eval_events", ctypes.c_void_p * 2),
+        ("out_kernel_stats", ctypes.c_void_p),
     ]
 
 

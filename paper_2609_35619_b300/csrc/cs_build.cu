@@ -185,34 +185,53 @@ __global__ void k_count_keys(const uint32_t *__restrict__ keys, int64_t n, uint3
     if (i < n) atomicAdd(&cnt[keys[i] >> kFineKeyBits], 1u);
 }
 
-// One warp per chunk block: lane l fills Gaussian 32c + l (sorted order) and
-// the warp reduces the block's bounding box and largest scale.
-__global__ void k_blocks(const uint32_t *__restrict__ perm, int n_kept, int nchunks,
-                         const float4 *__restrict__ pos, const float4 *__restrict__ covA,
-                         const float4 *__restrict__ covB, ChunkBlock *__restrict__ blocks,
-                         float *__restrict__ smax, int32_t *__restrict__ index) {
-    int c = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
+// Every slot starts as padding: a point at 1e18 with zero covariance.
+__global__ void k_fill_padding(ChunkBlock *__restrict__ blocks, int nchunks, float *__restrict__ slot_smax) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nchunks * kChunk) return;
+    ChunkBlock &b = blocks[t / kChunk];
+    int l = t % kChunk;
+    b.x[l] = 1e18f; b.y[l] = 1e18f; b.z[l] = 1e18f;
+    b.sxx[l] = 0.f; b.syy[l] = 0.f; b.szz[l] = 0.f;
+    b.sxy2[l] = 0.f; b.sxz2[l] = 0.f; b.syz2[l] = 0.f;
+    slot_smax[t] = -1.f;  // marks padding for the header pass
+}
+
+// Sorted Gaussian p of cell c goes to slot cell_slot[c] + (p - cell_first[c]).
+__global__ void k_scatter_slots(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ perm, int n_gauss,
+                                const uint32_t *__restrict__ cell_first, const uint32_t *__restrict__ cell_slot,
+                                const float4 *__restrict__ pos, const float4 *__restrict__ covA,
+                                const float4 *__restrict__ covB, ChunkBlock *__restrict__ blocks,
+                                float *__restrict__ slot_smax, float *__restrict__ smax,
+                                int32_t *__restrict__ index, int32_t *__restrict__ slot_of) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_gauss) return;
+    const uint32_t c = keys[p] >> kFineKeyBits;
+    const uint32_t slot = cell_slot[c] + ((uint32_t)p - cell_first[c]);
+    const uint32_t i = perm[p];
+    const float4 P = pos[i], A = covA[i], B = covB[i];
+    ChunkBlock &b = blocks[slot / kChunk];
+    const int l = (int)(slot % kChunk);
+    b.x[l] = P.x; b.y[l] = P.y; b.z[l] = P.z;
+    b.sxx[l] = A.x; b.syy[l] = A.y; b.szz[l] = A.z; b.sxy2[l] = A.w;
+    b.sxz2[l] = B.x; b.syz2[l] = B.y;
+    slot_smax[slot] = P.w;
+    smax[p] = P.w;
+    index[p] = (int32_t)i;
+    slot_of[p] = (int32_t)slot;
+}
+
+// One warp per chunk: the box of its real slots and their largest scale.
+__global__ void k_chunk_headers(ChunkBlock *__restrict__ blocks, int nchunks, const float *__restrict__ slot_smax) {
+    int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (c >= nchunks) return;
-    int p = c * kChunk + lane;
     ChunkBlock &b = blocks[c];
-    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
-    float sg = 0.f;
-    if (p < n_kept) {
-        uint32_t i = perm[p];
-        float4 P = pos[i], A = covA[i], B = covB[i];
-        b.x[lane] = P.x; b.y[lane] = P.y; b.z[lane] = P.z;
-        b.sxx[lane] = A.x; b.syy[lane] = A.y; b.szz[lane] = A.z; b.sxy2[lane] = A.w;
-        b.sxz2[lane] = B.x; b.syz2[lane] = B.y;
-        smax[p] = P.w;
-        index[p] = (int32_t)i;
-        lx = hx = P.x; ly = hy = P.y; lz = hz = P.z; sg = P.w;
-    } else {
-        b.x[lane] = __int_as_float(0x7fc00000);  // never a neighbour
-        b.y[lane] = 0.f; b.z[lane] = 0.f;
-        b.sxx[lane] = 0.f; b.syy[lane] = 0.f; b.szz[lane] = 0.f;
-        b.sxy2[lane] = 0.f; b.sxz2[lane] = 0.f; b.syz2[lane] = 0.f;
-    }
+    const float sg0 = slot_smax[(size_t)c * kChunk + lane];
+    const bool real = sg0 >= 0.f;
+    float lx = real ? b.x[lane] : INFINITY, ly = real ? b.y[lane] : INFINITY, lz = real ? b.z[lane] : INFINITY;
+    float hx = real ? b.x[lane] : -INFINITY, hy = real ? b.y[lane] : -INFINITY, hz = real ? b.z[lane] : -INFINITY;
+    float sg = real ? sg0 : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
@@ -227,6 +246,18 @@ __global__ void k_blocks(const uint32_t *__restrict__ perm, int n_kept, int nchu
         b.lo = make_float4(lx, ly, lz, sg);
         b.hi = make_float4(hx, hy, hz, 0.f);
     }
+}
+
+// Slots per cell: the cell's count rounded up to a multiple of kCellAlign
+// (the dropped bucket, the last one, gets none).  kCellAlign = 32 would start
+// every cell on a chunk boundary (tighter chunk boxes, more chunks); measured
+// on the tabletop workloads, the kernel's cost follows the number of
+// (primitive, chunk) hits, so cells are packed densely.
+constexpr uint32_t kCellAlign = 1;
+__global__ void k_pad_counts(const uint32_t *__restrict__ cnt, uint32_t *__restrict__ pcnt, uint32_t nkeys) {
+    uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nkeys) return;
+    pcnt[c] = (c + 1 < nkeys) ? ((cnt[c] + kCellAlign - 1) / kCellAlign) * kCellAlign : 0u;
 }
 
 struct DevBuf {
@@ -363,15 +394,50 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
                          (uint32_t *)tmp_scan.p, s);
     }
 
-    // owned memory: chunk blocks, key starts, per-Gaussian largest scale and input row
-    const int64_t kmax = std::max<int64_t>(kept_est, 1);
-    const int nchunks = (int)((kept_est + kChunk - 1) / kChunk);
+    // ---- real and padded (slot) starts of every cell
+    uint32_t *cnt = (uint32_t *)tmp_hist.p;  // nkeys + 1 counters
+    DevBuf tmp_first, tmp_pcnt;
+    CS_CUDA(cudaMalloc(&tmp_first.p, 4 * ((size_t)nkeys + 1)));
+    CS_CUDA(cudaMalloc(&tmp_pcnt.p, 4 * ((size_t)nkeys + 1)));
+    uint32_t *first = (uint32_t *)tmp_first.p, *pcnt = (uint32_t *)tmp_pcnt.p;
+    CS_CUDA(cudaMemsetAsync(cnt, 0, 4 * ((size_t)nkeys + 1), s));
+    if (n > 0) {
+        k_count_keys<<<blocks_for(n), kThreads, 0, s>>>(keys[res], n, cnt);
+        count_launches(1);
+    }
+    scan_exclusive(cnt, first, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
+    k_pad_counts<<<blocks_for((int64_t)nkeys + 1), kThreads, 0, s>>>(cnt, pcnt, nkeys);
+    count_launches(1);
+    DevBuf tmp_slot;
+    CS_CUDA(cudaMalloc(&tmp_slot.p, 4 * ((size_t)nkeys + 1)));
+    uint32_t *slot_first = (uint32_t *)tmp_slot.p;
+    scan_exclusive(pcnt, slot_first, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
+    uint32_t bounds[4] = {0, 0, 0, 0};
+    CS_CUDA(cudaMemcpyAsync(&bounds[0], first + g.ncells, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaMemcpyAsync(&bounds[1], first + g.ncells + ncoarse, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaMemcpyAsync(&bounds[2], slot_first + g.ncells, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaMemcpyAsync(&bounds[3], slot_first + g.ncells + ncoarse, 4, cudaMemcpyDeviceToHost, s));
+    int sgm = INT_MIN;
+    CS_CUDA(cudaMemcpyAsync(&sgm, &st->sigma_grid_max, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_grid = bounds[0], n_kept = bounds[1];
+    const int64_t grid_end = bounds[2], slot_end = bounds[3];
+    if (n_kept != kept_est || slot_end > ((int64_t)1 << 31) - kChunk) {
+        set_error("internal: slot layout mismatch in scene build");
+        return CS_ERR_CUDA;
+    }
+    const int nchunks = (int)((slot_end + kChunk - 1) / kChunk);
+
+    // owned memory: chunk blocks, slot starts of the cells, and per sorted
+    // Gaussian its largest scale, input row and slot (export)
+    const int64_t kmax = std::max<int64_t>(n_kept, 1);
     size_t bytes_blocks = sizeof(ChunkBlock) * (size_t)std::max(nchunks, 1);
     size_t bytes_keys = (size_t)4 * (nkeys + 1);
     size_t off_keys = (bytes_blocks + 255) & ~(size_t)255;
     size_t off_smax = (off_keys + bytes_keys + 255) & ~(size_t)255;
     size_t off_index = (off_smax + 4 * (size_t)kmax + 255) & ~(size_t)255;
-    size_t total = off_index + 4 * (size_t)kmax;
+    size_t off_slot = (off_index + 4 * (size_t)kmax + 255) & ~(size_t)255;
+    size_t total = off_slot + 4 * (size_t)kmax;
     void *blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, total);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation
@@ -384,32 +450,25 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     uint32_t *kstart = (uint32_t *)(base + off_keys);
     float *smax = (float *)(base + off_smax);
     int32_t *index = (int32_t *)(base + off_index);
-
-    uint32_t *cnt = (uint32_t *)tmp_hist.p;  // reuse: nkeys + 1 counters
-    CS_CUDA(cudaMemsetAsync(cnt, 0, 4 * ((size_t)nkeys + 1), s));
-    if (n > 0) {
-        k_count_keys<<<blocks_for(n), kThreads, 0, s>>>(keys[res], n, cnt);
-        count_launches(1);
-    }
-    scan_exclusive(cnt, kstart, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
-    uint32_t bounds[2] = {0, 0};
-    CS_CUDA(cudaMemcpyAsync(&bounds[0], kstart + g.ncells, 4, cudaMemcpyDeviceToHost, s));
-    CS_CUDA(cudaMemcpyAsync(&bounds[1], kstart + g.ncells + ncoarse, 4, cudaMemcpyDeviceToHost, s));
-    int sgm = INT_MIN;
-    CS_CUDA(cudaMemcpyAsync(&sgm, &st->sigma_grid_max, 4, cudaMemcpyDeviceToHost, s));
-    CS_CUDA(cudaStreamSynchronize(s));
-    const int64_t n_grid = bounds[0], n_kept = bounds[1];
-    if (n_kept != kept_est) {
-        set_error("internal: kept count mismatch in scene build");
-        return CS_ERR_CUDA;
-    }
+    int32_t *slot_of = (int32_t *)(base + off_slot);
+    CS_CUDA(cudaMemcpyAsync(kstart, slot_first, bytes_keys, cudaMemcpyDeviceToDevice, s));
     if (nchunks > 0) {
-        k_blocks<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            vals[res], (int)n_kept, nchunks, upos, ucovA, ucovB, blocks, smax, index);
-        count_launches(1);
+        DevBuf tmp_ss;
+        CS_CUDA(cudaMalloc(&tmp_ss.p, 4 * (size_t)nchunks * kChunk));
+        float *slot_smax = (float *)tmp_ss.p;
+        k_fill_padding<<<(unsigned)(((int64_t)nchunks * kChunk + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            blocks, nchunks, slot_smax);
+        k_scatter_slots<<<blocks_for(n_kept), kThreads, 0, s>>>(keys[res], vals[res], (int)n_kept, first, slot_first,
+                                                                upos, ucovA, ucovB, blocks, slot_smax, smax,
+                                                                index, slot_of);
+        k_chunk_headers<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            blocks, nchunks, slot_smax);
+        count_launches(3);
+        CS_CUDA(cudaGetLastError());
+        CS_CUDA(cudaStreamSynchronize(s));  // before the temporaries are freed
     }
     CS_CUDA(cudaGetLastError());
-    CS_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
+    CS_CUDA(cudaStreamSynchronize(s));
 
     sc->n_kept = n_kept;
     sc->n_grid = n_grid;
@@ -419,8 +478,10 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     dv.cell_start = kstart;
     dv.smax = smax;
     dv.index = index;
-    dv.n_kept = (int)n_kept;
-    dv.n_grid = (int)n_grid;
+    dv.slot_of = slot_of;
+    dv.n_gauss = (int)n_kept;
+    dv.grid_end = (int)grid_end;
+    dv.slot_end = (int)slot_end;
     dv.nchunks = nchunks;
     for (int k = 0; k < 3; ++k) {
         dv.dims[k] = dims[k];
@@ -443,12 +504,13 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
 namespace {
 // Unpack the chunk blocks into row-major arrays (cs_scene_export).
 __global__ void k_export(const ChunkBlock *__restrict__ blocks, const float *__restrict__ smax,
-                         const int32_t *__restrict__ index, int n, float *__restrict__ pos,
-                         float *__restrict__ cov, int32_t *__restrict__ oidx) {
+                         const int32_t *__restrict__ index, const int32_t *__restrict__ slot_of, int n,
+                         float *__restrict__ pos, float *__restrict__ cov, int32_t *__restrict__ oidx) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const ChunkBlock &b = blocks[p / kChunk];
-    int l = p % kChunk;
+    const int t = slot_of[p];
+    const ChunkBlock &b = blocks[t / kChunk];
+    int l = t % kChunk;
     if (pos) {
         pos[4 * p + 0] = b.x[l]; pos[4 * p + 1] = b.y[l]; pos[4 * p + 2] = b.z[l];
         pos[4 * p + 3] = smax[p];
@@ -464,8 +526,8 @@ __global__ void k_export(const ChunkBlock *__restrict__ blocks, const float *__r
 }  // namespace
 
 void launch_export(const SceneDev &sc, float *pos, float *cov, int32_t *index, cudaStream_t s) {
-    k_export<<<(sc.n_kept + 255) / 256, 256, 0, s>>>(sc.blocks, sc.smax, sc.index, sc.n_kept, pos, cov,
-                                                     index);
+    k_export<<<(sc.n_gauss + 255) / 256, 256, 0, s>>>(sc.blocks, sc.smax, sc.index, sc.slot_of, sc.n_gauss, pos,
+                                                      cov, index);
     count_launches(1);
 }
 

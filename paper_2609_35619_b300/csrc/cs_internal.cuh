@@ -33,16 +33,19 @@ constexpr unsigned kErrTimeout = 2u;
 constexpr long long kWaitPolls = 1ll << 27;
 
 // ------------------------------------------------------------- scene layout
-// Repacked Gaussians are stored in chunk blocks of kChunk = 32 consecutive
-// (grid-sorted) Gaussians, one 1184-byte block each, so that a run of chunks
-// is one contiguous 1-D bulk copy and lane l of a warp reads Gaussian l of a
-// chunk with conflict-free 4-byte shared-memory loads:
+// Repacked Gaussians are stored in chunk blocks of kChunk = 32 slots, one
+// 1184-byte block each, so that a run of chunks is one contiguous 1-D bulk
+// copy and lane l of a warp reads slot l of a chunk with conflict-free 4-byte
+// shared-memory loads.  Slots follow the sort order (grid cell, then a fine
+// Morton code inside the cell), so a chunk's box is small; a cell may be
+// padded to an alignment (see k_pad_counts).
 //   lo  = (min mu over the chunk, max scale over the chunk)
 //   hi  = (max mu over the chunk, 0)
 //   x, y, z          the means
 //   sxx, syy, szz    the covariance diagonal (Eq. 2)
 //   sxy2, sxz2, syz2 the off-diagonals, doubled so d^T Sigma d takes 9 FP32 ops
-// Slots past the last Gaussian hold x = NaN (never a neighbour).
+// Padding slots hold a point at 1e18 with a zero covariance: every pair with
+// it has st2 = +inf (or ~1e36) and adds exactly nothing to any reduction.
 struct __align__(16) ChunkBlock {
     float4 lo;
     float4 hi;
@@ -55,12 +58,14 @@ static_assert(sizeof(ChunkBlock) % 16 == 0, "bulk copies move whole 16-byte unit
 
 struct SceneDev {
     const ChunkBlock *blocks = nullptr;    // [nchunks]
-    const uint32_t *cell_start = nullptr;  // [ncells + 1]: first sorted index of each cell
-    const float *smax = nullptr;           // [n_kept] largest scale per Gaussian (export only)
-    const int32_t *index = nullptr;        // [n_kept] input row per sorted Gaussian (export only)
-    int n_kept = 0;
-    int n_grid = 0;       // [0, n_grid) grid tier, [n_grid, n_kept) large tier
-    int nchunks = 0;
+    const uint32_t *cell_start = nullptr;  // [ncells + 1]: first slot of each cell (multiple of 32)
+    const float *smax = nullptr;           // [n_gauss] largest scale per sorted Gaussian (export only)
+    const int32_t *index = nullptr;        // [n_gauss] input row per sorted Gaussian (export only)
+    const int32_t *slot_of = nullptr;      // [n_gauss] slot of each sorted Gaussian (export only)
+    int n_gauss = 0;      // kept Gaussians
+    int grid_end = 0;     // slots [0, grid_end) hold the grid tier
+    int slot_end = 0;     // slots [grid_end, slot_end) hold the large tier
+    int nchunks = 0;      // ceil(slot_end / 32)
     int dims[3] = {1, 1, 1};
     float lo[3] = {0, 0, 0};   // grid origin
     float h = 1.f, inv_h = 1.f;
@@ -210,6 +215,34 @@ __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Packed FP32x2 arithmetic (sm_100 family): two independent IEEE
+// round-to-nearest operations per instruction, so a packed evaluation gives
+// exactly the bits of two scalar ones.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
 __device__ __forceinline__ float lg2_approx(float x) {

@@ -52,14 +52,24 @@ struct EvalArgs {
     float *grad_centres;     // GRAD: [Q,3]
     unsigned *err;
     unsigned long long *stats;
+    unsigned long long *kstats;  // optional kernel counters (see cs_params.out_kernel_stats)
     long long wait_polls;
 };
 
 // Kernel shape: NCW consumer warps, each owning QW primitives of the tile,
-// plus one producer warp.  Stages hold kCHB chunk blocks.
-constexpr int kNCW = 8;
-constexpr int kNS = 4;      // pipeline stages
-constexpr int kCHB = 16;    // chunk blocks per stage (512 Gaussians)
+// one producer warp, NS pipeline stages of CHB chunk blocks each, and MINB
+// CTAs resident per SM (the register budget follows from it).
+// GROUP (packed sphere-cost path): primitives are evaluated in groups of
+// GROUP whenever any member reaches the chunk (a member that does not adds
+// exactly nothing, st2 > S_cut); larger groups give the scheduler more
+// independent dependency chains per basic block.  GROUP == QW drops the
+// per-primitive test altogether.
+template <int NCW_, int QW_, int NS_, int CHB_, int MINB_, int GROUP_ = 2>
+struct Cfg {
+    static constexpr int NCW = NCW_, QW = QW_, NS = NS_, CHB = CHB_, MINB = MINB_, GROUP = GROUP_;
+    static_assert(CHB <= 32, "one lane tests each chunk slot of a stage");
+    static_assert(QW == 8 || QW == 16, "primitive masks are tested 32 / QW chunks per round");
+};
 
 struct SlotMeta {
     int chunk;  // global chunk id
@@ -73,16 +83,19 @@ struct SlotMeta {
 //   ellipsoid: (c, 2n) (Axx, Ayy, Azz, Axy) (Axz, Ayz, alpha, beta) (live, - - -)
 constexpr int kQRec = 4;
 
-template <int QW>
+template <class C>
 struct __align__(16) EvalSmem {
-    ChunkBlock blk[kNS][kCHB];
-    SlotMeta meta[kNS][kCHB];
-    int count[kNS];
+    ChunkBlock blk[C::NS][C::CHB];
+    SlotMeta meta[C::NS][C::CHB];
+    int count[C::NS];
     int abort;  // an earlier launch on this stream timed out: skip the work
     int pad[3];
-    uint64_t full[kNS];
-    uint64_t empty[kNS];
-    float4 q[kNCW * QW][kQRec];
+    uint64_t full[C::NS];
+    uint64_t empty[C::NS];
+    float4 q[C::NCW * C::QW][kQRec];
+    // spheres, each value duplicated for packed evaluation against two
+    // Gaussians at once: (-cx, -cx, -cy, -cy) (-cz, -cz, 1/r^2, 1/r^2) (-2n, -2n, 0, 0)
+    float4 qd[C::NCW * C::QW][3];
 };
 
 template <int PRIM> struct PrimTraits;
@@ -128,13 +141,14 @@ __device__ __forceinline__ long long globaltimer_ns() {
 
 // Bounded wait by poll count and wall time (1 s; a healthy wait is a few
 // microseconds).
-__device__ __noinline__ bool wait_phase(uint64_t *bar, unsigned parity, long long polls) {
+// Returns the number of polls the wait took, or -1 when it gave up.
+__device__ __noinline__ long long wait_phase(uint64_t *bar, unsigned parity, long long polls) {
     long long t0 = globaltimer_ns();
     for (long long i = 0; i < polls; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return i + 1;
         if ((i & 255) == 255 && globaltimer_ns() - t0 > 1000000000ll) break;
     }
-    return false;
+    return -1;
 }
 
 __device__ __forceinline__ int cell_of(float x, float lo, float inv_h, int dim) {
@@ -143,9 +157,9 @@ __device__ __forceinline__ int cell_of(float x, float lo, float inv_h, int dim) 
 }
 
 // ------------------------------------------------------------- producer
-template <int QW>
+template <class C>
 struct Producer {
-    EvalSmem<QW> *sm;
+    EvalSmem<C> *sm;
     const SceneDev *sc;
     long long polls;
     float lx, ly, lz, hx, hy, hz, al, be;  // tile box and reach parameters
@@ -153,23 +167,32 @@ struct Producer {
     int nslot = 0;   // chunk slots filled in the open stage
     bool failed = false;
     int lane;
+    unsigned long long n_chunks = 0, n_polls = 0, n_wait_cycles = 0, t_first = 0;
+    long long t0 = 0;
 
     __device__ void open_stage() {
-        int s = k % kNS;
-        if (k >= kNS) {
+        int s = k % C::NS;
+        if (k >= C::NS) {
             bool ok = true;
-            if (lane == 0) ok = wait_phase(&sm->empty[s], (unsigned)((k / kNS - 1) & 1), polls);
+            if (lane == 0) {
+                const long long c0 = clock64();
+                const long long w = wait_phase(&sm->empty[s], (unsigned)((k / C::NS - 1) & 1), polls);
+                n_wait_cycles += (unsigned long long)(clock64() - c0);
+                ok = w >= 0;
+                n_polls += ok ? (unsigned long long)w : 0ull;
+            }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) failed = true;
         }
         nslot = 0;
     }
     __device__ void close_stage() {
-        int s = k % kNS;
+        int s = k % C::NS;
         __syncwarp();  // slot metadata written by other lanes before the release
         if (lane == 0) {
             sm->count[s] = nslot;
             mbar_arrive(&sm->full[s]);
+            if (k == 0) t_first = (unsigned long long)(clock64() - t0);
         }
         __syncwarp();
         ++k;
@@ -179,8 +202,8 @@ struct Producer {
     // [s, e) of the stream.
     __device__ void emit_run(int c, int len, int s, int e) {
         while (len > 0 && !failed) {
-            const int st = k % kNS;
-            const int take = min(len, kCHB - nslot);
+            const int st = k % C::NS;
+            const int take = min(len, C::CHB - nslot);
             if (lane < take) {
                 int cc = c + lane;
                 sm->meta[st][nslot + lane] = SlotMeta{cc, max(s - cc * kChunk, 0),
@@ -192,9 +215,10 @@ struct Producer {
                 bulk_g2s(&sm->blk[st][nslot], sc->blocks + c, bytes, &sm->full[st]);
             }
             nslot += take;
+            n_chunks += (unsigned long long)take;
             c += take;
             len -= take;
-            if (nslot == kCHB) close_stage();
+            if (nslot == C::CHB) close_stage();
         }
     }
     // Every chunk overlapping sorted Gaussians [s, e) (a grid row span: the
@@ -246,7 +270,7 @@ struct Producer {
         if (failed) return;
         if (nslot > 0) close_stage();
         if (failed) return;
-        int s = k % kNS;
+        int s = k % C::NS;
         if (lane == 0) {
             sm->count[s] = 0;  // terminator
             mbar_arrive(&sm->full[s]);
@@ -258,24 +282,25 @@ struct Producer {
     __device__ void drain() {
         __syncwarp();
         if (lane == 0) {
-            int s = k % kNS;
+            int s = k % C::NS;
             if (nslot > 0) {
                 sm->count[s] = nslot;
                 mbar_arrive(&sm->full[s]);
                 ++k;
             }
-            for (int j = max(0, k - kNS); j < k; ++j)
-                wait_phase(&sm->full[j % kNS], (unsigned)((j / kNS) & 1), polls);
+            for (int j = max(0, k - C::NS); j < k; ++j)
+                wait_phase(&sm->full[j % C::NS], (unsigned)((j / C::NS) & 1), polls);
         }
         __syncwarp();
     }
 };
 
-template <int PRIM, int QW>
-__device__ void producer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile) {
+template <int PRIM, class C>
+__device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
-    constexpr int TQ = kNCW * QW;
+    constexpr int TQ = C::NCW * C::QW;
     const int lane = threadIdx.x & 31;
+    const long long t_start = clock64();
     const SceneDev &sc = a.sc;
     float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY,
           hz = -INFINITY, al = 0.f, be = 0.f;
@@ -304,10 +329,11 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile) {
         al = fmaxf(al, __shfl_xor_sync(0xffffffffu, al, o));
         be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
     }
-    Producer<QW> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
+    Producer<C> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
     pr.lane = lane;
+    pr.t0 = t_start;
     const bool any = lx <= hx;  // at least one valid primitive
-    if (any && sc.n_grid > 0) {
+    if (any && sc.grid_end > 0) {
         // ---- grid rows within reach of the tile box (sigma = grid-tier max)
         const float R = reach(al, be, sc.sigma_tier, sc.pad_abs);
         const float R2 = R * R;
@@ -374,11 +400,20 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile) {
             }
         }
     }
-    if (any && sc.n_kept > sc.n_grid && !pr.failed) pr.append_tested(sc.n_grid, sc.n_kept);  // large tier
+    if (any && sc.slot_end > sc.grid_end && !pr.failed) pr.append_tested(sc.grid_end, sc.slot_end);  // large tier
     pr.finish();
     if (pr.failed) {
         if (lane == 0) atomicOr(a.err, kErrTimeout);
         pr.drain();
+    }
+    if (a.kstats && lane == 0) {
+        atomicAdd(a.kstats + 4, pr.n_chunks);
+        atomicAdd(a.kstats + 5, (unsigned long long)pr.k);
+        atomicAdd(a.kstats + 7, pr.n_polls);
+        atomicAdd(a.kstats + 10, (unsigned long long)(clock64() - t_start));
+        atomicAdd(a.kstats + 11, pr.n_wait_cycles);
+        atomicAdd(a.kstats + 13, pr.t_first);
+        atomicAdd(a.kstats + 15, 1ull);
     }
 }
 
@@ -390,7 +425,8 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile) {
 // whatever the tile: results do not depend on which rows share the launch.
 template <int PRIM, int QW, int MODE, bool GRAD>
 struct Acc {
-    float sumb[(MODE == 0 && !GRAD) ? QW : 1];  // cost partial over the current chunk group
+    // cost partial over the current chunk group (ellipsoids; spheres sum directly)
+    float sumb[(MODE == 0 && !GRAD && PRIM == 1) ? QW : 1];
     float sum[(MODE == 0 && !GRAD) ? QW : 1];
     float mn[(MODE == 1) ? QW : 1];
     float sm_m[(MODE == 2) ? QW : 1];
@@ -466,7 +502,10 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
     A.cnt[j] += nb ? 1 : 0;
     if (!GRAD) {
         A.cin[j] += (st2 < k.T_in) ? 1 : 0;
-        if (MODE == 0) A.sumb[j] += nb ? dc : 0.f;
+        if (MODE == 0) {
+            if (PRIM == 1) A.sumb[j] += nb ? dc : 0.f;
+            else A.sum[j] += nb ? dc : 0.f;
+        }
         if (MODE == 1) A.mn[j] = fminf(A.mn[j], st2);
         if (MODE == 2) {
             const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
@@ -532,10 +571,154 @@ __device__ __forceinline__ bool reaches(const float4 *qd, const float4 &blo, con
     return live != 0.f && box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) <= R * R;
 }
 
+// Lane-local Gaussian duplicated into both halves of packed registers.
+struct LaneG2 {
+    f32x2 x, y, z, sxx, syy, szz, sxy2, sxz2, syz2;
+};
+
+// One sphere (cost reductions, forward) against the lane's two Gaussians
+// (one from each chunk of a chunk pair), with the geometry of Eq. 5, 7, 8 and
+// the Eq. 11 exponent in packed FP32x2: the same operations in the same
+// order as pair_update, hence the same bits; half 0 is accumulated before
+// half 1, so each lane still adds its Gaussians in increasing order.
+template <int QW>
+__device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, const LaneG2 &g,
+                                               const float4 *qd, const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
+    const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&qd[0]);  // -cx, -cy
+    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
+    const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
+    const f32x2 dx = add2(g.x, pa.x), dy = add2(g.y, pa.y), dz = add2(g.z, pb.x);
+    const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    const f32x2 t1 = fma2(g.sxz2, dz, fma2(g.sxy2, dy, mul2(g.sxx, dx)));
+    const f32x2 t2 = fma2(g.syz2, dz, mul2(g.syy, dy));
+    const f32x2 u = fma2(dx, t1, fma2(dy, t2, mul2(dz, mul2(g.szz, dz))));
+    float u0, u1;
+    upk2(u, u0, u1);
+    const f32x2 sq = pk2(sqrt_approx(fmaxf(u0, 0.f)), sqrt_approx(fmaxf(u1, 0.f)));
+    float r0, r1;
+    upk2(fma2(nns2, sq, r2), r0, r1);
+    const f32x2 st = mul2(pk2(fmaxf(r0, 0.f), fmaxf(r1, 0.f)), pb.y);
+    float e0, e1, s0, s1;
+    upk2(fma2(st, nG2, Gs2), e0, e1);
+    upk2(st, s0, s1);
+    const float dc0 = ex2_approx(fminf(e0, 0.f)), dc1 = ex2_approx(fminf(e1, 0.f));
+    const bool nb0 = s0 <= k.S_cut, nb1 = s1 <= k.S_cut;
+    A.cnt[j] += (nb0 ? 1 : 0) + (nb1 ? 1 : 0);
+    A.cin[j] += ((s0 < k.T_in) ? 1 : 0) + ((s1 < k.T_in) ? 1 : 0);
+    A.sum[j] += nb0 ? dc0 : 0.f;
+    A.sum[j] += nb1 ? dc1 : 0.f;
+}
+
+// Lane l of a chunk slot: Gaussian l when the slot's range holds it, else a
+// point that meets no primitive.
+__device__ __forceinline__ void lane_gaussian(const ChunkBlock &B, const SlotMeta mt, int lane, LaneG &g) {
+    if (mt.lo == 0 && mt.hi == kChunk) {
+        g.x = B.x[lane]; g.y = B.y[lane]; g.z = B.z[lane];
+        g.sxx = B.sxx[lane]; g.syy = B.syy[lane]; g.szz = B.szz[lane];
+        g.sxy2 = B.sxy2[lane]; g.sxz2 = B.sxz2[lane]; g.syz2 = B.syz2[lane];
+    } else {
+        const bool lv = lane >= mt.lo && lane < mt.hi;
+        g.x = lv ? B.x[lane] : 1e18f;
+        g.y = lv ? B.y[lane] : 1e18f;
+        g.z = lv ? B.z[lane] : 1e18f;
+        g.sxx = lv ? B.sxx[lane] : 0.f;
+        g.syy = lv ? B.syy[lane] : 0.f;
+        g.szz = lv ? B.szz[lane] : 0.f;
+        g.sxy2 = lv ? B.sxy2[lane] : 0.f;
+        g.sxz2 = lv ? B.sxz2[lane] : 0.f;
+        g.syz2 = lv ? B.syz2[lane] : 0.f;
+    }
+}
+
+// Two staged chunks (B1 may be absent, mt1.hi == 0) against the spheres of
+// `qmask` (the primitives reaching either chunk): lane l holds Gaussian l of
+// each chunk in the two halves of packed registers; spheres are evaluated in
+// groups of GROUP (a member reaching neither chunk adds exactly nothing).
+template <int QW, int GROUP>
+__device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, const SlotMeta mt0,
+                                                const ChunkBlock &B1, const SlotMeta mt1, unsigned qmask,
+                                                float4 (*wqd)[3], const QueryConsts &k, int lane,
+                                                unsigned long long &cand, unsigned long long &c_hits) {
+    if (qmask == 0u) return;
+    LaneG g0, g1;
+    lane_gaussian(B0, mt0, lane, g0);
+    lane_gaussian(B1, mt1, lane, g1);
+    LaneG2 g2;
+    g2.x = pk2(g0.x, g1.x); g2.y = pk2(g0.y, g1.y); g2.z = pk2(g0.z, g1.z);
+    g2.sxx = pk2(g0.sxx, g1.sxx); g2.syy = pk2(g0.syy, g1.syy); g2.szz = pk2(g0.szz, g1.szz);
+    g2.sxy2 = pk2(g0.sxy2, g1.sxy2); g2.sxz2 = pk2(g0.sxz2, g1.sxz2); g2.syz2 = pk2(g0.syz2, g1.syz2);
+    const f32x2 nG2 = pk2(-k.G, -k.G), Gs2 = pk2(k.Gsmin, k.Gsmin);
+    const unsigned long long lanes_evaluated = (unsigned long long)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo));
+    constexpr unsigned GMASK = (1u << GROUP) - 1u;
+#pragma unroll
+    for (int j0 = 0; j0 < QW; j0 += GROUP) {
+        if ((qmask >> j0) & GMASK) {
+            c_hits += (unsigned long long)GROUP;
+            cand += (unsigned long long)GROUP * lanes_evaluated;
+#pragma unroll
+            for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW>(A, j, g2, wqd[j], k, nG2, Gs2);
+        }
+    }
+}
+
+// One staged chunk against the primitives of `qmask`: lane l takes Gaussian
+// l of the chunk (lanes outside the staged range hold a point that meets no
+// primitive), then the primitives are evaluated two per basic block.
 template <int PRIM, int QW, int MODE, bool GRAD>
-__device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int warp, bool abort) {
+__device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const ChunkBlock &B, const SlotMeta &mt,
+                                           unsigned qmask, float4 (*wq)[kQRec], const QueryConsts &k, int lane,
+                                           int &group, unsigned long long &cand, unsigned long long &c_hits) {
+    if (qmask == 0u) return;
+    c_hits += (unsigned long long)__popc(qmask);
+    if (MODE == 0 && !GRAD && PRIM == 1) {
+        // fixed grouping of the cost partials (16 chunks) keeps the
+        // summation order independent of the tile
+        const int grp = mt.chunk >> 4;
+        if (grp != group) {
+#pragma unroll
+            for (int j = 0; j < QW; ++j) { A.sum[j] += A.sumb[j]; A.sumb[j] = 0.f; }
+            group = grp;
+        }
+    }
+    LaneG g;
+    if (mt.lo == 0 && mt.hi == kChunk) {  // whole chunk (the common case)
+        g.x = B.x[lane]; g.y = B.y[lane]; g.z = B.z[lane];
+        g.sxx = B.sxx[lane]; g.syy = B.syy[lane]; g.szz = B.szz[lane];
+        g.sxy2 = B.sxy2[lane]; g.sxz2 = B.sxz2[lane]; g.syz2 = B.syz2[lane];
+    } else {
+        const bool lv = lane >= mt.lo && lane < mt.hi;
+        g.x = lv ? B.x[lane] : 1e18f;
+        g.y = lv ? B.y[lane] : 1e18f;
+        g.z = lv ? B.z[lane] : 1e18f;
+        g.sxx = lv ? B.sxx[lane] : 0.f;
+        g.syy = lv ? B.syy[lane] : 0.f;
+        g.szz = lv ? B.szz[lane] : 0.f;
+        g.sxy2 = lv ? B.sxy2[lane] : 0.f;
+        g.sxz2 = lv ? B.sxz2[lane] : 0.f;
+        g.syz2 = lv ? B.syz2[lane] : 0.f;
+    }
+    cand += (unsigned long long)__popc(qmask) * (unsigned long long)(mt.hi - mt.lo);
+    {
+#pragma unroll
+        for (int j = 0; j < QW; j += 2) {
+            const bool p0 = (qmask >> j) & 1u, p1 = (qmask >> (j + 1)) & 1u;
+            if (p0 && p1) {
+                pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
+                pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+            } else if (p0) {
+                pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
+            } else if (p1) {
+                pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+            }
+        }
+    }
+}
+
+template <int PRIM, class C, int MODE, bool GRAD>
+__device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int warp, bool abort) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
-    constexpr int TQ = kNCW * QW;
+    constexpr int QW = C::QW;
+    constexpr int TQ = C::NCW * QW;
     const int lane = threadIdx.x & 31;
     const QueryConsts &k = a.k;
     const SceneDev &sc = a.sc;
@@ -572,6 +755,14 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
     }
     nvalid = __reduce_add_sync(0xffffffffu, nvalid);
     __syncwarp();
+    float4(*wqd)[3] = &sm->qd[warp * QW];
+    if (PRIM == 0 && lane < QW) {
+        const float4 a = wq[lane][0], b = wq[lane][1];
+        wqd[lane][0] = make_float4(-a.x, -a.x, -a.y, -a.y);
+        wqd[lane][1] = make_float4(-a.z, -a.z, a.w, a.w);
+        wqd[lane][2] = make_float4(-b.x, -b.x, 0.f, 0.f);
+    }
+    __syncwarp();
     // the warp's box of primitive centres and its largest reach parameters:
     // a chunk outside box + reach is out of reach of every primitive here
     float wlx = INFINITY, wly = INFINITY, wlz = INFINITY, whx = -INFINITY, why = -INFINITY, whz = -INFINITY;
@@ -603,22 +794,35 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
     for (int j = 0; j < QW; ++j) {
         A.cnt[j] = 0;
         if (!GRAD) A.cin[j] = 0;
-        if (MODE == 0 && !GRAD) { A.sumb[j] = 0.f; A.sum[j] = 0.f; }
+        if (MODE == 0 && !GRAD) { A.sum[j] = 0.f; if (PRIM == 1) A.sumb[j] = 0.f; }
         if (MODE == 1) A.mn[j] = INFINITY;
         if (MODE == 2) { A.sm_m[j] = k.S_cut; A.sm_acc[j] = 0.f; }
         if (GRAD) { A.gx[j] = 0.f; A.gy[j] = 0.f; A.gz[j] = 0.f; }
     }
     unsigned long long cand = 0;  // (primitive, Gaussian) pairs evaluated
+    unsigned long long c_stages = 0, c_tested = 0, c_pass = 0, c_hits = 0, c_polls = 0;
+    unsigned long long c_wait = 0, c_first = 0;
+    const long long c_start = clock64();
     int group = -1;               // chunk group of the cost partials
     bool ok = !abort;
     for (int kk = 0; ok; ++kk) {
-        const int s = kk % kNS;
+        const int s = kk % C::NS;
         bool got = true;
-        if (lane == 0) got = wait_phase(&sm->full[s], (unsigned)((kk / kNS) & 1), a.wait_polls);
+        if (lane == 0) {
+            const long long c0 = clock64();
+            const long long w = wait_phase(&sm->full[s], (unsigned)((kk / C::NS) & 1), a.wait_polls);
+            const long long c1 = clock64();
+            c_wait += (unsigned long long)(c1 - c0);
+            if (kk == 0) c_first = (unsigned long long)(c1 - c_start);
+            got = w >= 0;
+            c_polls += got ? (unsigned long long)w : 0ull;
+        }
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) { ok = false; break; }
         const int nslots = sm->count[s];
         if (nslots == 0) break;
+        ++c_stages;
+        c_tested += (unsigned long long)nslots;
         if (nvalid > 0) {
             // lane t tests chunk slot t against the warp's box + reach
             bool wpass = false;
@@ -628,51 +832,45 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
                 wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
             }
             unsigned cmask = __ballot_sync(0xffffffffu, wpass);
+            c_pass += (unsigned long long)__popc(cmask);
+            constexpr int CPR = 32 / QW;  // chunks whose primitive tests share one round
+            constexpr unsigned QMASK = (1u << QW) - 1u;
             while (cmask) {
-                const int slot = __ffs(cmask) - 1;
+                const int s0 = __ffs(cmask) - 1;
                 cmask &= cmask - 1;
-                const SlotMeta mt = sm->meta[s][slot];
-                const ChunkBlock &B = sm->blk[s][slot];
-                const float4 blo = B.lo, bhi = B.hi;
-                // lane j tests primitive j against the chunk
-                const bool qp = lane < QW && reaches<PRIM>(wq[lane], blo, bhi, sc.pad_abs);
-                const unsigned qmask = __ballot_sync(0xffffffffu, qp);
-                if (qmask == 0u) continue;
-                if (MODE == 0 && !GRAD) {
-                    // fixed grouping of the cost partials (16 chunks) keeps
-                    // the summation order independent of the tile
-                    const int grp = mt.chunk >> 4;
-                    if (grp != group) {
-#pragma unroll
-                        for (int j = 0; j < QW; ++j) { A.sum[j] += A.sumb[j]; A.sumb[j] = 0.f; }
-                        group = grp;
+                int s1 = -1, s2 = -1, s3 = -1;
+                if (CPR > 1 && cmask) { s1 = __ffs(cmask) - 1; cmask &= cmask - 1; }
+                if (CPR > 2 && cmask) { s2 = __ffs(cmask) - 1; cmask &= cmask - 1; }
+                if (CPR > 3 && cmask) { s3 = __ffs(cmask) - 1; cmask &= cmask - 1; }
+                // lane l tests primitive l % QW against the chunk of round slot l / QW
+                const int part = lane / QW;
+                const int my = part == 0 ? s0 : part == 1 ? s1 : part == 2 ? s2 : s3;
+                bool qp = false;
+                if (my >= 0) qp = reaches<PRIM>(wq[lane % QW], sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs);
+                const unsigned hits = __ballot_sync(0xffffffffu, qp);
+                if constexpr (PRIM == 0 && MODE == 0 && !GRAD) {
+                    // spheres, cost reductions: chunks of the round in pairs, two
+                    // Gaussians per lane in packed registers
+#pragma unroll 1
+                    for (int r = 0; r < CPR; r += 2) {
+                        const int sa = r == 0 ? s0 : s2, sb = r == 0 ? s1 : s3;
+                        if (sa < 0) break;
+                        const unsigned qa = (hits >> (r * QW)) & QMASK;
+                        const unsigned qb = sb >= 0 ? (hits >> ((r + 1) * QW)) & QMASK : 0u;
+                        eval_chunk_pair<QW, C::GROUP>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
+                                                      sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd,
+                                                      k, lane, cand,
+                                                      c_hits);
                     }
-                }
-                const bool lv = lane >= mt.lo && lane < mt.hi;
-                LaneG g;
-                g.x = lv ? B.x[lane] : 1e18f;
-                g.y = lv ? B.y[lane] : 1e18f;
-                g.z = lv ? B.z[lane] : 1e18f;
-                g.sxx = lv ? B.sxx[lane] : 0.f;
-                g.syy = lv ? B.syy[lane] : 0.f;
-                g.szz = lv ? B.szz[lane] : 0.f;
-                g.sxy2 = lv ? B.sxy2[lane] : 0.f;
-                g.sxz2 = lv ? B.sxz2[lane] : 0.f;
-                g.syz2 = lv ? B.syz2[lane] : 0.f;
-                cand += (unsigned long long)__popc(qmask) * (unsigned long long)(mt.hi - mt.lo);
-#pragma unroll
-                for (int j = 0; j < QW; j += 2) {
-                    // two primitives per step: when both reach the chunk their
-                    // pair updates share one basic block (two independent
-                    // dependency chains for the scheduler)
-                    const bool p0 = (qmask >> j) & 1u, p1 = (qmask >> (j + 1)) & 1u;
-                    if (p0 && p1) {
-                        pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
-                        pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
-                    } else if (p0) {
-                        pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
-                    } else if (p1) {
-                        pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+                } else {
+                    // one inlined copy of the chunk body for the CPR chunks of the round
+#pragma unroll 1
+                    for (int r = 0; r < CPR; ++r) {
+                        const int sl = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
+                        if (sl < 0) break;
+                        eval_chunk<PRIM, QW, MODE, GRAD>(A, sm->blk[s][sl], sm->meta[s][sl],
+                                                         (hits >> (r * QW)) & QMASK, wq, k, lane, group, cand,
+                                                         c_hits);
                     }
                 }
             }
@@ -681,6 +879,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
         if (lane == 0) mbar_arrive(&sm->empty[s]);
     }
     if (!ok && !abort && lane == 0) atomicOr(a.err, kErrTimeout);
+    const long long c_loop_end = clock64();
 
     // ---- reductions across lanes (fixed trees) and outputs
     unsigned long long nb_total = 0;
@@ -693,7 +892,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
             const int cinj = __reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
             float metric = 0.f;
             if (MODE == 0) {
-                const float tot = warp_sum(A.sum[j] + A.sumb[j]);
+                const float tot = warp_sum(PRIM == 1 ? A.sum[j] + A.sumb[j] : A.sum[j]);
                 metric = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? tot * k.d_max / (float)cntj : 0.f)
                                                          : tot * k.d_max;
             } else if (MODE == 1) {
@@ -744,23 +943,35 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<QW> *sm, int tile, int
                 a.grad_centres[3 * (size_t)row + 2] = good ? gz * f * up : nanv;
             }
         }
-        nb_total += (unsigned long long)cntj;
+        if (vq) nb_total += (unsigned long long)cntj;
     }
     if (a.stats && lane == 0) {
         atomicAdd(a.stats + 0, cand);
         atomicAdd(a.stats + 1, nb_total);
     }
+    if (a.kstats && lane == 0) {
+        atomicAdd(a.kstats + 0, c_stages);
+        atomicAdd(a.kstats + 1, c_tested);
+        atomicAdd(a.kstats + 2, c_pass);
+        atomicAdd(a.kstats + 3, c_hits);
+        atomicAdd(a.kstats + 6, c_polls);
+        const long long c_end = clock64();
+        atomicAdd(a.kstats + 8, (unsigned long long)(c_end - c_start));
+        atomicAdd(a.kstats + 9, c_wait);
+        atomicAdd(a.kstats + 12, c_first);
+        atomicAdd(a.kstats + 14, (unsigned long long)(c_end - c_loop_end));
+    }
 }
 
-template <int PRIM, int QW, int MODE, bool GRAD>
-__global__ void __launch_bounds__((kNCW + 1) * 32, (GRAD || QW > 8) ? 1 : 2) k_eval(const EvalArgs a) {
+template <int PRIM, class C, int MODE, bool GRAD>
+__global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    EvalSmem<QW> *sm = reinterpret_cast<EvalSmem<QW> *>(smem_raw);
+    EvalSmem<C> *sm = reinterpret_cast<EvalSmem<C> *>(smem_raw);
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kNS; ++s) {
+        for (int s = 0; s < C::NS; ++s) {
             mbar_init(&sm->full[s], 1);
-            mbar_init(&sm->empty[s], kNCW);
+            mbar_init(&sm->empty[s], C::NCW);
         }
         fence_mbar_init();
         sm->abort = (*(volatile unsigned *)a.err & kErrTimeout) ? 1 : 0;
@@ -768,10 +979,10 @@ __global__ void __launch_bounds__((kNCW + 1) * 32, (GRAD || QW > 8) ? 1 : 2) k_e
     __syncthreads();
     const int tile = blockIdx.x;
     const bool abort = sm->abort != 0;
-    if (warp == kNCW) {
-        if (!abort) producer_warp<PRIM, QW>(a, sm, tile);
+    if (warp == C::NCW) {
+        if (!abort) producer_warp<PRIM, C>(a, sm, tile);
     } else {
-        consumer_warp<PRIM, QW, MODE, GRAD>(a, sm, tile, warp, abort);
+        consumer_warp<PRIM, C, MODE, GRAD>(a, sm, tile, warp, abort);
     }
 }
 
@@ -898,64 +1109,80 @@ QueryConsts make_consts(const cs_params &p) {
 }
 
 
-struct TileCfg {
-    int id;
-    int qw;  // primitives per consumer warp
-};
-// ids: 1 = 8 primitives per warp (64 per tile, two tiles per SM),
-//      2 = 16 (128 per tile, one tile per SM)
-static const TileCfg kTileCfgs[] = {{1, 8}, {2, 16}};
+// Tile shapes (cs_tile_configs):
+//   1: 8 consumer warps x 8 primitives, 4 stages x 16 chunks, 2 CTAs/SM (default)
+//   2: 8 x 16, 4 x 16, 1 CTA/SM
+//   3: 4 x 8, 3 x 8, 4 CTAs/SM
+//   4: 4 x 16, 3 x 8, 3 CTAs/SM
+//   5-8: shapes 1, 1, 4, 4 evaluating sphere primitives in groups of 4, 8, 4, 8
+using Cfg1 = Cfg<8, 8, 4, 16, 2>;
+using Cfg2 = Cfg<8, 16, 4, 16, 1>;
+using Cfg3 = Cfg<4, 8, 3, 8, 4>;
+using Cfg4 = Cfg<4, 16, 3, 8, 3>;
+using Cfg5 = Cfg<8, 8, 4, 16, 2, 4>;
+using Cfg6 = Cfg<8, 8, 4, 16, 2, 8>;
+using Cfg7 = Cfg<4, 16, 3, 8, 3, 4>;
+using Cfg8 = Cfg<4, 16, 3, 8, 3, 8>;
+using CfgGrad = Cfg<4, 8, 3, 8, 3>;  // the adjoint keeps three gradient sums per primitive
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8};
+constexpr int kDefaultTile = 1;
 
 int tile_configs(int32_t *ids, int32_t cap) {
-    int n = (int)(sizeof(kTileCfgs) / sizeof(kTileCfgs[0]));
-    for (int i = 0; i < n && i < cap; ++i) ids[i] = kTileCfgs[i].id;
+    int n = (int)(sizeof(kTileIds) / sizeof(kTileIds[0]));
+    for (int i = 0; i < n && i < cap; ++i) ids[i] = kTileIds[i];
     return n;
 }
 
-template <int PRIM, int QW, int MODE, bool GRAD>
+template <int PRIM, class C, int MODE, bool GRAD>
 static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
-    constexpr int TQ = kNCW * QW;
+    constexpr int TQ = C::NCW * C::QW;
     const int ntiles = (a.Q + TQ - 1) / TQ;
-    const size_t smem = sizeof(EvalSmem<QW>);
-    auto kern = k_eval<PRIM, QW, MODE, GRAD>;
+    const size_t smem = sizeof(EvalSmem<C>);
+    auto kern = k_eval<PRIM, C, MODE, GRAD>;
     static bool attr = false;  // once per instantiation (idempotent)
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    kern<<<ntiles, (kNCW + 1) * 32, smem, s>>>(a);
+    kern<<<ntiles, (C::NCW + 1) * 32, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int PRIM, int QW>
-static cudaError_t launch_eval_qw(const EvalArgs &a, bool grad, cudaStream_t s) {
+template <int PRIM, class C>
+static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
     const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
-    if (grad) {
-        if (mode == 0) return launch_eval_t<PRIM, 8, 0, true>(a, s);
-        if (mode == 1) return launch_eval_t<PRIM, 8, 1, true>(a, s);
-        return launch_eval_t<PRIM, 8, 2, true>(a, s);
-    }
-    if (mode == 0) return launch_eval_t<PRIM, QW, 0, false>(a, s);
-    if (mode == 1) return launch_eval_t<PRIM, QW, 1, false>(a, s);
-    return launch_eval_t<PRIM, QW, 2, false>(a, s);
+    if (mode == 0) return launch_eval_t<PRIM, C, 0, false>(a, s);
+    if (mode == 1) return launch_eval_t<PRIM, C, 1, false>(a, s);
+    return launch_eval_t<PRIM, C, 2, false>(a, s);
 }
 
-static int choose_qw(int Q, int tile_cfg, int num_sms) {
-    for (const TileCfg &t : kTileCfgs)
-        if (t.id == tile_cfg) return t.qw;
-    (void)Q;
-    (void)num_sms;
-    return 8;  // automatic: two 64-primitive tiles per SM
+template <int PRIM>
+static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStream_t s) {
+    if (grad) {
+        const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
+        if (mode == 0) return launch_eval_t<PRIM, CfgGrad, 0, true>(a, s);
+        if (mode == 1) return launch_eval_t<PRIM, CfgGrad, 1, true>(a, s);
+        return launch_eval_t<PRIM, CfgGrad, 2, true>(a, s);
+    }
+    switch (tile) {
+        case 2: return launch_mode<PRIM, Cfg2>(a, s);
+        case 3: return launch_mode<PRIM, Cfg3>(a, s);
+        case 4: return launch_mode<PRIM, Cfg4>(a, s);
+        case 5: return launch_mode<PRIM, Cfg5>(a, s);
+        case 6: return launch_mode<PRIM, Cfg6>(a, s);
+        case 7: return launch_mode<PRIM, Cfg7>(a, s);
+        case 8: return launch_mode<PRIM, Cfg8>(a, s);
+        default: return launch_mode<PRIM, Cfg1>(a, s);
+    }
 }
 
 cudaError_t launch_eval(int prim_type, const EvalArgs &a, bool grad, int tile_cfg, int num_sms,
                         cudaStream_t s) {
-    const int qw = choose_qw(a.Q, tile_cfg, num_sms);
-    if (prim_type == CS_PRIM_SPHERE)
-        return qw == 16 ? launch_eval_qw<0, 16>(a, grad, s) : launch_eval_qw<0, 8>(a, grad, s);
-    return qw == 16 ? launch_eval_qw<1, 16>(a, grad, s) : launch_eval_qw<1, 8>(a, grad, s);
+    (void)num_sms;
+    const int tile = tile_cfg ? tile_cfg : kDefaultTile;
+    return prim_type == CS_PRIM_SPHERE ? launch_prim<0>(a, grad, tile, s) : launch_prim<1>(a, grad, tile, s);
 }
 
 cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, const float *qns,
@@ -977,6 +1204,7 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
     a.grad_centres = grad_centres;
     a.err = err;
     a.stats = p.out_pair_stats;
+    a.kstats = p.out_kernel_stats;
     a.wait_polls = polls;
     cudaError_t e;
     if (p.eval_events[0] && (e = cudaEventRecord((cudaEvent_t)p.eval_events[0], s)) != cudaSuccess) return e;
@@ -992,7 +1220,7 @@ __global__ void k_wait_selftest(long long polls, unsigned *err) {
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
-        if (!wait_phase(&bar, 0u, polls)) atomicOr(err, kErrTimeout);
+        if (wait_phase(&bar, 0u, polls) < 0) atomicOr(err, kErrTimeout);
     }
 }
 

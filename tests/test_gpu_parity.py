@@ -52,7 +52,7 @@ def test_tiny_scene_all_modes(cs, nsigma, mode):
     assert rep["checked"] > 0.9 * rep["Q"]
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4])
 @pytest.mark.parametrize("Q", [1, 37, 1000, 5000])
 def test_tile_configs_and_ragged_batches(cs, cfg, Q):
     """Every tile shape, batch sizes spanning one to many tiles with a ragged tail."""
@@ -83,7 +83,7 @@ def test_ellipsoids(cs, mode):
     centres = rng.uniform(0, 2, (600, 3))
     e = S.ellipsoid_queries(5, centres)
     scene = _scene(cs, sc)
-    for cfg in (1, 2):
+    for cfg in (1, 2, 3, 4):
         out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode, tile_config=cfg)
         compare(out, oracle.query(sc, e, 1, 1.0), mode, oracle.Params(), f"ellipsoid mode={mode}")
 
