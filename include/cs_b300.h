@@ -97,6 +97,8 @@ typedef struct cs_scene_desc {
                                the separately culled large tier; 0 = default 0.99 */
 } cs_scene_desc;
 
+#define CS_TILE_TUNED (-1)
+
 /* Per-call parameters for cs_query / cs_query_grad.  Initialise with
  * cs_params_init; every pointer member may be NULL. */
 typedef struct cs_params {
@@ -113,7 +115,10 @@ typedef struct cs_params {
     int32_t host_io;           /* 1: prims, nsigma_per_query, grad_out and every output are
                                   host pointers; the call copies in, computes, copies out and
                                   returns after the stream has finished */
-    int32_t tile_config;       /* 0 = automatic; otherwise a value from cs_tile_configs */
+    int32_t tile_config;       /* 0 = the default shape; CS_TILE_TUNED = the shape cs_autotune
+                                  chose for this scene, primitive type, mode and batch-size
+                                  class (the default when none was tuned); otherwise a value
+                                  from cs_tile_configs */
     const float *nsigma_per_query; /* [Q] n_sigma per row (overrides the scalar), each >= 0 */
     void *stream;              /* cudaStream_t */
     int32_t *out_count;        /* [Q] |N_j| per row */
@@ -252,6 +257,143 @@ CS_API cs_status cs_sync(const cs_scene *scene, void *stream);
 /* Tile configurations available to cs_params.tile_config: writes up to `cap`
  * ids to `ids` and returns how many exist. */
 CS_API int32_t cs_tile_configs(int32_t *ids, int32_t cap);
+
+/* ------------------------------------------------------------------------
+ * Captured query graphs.  The paper has no counterpart: this is launch
+ * machinery for callers that repeat one query shape (an MPPI or optimiser
+ * loop rewriting its primitives in place).
+ *
+ * cs_graph_create captures one cs_query call (grad_centres == NULL) or one
+ * cs_query_grad call (grad_centres != NULL; out_metric and out_collide must
+ * then be NULL) with the given device buffers into a CUDA graph.
+ * cs_graph_launch replays it on `stream`, reading whatever the buffers hold
+ * when it runs.  Arguments mean what they mean for cs_query / cs_query_grad;
+ * every pointer is a device pointer (params->host_io must be 0) and
+ * params->stream, params->eval_events are ignored.  The graph owns private
+ * query scratch, so distinct graphs may run concurrently on different
+ * streams; CUDA orders the launches of one graph.  The scene and every
+ * buffer must outlive the graph.  Errors: the argument errors of cs_query,
+ * CS_ERR_CUDA when capture or instantiation fails, CS_ERR_NO_MEMORY. */
+typedef struct cs_graph cs_graph;
+
+CS_API cs_status cs_graph_create(const cs_scene *scene, int32_t prim_type, const float *prims,
+                                 int64_t Q, float conservatism, float *out_metric,
+                                 uint8_t *out_collide, const float *grad_out, float *grad_centres,
+                                 const cs_params *params, cs_graph **out);
+CS_API cs_status cs_graph_launch(cs_graph *graph, void *stream);
+/* Wait for `stream`, then report and clear the device-side conditions of
+ * the graph's launches, as cs_sync does for a stream. */
+CS_API cs_status cs_graph_sync(cs_graph *graph, void *stream);
+/* Kernels one launch of the graph runs (also added to cs_launch_count by
+ * every cs_graph_launch); -1 for an invalid handle. */
+CS_API int64_t cs_graph_kernels(const cs_graph *graph);
+/* Free the graph and its scratch; no launch of it may be in flight.  NULL
+ * is a no-op. */
+CS_API cs_status cs_graph_destroy(cs_graph *graph);
+
+/* Tile autotuner.  The paper has no counterpart.  Runs the fused kernel of
+ * cs_query on this batch (device pointers, as cs_query with host_io = 0)
+ * with every tile configuration, one warm-up launch then `reps` (>= 1)
+ * launches each timed with CUDA events on params->stream, and records the
+ * fastest for (scene, prim_type, params->mode, floor(log2 Q)); calls with
+ * tile_config = CS_TILE_TUNED then use it.  Writes the chosen id to *best
+ * and, when ms is not NULL, the mean milliseconds per launch of the first
+ * `cap` configurations in the order cs_tile_configs lists them.  Outputs of
+ * the timed launches go to internal scratch.  Synchronises params->stream.
+ * Errors: those of cs_query; CS_ERR_INVALID_ARG for best == NULL, reps < 1,
+ * Q == 0 or host_io = 1. */
+CS_API cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
+                             float conservatism, const cs_params *params, int32_t reps,
+                             int32_t *best, float *ms, int32_t cap);
+
+/* ------------------------------------------------------------------------
+ * Serving loop.  The paper has no counterpart: this is the runtime that keeps
+ * scenes resident and answers collision-query requests of uneven size (one
+ * RRT edge to a whole MPPI batch) for many clients.
+ *
+ * The server owns `slots` batch slots, each with its own CUDA stream and
+ * fixed device and pinned host buffers for `slot_rows` query rows, all
+ * allocated by cs_server_create (about slots x slot_rows x 140 bytes of
+ * device memory and x 60 bytes of pinned host memory), so requests are
+ * admitted by memory: a request waits until a slot is free, then joins that
+ * slot's batch together with the other waiting requests for the same scene
+ * and primitive type, in submission order, while the slot's rows and
+ * max_requests allow.  A launcher thread forms a batch whenever a slot is
+ * free and requests wait, so batches overlap on the device (continuous
+ * batching).  Each batch is one pass of the cs_query path over the
+ * concatenated rows with per-row n_sigma; a request's results are bitwise
+ * those of a cs_query call on that request alone with the same parameters
+ * and tile configuration. */
+typedef struct cs_server cs_server;
+
+typedef struct cs_server_config {
+    int32_t slots;        /* batches in flight, 1..16 (default 3) */
+    int64_t slot_rows;    /* rows one batch holds, also the largest request (default 2^19) */
+    int32_t max_requests; /* requests one batch holds (default 4096) */
+    int32_t tile_config;  /* as cs_params.tile_config (default CS_TILE_TUNED) */
+    cs_params params;     /* metric parameters of every request: gamma, d_max, s_min, eps, tau,
+                             k_thr, mode (the pointer, stream and group members are ignored) */
+} cs_server_config;
+
+/* One request.  Every pointer is a host pointer; `prims` is read when the
+ * request is batched and the outputs are written when it completes, so all
+ * of them must stay valid until cs_server_wait has returned for it. */
+typedef struct cs_request {
+    int32_t scene;        /* index into the scenes passed to cs_server_create */
+    int32_t prim_type;    /* cs_prim_type */
+    const float *prims;   /* [Q, 4] spheres or [Q, 10] ellipsoids, as for cs_query */
+    int64_t Q;            /* rows, 1..slot_rows */
+    float conservatism;   /* n_sigma >= 0 for every row of the request */
+    int32_t group_size;   /* > 0: group outputs as cs_params.group_size */
+    float *out_metric;    /* [Q] or NULL */
+    uint8_t *out_collide; /* [Q] or NULL */
+    int32_t *out_count;   /* [Q] or NULL */
+    float *out_group_metric;    /* [ceil(Q/group_size)] or NULL */
+    uint8_t *out_group_collide; /* [ceil(Q/group_size)] or NULL */
+} cs_request;
+
+/* Timeline of a completed request, in seconds of cs_server_clock. */
+typedef struct cs_request_times {
+    double submitted;        /* cs_server_submit accepted it */
+    double launched;         /* its batch started to be assembled */
+    double completed;        /* its results were in the caller's buffers */
+    int64_t batch_rows;      /* rows of the batch it ran in */
+    int64_t batch_requests;  /* requests of that batch */
+    int32_t status;          /* cs_status of the request */
+} cs_request_times;
+
+typedef struct cs_server_stats {
+    int64_t batches, rows, requests;             /* launched so far */
+    int64_t max_batch_rows, max_batch_requests;
+    int64_t pending;                             /* submitted, not yet batched */
+    int64_t busy_slots;
+} cs_server_stats;
+
+/* Defaults as listed in cs_server_config.  CS_ERR_INVALID_ARG for NULL. */
+CS_API cs_status cs_server_config_init(cs_server_config *cfg);
+/* Start a server over `n_scenes` resident scenes (all on the current
+ * device; they must outlive the server).  cfg NULL = defaults.  Errors:
+ * CS_ERR_INVALID_ARG for bad sizes or parameters, CS_ERR_BAD_HANDLE for a
+ * bad scene, CS_ERR_NO_MEMORY / CS_ERR_CUDA when the slots cannot be
+ * allocated. */
+CS_API cs_status cs_server_create(cs_scene *const *scenes, int32_t n_scenes, const cs_server_config *cfg,
+                                  cs_server **out);
+/* Queue a request and return its ticket.  The rows are validated on the host
+ * first (finite values, positive radius or semi-axes): CS_ERR_INVALID_ARG
+ * and nothing queued on failure.  Thread-safe. */
+CS_API cs_status cs_server_submit(cs_server *server, const cs_request *req, uint64_t *ticket);
+/* Wait until the request of `ticket` has completed (timeout_s < 0: no
+ * limit), fill *times (may be NULL) and retire the ticket.  Returns the
+ * request's status, CS_ERR_TIMEOUT when the limit ran out (the ticket stays
+ * valid), CS_ERR_INVALID_ARG for an unknown ticket.  Thread-safe. */
+CS_API cs_status cs_server_wait(cs_server *server, uint64_t ticket, double timeout_s, cs_request_times *times);
+CS_API cs_status cs_server_stats_get(cs_server *server, cs_server_stats *out);
+/* The monotonic clock of cs_request_times, in seconds. */
+CS_API double cs_server_clock(void);
+/* Stop the launcher, finish the batches in flight and free the server.
+ * Requests not yet batched are dropped; no cs_server_wait may be in
+ * progress.  NULL is a no-op. */
+CS_API cs_status cs_server_destroy(cs_server *server);
 
 /* Self-test of the bounded-wait machinery: launches one block that waits on
  * a barrier nothing completes, with a budget of `spins` polls, and returns

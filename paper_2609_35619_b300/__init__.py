@@ -10,6 +10,9 @@ the metric runs in the library's CUDA kernels):
   pose_spheres / pose_spheres_grad             cs_pose_spheres(_grad)
   CollisionCost.apply(poses, ...)              torch.autograd.Function over the
                                                pose chain and the metric
+  Scene.autotune(prims, nsigma, ...)           cs_autotune (tile shape per batch class)
+  QueryGraph(scene, prims, ...)                cs_graph_create / launch / destroy
+  Server(scenes, ...)                          cs_server_* (continuous batching)
 The raw one-to-one binding is `paper_2609_35619_b300.abi`.
 """
 from __future__ import annotations
@@ -21,7 +24,7 @@ from . import abi
 from .abi import (CS_METRIC_MEAN_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_SUM_COST,
                   CS_PRIM_ELLIPSOID, CS_PRIM_SPHERE, CsError, check)
 
-__all__ = ["Scene", "QueryParams", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
+__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
            "CS_PRIM_SPHERE", "CS_PRIM_ELLIPSOID", "CS_METRIC_MEAN_COST", "CS_METRIC_SUM_COST",
            "CS_METRIC_MIN_S2", "CS_METRIC_SOFTMIN_S2", "CsError"]
 
@@ -176,6 +179,158 @@ class Scene:
 
     def sync(self, stream=None):
         check(abi.cs_sync(self._h, stream))
+
+    def autotune(self, prims, nsigma=1.0, *, prim_type=CS_PRIM_SPHERE, params: QueryParams | None = None,
+                 reps: int = 3, stream=None):
+        """cs_autotune on a device batch: returns (best tile id, {id: ms})."""
+        params = params or QueryParams()
+        cols = 4 if prim_type == CS_PRIM_SPHERE else 10
+        prims = _as_f32(prims, self.device).reshape(-1, cols)
+        p = params.to_c()
+        p.stream = abi.stream_handle(stream)
+        ids = abi.cs_tile_configs()
+        ms = (ctypes.c_float * len(ids))()
+        best = ctypes.c_int32()
+        check(abi.cs_autotune(self._h, prim_type, prims, prims.shape[0], float(nsigma), p, reps, best,
+                              ctypes.addressof(ms), len(ids)))
+        return best.value, dict(zip(ids, list(ms)))
+
+
+class QueryGraph:
+    """One query call captured into a CUDA graph (cs_graph_create) over fixed
+    device buffers: rewrite `prims` in place, then launch().  Forward graphs
+    fill `out` (metric, collide and, per params, count / group outputs);
+    adjoint graphs (grad=True) fill `grad_centres`."""
+
+    def __init__(self, scene: Scene, prims, nsigma=1.0, *, prim_type=CS_PRIM_SPHERE,
+                 params: QueryParams | None = None, grad=False, grad_out=None, want_count=False):
+        torch = _torch()
+        params = params or QueryParams()
+        self.scene = scene
+        self.prims = prims
+        assert prims.is_cuda and prims.is_contiguous() and prims.dtype == torch.float32
+        cols = 4 if prim_type == CS_PRIM_SPHERE else 10
+        Q = prims.numel() // cols
+        dev = prims.device
+        p = params.to_c()
+        self.out = {}
+        self.grad_out = grad_out
+        if grad:
+            self.out["grad_centres"] = torch.empty((Q, 3), dtype=torch.float32, device=dev)
+            m = c = None
+            g = self.out["grad_centres"]
+        else:
+            m = self.out["metric"] = torch.empty(Q, dtype=torch.float32, device=dev)
+            c = self.out["collide"] = torch.empty(Q, dtype=torch.uint8, device=dev)
+            g = None
+            if want_count:
+                self.out["count"] = torch.empty(Q, dtype=torch.int32, device=dev)
+                p.out_count = abi.ptr(self.out["count"])
+            if params.group_size > 0:
+                ng = (Q + params.group_size - 1) // params.group_size
+                self.out["group_metric"] = torch.empty(ng, dtype=torch.float32, device=dev)
+                self.out["group_collide"] = torch.empty(ng, dtype=torch.uint8, device=dev)
+                p.out_group_metric = abi.ptr(self.out["group_metric"])
+                p.out_group_collide = abi.ptr(self.out["group_collide"])
+        self._h = ctypes.c_void_p()
+        check(abi.cs_graph_create(scene.handle, prim_type, prims, Q, float(nsigma), m, c, grad_out, g, p,
+                                  self._h))
+        self.kernels = abi.cs_graph_kernels(self._h)
+
+    def launch(self, stream=None):
+        check(abi.cs_graph_launch(self._h, stream))
+        return self.out
+
+    def sync(self, stream=None):
+        check(abi.cs_graph_sync(self._h, stream))
+
+    def close(self):
+        if self._h:
+            check(abi.cs_graph_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop over resident scenes (cs_server_*): submit() host numpy
+    requests, wait() for their results and timeline."""
+
+    def __init__(self, scenes, *, slots=3, slot_rows=1 << 19, max_requests=4096, tile_config=abi.CS_TILE_TUNED,
+                 params: QueryParams | None = None):
+        params = params or QueryParams()
+        self.scenes = list(scenes)
+        cfg = abi.cs_server_config()
+        check(abi.cs_server_config_init(cfg))
+        cfg.slots, cfg.slot_rows, cfg.max_requests, cfg.tile_config = slots, slot_rows, max_requests, tile_config
+        cfg.params = params.to_c()
+        self._h = ctypes.c_void_p()
+        check(abi.cs_server_create([s.handle for s in self.scenes], len(self.scenes), cfg, self._h))
+        self._live = {}
+
+    def submit(self, scene: int, prims, nsigma: float, *, prim_type=CS_PRIM_SPHERE, group_size=0,
+               want_count=False, out=None) -> int:
+        """Queue one request (host float32 [Q,4] or [Q,10]); returns its ticket."""
+        import numpy as np
+        prims = np.ascontiguousarray(prims, dtype=np.float32)
+        cols = 4 if prim_type == CS_PRIM_SPHERE else 10
+        Q = prims.size // cols
+        if out is None:
+            out = {"metric": np.empty(Q, np.float32), "collide": np.empty(Q, np.uint8)}
+            if want_count:
+                out["count"] = np.empty(Q, np.int32)
+            if group_size > 0:
+                ng = (Q + group_size - 1) // group_size
+                out["group_metric"] = np.empty(ng, np.float32)
+                out["group_collide"] = np.empty(ng, np.uint8)
+        r = abi.cs_request()
+        r.scene, r.prim_type, r.prims, r.Q = scene, prim_type, abi.ptr(prims), Q
+        r.conservatism, r.group_size = float(nsigma), int(group_size)
+        r.out_metric = abi.ptr(out.get("metric"))
+        r.out_collide = abi.ptr(out.get("collide"))
+        r.out_count = abi.ptr(out.get("count"))
+        r.out_group_metric = abi.ptr(out.get("group_metric"))
+        r.out_group_collide = abi.ptr(out.get("group_collide"))
+        t = ctypes.c_uint64()
+        check(abi.cs_server_submit(self._h, r, t))
+        self._live[t.value] = (prims, out)  # the buffers stay alive until wait()
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """Results (dict of numpy arrays) and timeline of a request."""
+        tm = abi.cs_request_times()
+        st = abi.cs_server_wait(self._h, ticket, timeout, tm)
+        if st == abi.CS_ERR_TIMEOUT and tm.status == 0 and tm.completed == 0:
+            raise CsError(st, abi.cs_last_error())
+        _, out = self._live.pop(ticket)
+        check(st)
+        return out, {"submitted": tm.submitted, "launched": tm.launched, "completed": tm.completed,
+                     "batch_rows": tm.batch_rows, "batch_requests": tm.batch_requests}
+
+    def stats(self) -> dict:
+        s = abi.cs_server_stats()
+        check(abi.cs_server_stats_get(self._h, s))
+        return {k: getattr(s, k) for k, _ in abi.cs_server_stats._fields_}
+
+    @staticmethod
+    def clock() -> float:
+        return abi.cs_server_clock()
+
+    def close(self):
+        if self._h:
+            check(abi.cs_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _set_events(p, events):

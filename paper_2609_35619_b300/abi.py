@@ -79,6 +79,57 @@ class cs_scene_info(ctypes.Structure):
     ]
 
 
+class cs_server_config(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int32),
+        ("slot_rows", ctypes.c_int64),
+        ("max_requests", ctypes.c_int32),
+        ("tile_config", ctypes.c_int32),
+        ("params", cs_params),
+    ]
+
+
+class cs_request(ctypes.Structure):
+    _fields_ = [
+        ("scene", ctypes.c_int32),
+        ("prim_type", ctypes.c_int32),
+        ("prims", ctypes.c_void_p),
+        ("Q", ctypes.c_int64),
+        ("conservatism", ctypes.c_float),
+        ("group_size", ctypes.c_int32),
+        ("out_metric", ctypes.c_void_p),
+        ("out_collide", ctypes.c_void_p),
+        ("out_count", ctypes.c_void_p),
+        ("out_group_metric", ctypes.c_void_p),
+        ("out_group_collide", ctypes.c_void_p),
+    ]
+
+
+class cs_request_times(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_double),
+        ("launched", ctypes.c_double),
+        ("completed", ctypes.c_double),
+        ("batch_rows", ctypes.c_int64),
+        ("batch_requests", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+    ]
+
+
+class cs_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("batches", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("requests", ctypes.c_int64),
+        ("max_batch_rows", ctypes.c_int64),
+        ("max_batch_requests", ctypes.c_int64),
+        ("pending", ctypes.c_int64),
+        ("busy_slots", ctypes.c_int64),
+    ]
+
+
+CS_TILE_TUNED = -1
+
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "cs_params_init": (ctypes.c_int, [ctypes.POINTER(cs_params)]),
@@ -95,6 +146,22 @@ _SIGNATURES = {
     "cs_pose_spheres": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_float, _P, _P]),
     "cs_pose_spheres_grad": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, _P, _P, _P]),
     "cs_sync": (ctypes.c_int, [_P, _P]),
+    "cs_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P,
+                                       ctypes.POINTER(cs_params), ctypes.POINTER(_P)]),
+    "cs_graph_launch": (ctypes.c_int, [_P, _P]),
+    "cs_graph_sync": (ctypes.c_int, [_P, _P]),
+    "cs_graph_kernels": (ctypes.c_int64, [_P]),
+    "cs_graph_destroy": (ctypes.c_int, [_P]),
+    "cs_autotune": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float,
+                                   ctypes.POINTER(cs_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                   _P, ctypes.c_int32]),
+    "cs_server_config_init": (ctypes.c_int, [ctypes.POINTER(cs_server_config)]),
+    "cs_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cs_server_config), ctypes.POINTER(_P)]),
+    "cs_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(cs_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "cs_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(cs_request_times)]),
+    "cs_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(cs_server_stats)]),
+    "cs_server_clock": (ctypes.c_double, []),
+    "cs_server_destroy": (ctypes.c_int, [_P]),
     "cs_tile_configs": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "cs_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int64, _P]),
     "cs_launch_count": (ctypes.c_int64, []),
@@ -220,6 +287,66 @@ def cs_pose_spheres_grad(poses, P, offsets, K, grad_centres, grad_poses, stream)
 
 def cs_sync(scene, stream) -> int:
     return load().cs_sync(scene, stream_handle(stream))
+
+
+def cs_graph_create(scene, prim_type, prims, Q, conservatism, out_metric, out_collide, grad_out,
+                    grad_centres, params, out: ctypes.c_void_p) -> int:
+    return load().cs_graph_create(scene, prim_type, ptr(prims), int(Q), float(conservatism), ptr(out_metric),
+                                  ptr(out_collide), ptr(grad_out), ptr(grad_centres),
+                                  None if params is None else ctypes.byref(params), ctypes.byref(out))
+
+
+def cs_graph_launch(graph, stream) -> int:
+    return load().cs_graph_launch(graph, stream_handle(stream))
+
+
+def cs_graph_sync(graph, stream) -> int:
+    return load().cs_graph_sync(graph, stream_handle(stream))
+
+
+def cs_graph_kernels(graph) -> int:
+    return int(load().cs_graph_kernels(graph))
+
+
+def cs_graph_destroy(graph) -> int:
+    return load().cs_graph_destroy(graph)
+
+
+def cs_autotune(scene, prim_type, prims, Q, conservatism, params, reps, best: ctypes.c_int32, ms, cap) -> int:
+    return load().cs_autotune(scene, prim_type, ptr(prims), int(Q), float(conservatism),
+                              None if params is None else ctypes.byref(params), int(reps), ctypes.byref(best),
+                              ptr(ms), int(cap))
+
+
+def cs_server_config_init(cfg: cs_server_config) -> int:
+    return load().cs_server_config_init(ctypes.byref(cfg))
+
+
+def cs_server_create(scenes, n_scenes, cfg, out: ctypes.c_void_p) -> int:
+    arr = (ctypes.c_void_p * max(1, int(n_scenes)))(*[s if isinstance(s, int) else s.value for s in scenes])
+    return load().cs_server_create(ctypes.cast(arr, ctypes.c_void_p), int(n_scenes),
+                                   None if cfg is None else ctypes.byref(cfg), ctypes.byref(out))
+
+
+def cs_server_submit(server, req: cs_request, ticket: ctypes.c_uint64) -> int:
+    return load().cs_server_submit(server, ctypes.byref(req), ctypes.byref(ticket))
+
+
+def cs_server_wait(server, ticket, timeout_s, times) -> int:
+    return load().cs_server_wait(server, int(ticket), float(timeout_s),
+                                 None if times is None else ctypes.byref(times))
+
+
+def cs_server_stats_get(server, out: cs_server_stats) -> int:
+    return load().cs_server_stats_get(server, ctypes.byref(out))
+
+
+def cs_server_clock() -> float:
+    return float(load().cs_server_clock())
+
+
+def cs_server_destroy(server) -> int:
+    return load().cs_server_destroy(server)
 
 
 def cs_tile_configs() -> list:

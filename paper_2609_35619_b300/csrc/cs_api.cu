@@ -35,6 +35,7 @@ static thread_local std::string g_err;
 static std::atomic<int64_t> g_launches{0};
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -81,15 +82,38 @@ Workspace *find_workspace(int device, cudaStream_t stream) {
     return it == g_ws.end() ? nullptr : it->second;
 }
 
+cs_status new_workspace(cudaStream_t stream, Workspace **out) {
+    Workspace *w = new Workspace();
+    w->stream = stream;
+    cudaError_t e = cudaMalloc(&w->err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->err, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) {
+        free_ws(w);
+        return cuda_fail(e, "workspace error word");
+    }
+    *out = w;
+    return CS_OK;
+}
+
+void delete_workspace(Workspace *w) {
+    if (w) free_ws(w);
+}
+
 cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io, Workspace **out) {
     std::lock_guard<std::mutex> lk(g_ws_mu);
     Workspace *&w = g_ws[WsKey{device, stream}];
     if (!w) {
-        w = new Workspace();
-        w->stream = stream;
-        CS_CUDA(cudaMalloc(&w->err, sizeof(unsigned)));
-        CS_CUDA(cudaMemsetAsync(w->err, 0, sizeof(unsigned), stream));
+        cs_status st = new_workspace(stream, &w);
+        if (st != CS_OK) {
+            g_ws.erase(WsKey{device, stream});
+            return st;
+        }
     }
+    *out = w;
+    return grow_workspace(w, Q, host_io);
+}
+
+cs_status grow_workspace(Workspace *w, size_t Q, bool host_io) {
     if (Q > w->cap_q) {
         size_t cap = std::max<size_t>({Q, 1024, w->cap_q + w->cap_q / 2});
         void *olds[] = {w->keys[0], w->keys[1], w->vals[0], w->vals[1], w->sort_hist, w->scan_tmp,
@@ -124,7 +148,6 @@ cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io,
         CS_CUDA(cudaMalloc(&w->io_gc, cap));
         w->cap_io_prims = cap;
     }
-    *out = w;
     return CS_OK;
 }
 
@@ -147,9 +170,9 @@ cs_status check_params(const cs_params &p) {
     if (p.mode < 0 || p.mode > 3) return invalid("mode must be a cs_metric_mode");
     if (p.group_size < 0) return invalid("group_size must be >= 0");
     if (p.host_io != 0 && p.host_io != 1) return invalid("host_io must be 0 or 1");
-    if (p.tile_config != 0) {
-        int32_t ids[16];
-        int n = tile_configs(ids, 16);
+    if (p.tile_config != 0 && p.tile_config != CS_TILE_TUNED) {
+        int32_t ids[32];
+        int n = tile_configs(ids, 32);
         bool found = false;
         for (int i = 0; i < n; ++i) found |= ids[i] == p.tile_config;
         if (!found) return invalid("unknown tile_config");
@@ -248,10 +271,13 @@ cs_status cs_scene_export(const cs_scene *s, float *pos, float *cov, int32_t *in
     return CS_OK;
 }
 
-static cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims, int64_t Q,
-                              float conservatism, const cs_params *params, bool grad,
-                              float *out_metric, uint8_t *out_collide, const float *grad_out,
-                              float *grad_centres) {
+}  // extern "C"
+
+namespace cs {
+cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims, int64_t Q,
+                       float conservatism, const cs_params *params, bool grad, float *out_metric,
+                       uint8_t *out_collide, const float *grad_out, float *grad_centres,
+                       Workspace *own_ws) {
     cs_status st = check_scene(s);
     if (st != CS_OK) return st;
     Scene *sc = reinterpret_cast<Scene *>(const_cast<cs_scene *>(s));
@@ -262,6 +288,11 @@ static cs_status query_common(const cs_scene *s, int32_t prim_type, const float 
     if (prim_type != CS_PRIM_SPHERE && prim_type != CS_PRIM_ELLIPSOID)
         return invalid("prim_type must be CS_PRIM_SPHERE or CS_PRIM_ELLIPSOID");
     if (Q < 0 || Q > kMaxRows) return invalid("Q out of range [0, 2^30]");
+    if (p.tile_config == CS_TILE_TUNED) {
+        std::lock_guard<std::mutex> lk(sc->tune_mu);
+        auto it = sc->tuned.find(tune_key(prim_type, p.mode, Q));
+        p.tile_config = it == sc->tuned.end() ? 0 : it->second;
+    }
     if (!p.nsigma_per_query && (!(conservatism >= 0.f) || !isfinite(conservatism)))
         return invalid("conservatism (n_sigma) must be finite and >= 0");
     if (Q == 0) return CS_OK;
@@ -285,8 +316,12 @@ static cs_status query_common(const cs_scene *s, int32_t prim_type, const float 
                 return invalid("nsigma_per_query must be finite and >= 0");
         }
     }
-    Workspace *ws = nullptr;
-    if ((st = get_workspace(sc->device, stream, (size_t)Q, p.host_io != 0, &ws)) != CS_OK) return st;
+    Workspace *ws = own_ws;
+    if (ws) {
+        if ((st = grow_workspace(ws, (size_t)Q, p.host_io != 0)) != CS_OK) return st;
+    } else if ((st = get_workspace(sc->device, stream, (size_t)Q, p.host_io != 0, &ws)) != CS_OK) {
+        return st;
+    }
 
     const float *d_prims = prims, *d_ns = p.nsigma_per_query, *d_gout = grad_out;
     float *d_metric = out_metric, *d_grad = grad_centres, *d_gm = p.out_group_metric;
@@ -343,19 +378,22 @@ static cs_status query_common(const cs_scene *s, int32_t prim_type, const float 
     }
     return CS_OK;
 }
+}  // namespace cs
+
+extern "C" {
 
 cs_status cs_query(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
                    float conservatism, float *out_metric, uint8_t *out_collide,
                    const cs_params *params) {
     return query_common(scene, prim_type, prims, Q, conservatism, params, false, out_metric,
-                        out_collide, nullptr, nullptr);
+                        out_collide, nullptr, nullptr, nullptr);
 }
 
 cs_status cs_query_grad(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
                         float conservatism, const float *grad_out, float *grad_centres,
                         const cs_params *params) {
     return query_common(scene, prim_type, prims, Q, conservatism, params, true, nullptr, nullptr,
-                        grad_out, grad_centres);
+                        grad_out, grad_centres, nullptr);
 }
 
 cs_status cs_pose_spheres(const float *poses, int64_t P, const float *offsets, int32_t K,

@@ -100,6 +100,9 @@ struct Workspace {
 
 struct Scene {
     SceneDev dev;
+    // tile shapes chosen by cs_autotune, keyed by tune_key()
+    std::mutex tune_mu;
+    std::unordered_map<uint32_t, int32_t> tuned;
     int64_t n_input = 0, n_kept = 0, n_grid = 0, n_large = 0, n_invalid = 0;
     int64_t ncells = 0;
     int64_t device_bytes = 0;
@@ -114,8 +117,29 @@ struct Scene {
 // used on that stream; it lives until cs_release_scratch or process exit.
 cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io, Workspace **out);
 Workspace *find_workspace(int device, cudaStream_t stream);
+// A workspace outside the pool (owned by a graph or a server slot).
+cs_status new_workspace(cudaStream_t stream, Workspace **out);
+cs_status grow_workspace(Workspace *w, size_t Q, bool host_io);
+void delete_workspace(Workspace *w);
 
 constexpr uint32_t kSceneMagic = 0xC5B300A1u;
+
+// Key of a tuned tile shape: primitive type, metric mode and batch-size class
+// floor(log2 Q).
+inline uint32_t tune_key(int32_t prim_type, int32_t mode, int64_t Q) {
+    uint32_t c = 0;
+    while (c < 40 && (int64_t(1) << (c + 1)) <= Q) ++c;
+    return (uint32_t)prim_type | ((uint32_t)mode << 2) | (c << 8);
+}
+
+// The query path behind cs_query / cs_query_grad (also captured by
+// cs_graph_create and driven by the serving loop).
+cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims, int64_t Q,
+                       float conservatism, const cs_params *params, bool grad, float *out_metric,
+                       uint8_t *out_collide, const float *grad_out, float *grad_centres,
+                       Workspace *own_ws);
+int tile_configs(int32_t *ids, int32_t cap);
+int64_t launch_total();
 
 // ------------------------------------------------------- launch accounting
 // Host-side count of kernel launches (cs_launch_count); every launcher adds

@@ -64,9 +64,14 @@ struct EvalArgs {
 // exactly nothing, st2 > S_cut); larger groups give the scheduler more
 // independent dependency chains per basic block.  GROUP == QW drops the
 // per-primitive test altogether.
-template <int NCW_, int QW_, int NS_, int CHB_, int MINB_, int GROUP_ = 2>
+template <int NCW_, int QW_, int NS_, int CHB_, int MINB_, int GROUP_ = 2, int IL_ = 0>
 struct Cfg {
     static constexpr int NCW = NCW_, QW = QW_, NS = NS_, CHB = CHB_, MINB = MINB_, GROUP = GROUP_;
+    // IL = 1: consumer warp w takes rows w, w + NCW, ... of the tile (its
+    // primitives spread over the tile, so the warps' loads even out);
+    // IL = 0: rows w QW .. w QW + QW - 1 (a compact warp box)
+    static constexpr int IL = IL_;
+    __device__ static int row(int warp, int j) { return IL ? j * NCW + warp : warp * QW + j; }
     static_assert(CHB <= 32, "one lane tests each chunk slot of a stage");
     static_assert(QW == 8 || QW == 16, "primitive masks are tested 32 / QW chunks per round");
 };
@@ -648,13 +653,16 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
     g2.sxx = pk2(g0.sxx, g1.sxx); g2.syy = pk2(g0.syy, g1.syy); g2.szz = pk2(g0.szz, g1.szz);
     g2.sxy2 = pk2(g0.sxy2, g1.sxy2); g2.sxz2 = pk2(g0.sxz2, g1.sxz2); g2.syz2 = pk2(g0.syz2, g1.syz2);
     const f32x2 nG2 = pk2(-k.G, -k.G), Gs2 = pk2(k.Gsmin, k.Gsmin);
-    const unsigned long long lanes_evaluated = (unsigned long long)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo));
     constexpr unsigned GMASK = (1u << GROUP) - 1u;
+    unsigned gm = 0u;  // bit j0: group j0 .. j0 + GROUP - 1 has a member reaching a chunk
+#pragma unroll
+    for (int j0 = 0; j0 < QW; j0 += GROUP) gm |= ((qmask >> j0) & GMASK) ? (1u << j0) : 0u;
+    const unsigned ng = (unsigned)__popc(gm) * (unsigned)GROUP;
+    c_hits += ng;
+    cand += (unsigned long long)(ng * (unsigned)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo)));
 #pragma unroll
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
-        if ((qmask >> j0) & GMASK) {
-            c_hits += (unsigned long long)GROUP;
-            cand += (unsigned long long)GROUP * lanes_evaluated;
+        if ((gm >> j0) & 1u) {
 #pragma unroll
             for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW>(A, j, g2, wqd[j], k, nG2, Gs2);
         }
@@ -726,7 +734,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     // ---- this warp's primitives into shared memory
     int nvalid = 0;
     if (lane < QW) {
-        const int q = tile * TQ + warp * QW + lane;
+        const int q = tile * TQ + C::row(warp, lane);
         float4 d0 = make_float4(0, 0, 0, 0), d1 = d0, d2 = d0, d3 = d0;
         if (q < a.Q) {
             const float4 *rec = a.qrec + (size_t)q * RECS;
@@ -885,7 +893,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     unsigned long long nb_total = 0;
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
-        const int q = tile * TQ + warp * QW + j;
+        const int q = tile * TQ + C::row(warp, j);
         const bool vq = wq[j][PRIM == 0 ? 1 : 3].w != 0.f || (PRIM == 1 && wq[j][3].x != 0.f);
         const int cntj = __reduce_add_sync(0xffffffffu, (unsigned)A.cnt[j]);
         if (!GRAD) {
@@ -1115,6 +1123,14 @@ QueryConsts make_consts(const cs_params &p) {
 //   3: 4 x 8, 3 x 8, 4 CTAs/SM
 //   4: 4 x 16, 3 x 8, 3 CTAs/SM
 //   5-8: shapes 1, 1, 4, 4 evaluating sphere primitives in groups of 4, 8, 4, 8
+//   9: 8 x 8, 8 stages x 8 chunks, 2 CTAs/SM (deeper ring, same staging memory as 1)
+//   10: 8 x 8, 16 stages x 4 chunks, 2 CTAs/SM
+//   11: 4 x 16, 6 stages x 8 chunks, 3 CTAs/SM
+//   12: shape 9 with groups of 4
+//   13: 4 x 16, 3 stages x 16 chunks, 3 CTAs/SM
+//   14: 4 x 16, 4 stages x 12 chunks, 3 CTAs/SM
+//   15: 8 x 8, 2 stages x 32 chunks, 2 CTAs/SM
+//   16: shape 1 with the tile's rows interleaved over the consumer warps
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1123,8 +1139,16 @@ using Cfg5 = Cfg<8, 8, 4, 16, 2, 4>;
 using Cfg6 = Cfg<8, 8, 4, 16, 2, 8>;
 using Cfg7 = Cfg<4, 16, 3, 8, 3, 4>;
 using Cfg8 = Cfg<4, 16, 3, 8, 3, 8>;
+using Cfg9 = Cfg<8, 8, 8, 8, 2>;
+using Cfg10 = Cfg<8, 8, 16, 4, 2>;
+using Cfg11 = Cfg<4, 16, 6, 8, 3>;
+using Cfg12 = Cfg<8, 8, 8, 8, 2, 4>;
+using Cfg13 = Cfg<4, 16, 3, 16, 3>;
+using Cfg14 = Cfg<4, 16, 4, 12, 3>;
+using Cfg15 = Cfg<8, 8, 2, 32, 2>;
+using Cfg16 = Cfg<8, 8, 4, 16, 2, 2, 1>;
 using CfgGrad = Cfg<4, 8, 3, 8, 3>;  // the adjoint keeps three gradient sums per primitive
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16};
 constexpr int kDefaultTile = 1;
 
 int tile_configs(int32_t *ids, int32_t cap) {
@@ -1174,6 +1198,14 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 6: return launch_mode<PRIM, Cfg6>(a, s);
         case 7: return launch_mode<PRIM, Cfg7>(a, s);
         case 8: return launch_mode<PRIM, Cfg8>(a, s);
+        case 9: return launch_mode<PRIM, Cfg9>(a, s);
+        case 10: return launch_mode<PRIM, Cfg10>(a, s);
+        case 11: return launch_mode<PRIM, Cfg11>(a, s);
+        case 12: return launch_mode<PRIM, Cfg12>(a, s);
+        case 13: return launch_mode<PRIM, Cfg13>(a, s);
+        case 14: return launch_mode<PRIM, Cfg14>(a, s);
+        case 15: return launch_mode<PRIM, Cfg15>(a, s);
+        case 16: return launch_mode<PRIM, Cfg16>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }
