@@ -47,10 +47,15 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="step", choices=["step", "eval"],
+    ap.add_argument("--serve-requests", type=int, default=1500,
+                    help="requests of the serving measurement in the default run")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--case", default="step", choices=["step", "eval", "serve"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
-                         "(two fused-kernel launches); prints a short JSON summary")
+                         "(two fused-kernel launches); prints a short JSON summary. "
+                         "serve: the serving sweep (two 3M apartment scenes, Poisson arrivals at "
+                         "25/50/75/90 %% of the served capacity, 10,000 requests per load)")
     ap.add_argument("--tile", type=int, default=0, help="tile configuration for --case eval (0 = auto)")
     ap.add_argument("--batch", default="arm", choices=["arm", "edge"], help="query batch for --case eval")
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
@@ -276,6 +281,8 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches // args.steps) if args.steps else 0,
         "gpu_launches_total": int(launches), "served": None,
     }
+    if not args.no_serve and world == 1:
+        result["served"] = run_served(torch, cs, dev, args.serve_requests)
     return result
 
 
@@ -349,6 +356,159 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
     ms = 1e3 * sum(times) / len(times)
     return {"value": world * useful_pairs / (ms * 1e-3), "unit": "pairs/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ------------------------------------------------------------ serving
+SERVE_WORKLOAD = ("2 apartment scenes x 3M Gaussians; Poisson requests of 16..262,144 spheres "
+                  "(log-uniform), n_sigma ~ U[0,2], scene ~ U{0,1}")
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def serve_setup(torch, cs, dev):
+    import cs_synth as S
+    scenes_h = [S.apartment_scene(seed=1005), S.apartment_scene(seed=1006)]
+    scenes = [cs.Scene(s["means"], s["scales"], s["quats"], s["opacity"], device=dev) for s in scenes_h]
+    # tile shape per scene from the autotuner, on a full-size request mix
+    tune = S.serving_requests(seed=1999, count=24, q_lo=4096, q_hi=262_144)
+    big = torch.as_tensor(np.concatenate([r["spheres"] for r in tune])[:1 << 19], device=dev)
+    tiles = [sc.autotune(big, 1.0, reps=2)[0] for sc in scenes]
+    torch.cuda.synchronize(dev)
+    return scenes_h, scenes, tiles
+
+
+def served_burst(cs, server, reqs):
+    """All requests submitted at once: the served capacity (rows/s)."""
+    t0 = server.clock()
+    ts = [server.submit(r["scene"], r["spheres"], r["nsigma"]) for r in reqs]
+    last = t0
+    for t in ts:
+        _, tm = server.wait(t, timeout=600.0)
+        last = max(last, tm["completed"])
+    rows = sum(r["spheres"].shape[0] for r in reqs)
+    return rows / (last - t0), last - t0
+
+
+def served_poisson(cs, server, reqs, rate_rows_s):
+    """Requests submitted at Poisson arrival times scaled to `rate_rows_s`
+    offered rows/s; latency = completion - intended arrival."""
+    rows = np.array([r["spheres"].shape[0] for r in reqs], np.float64)
+    arr = np.array([r["arrival"] for r in reqs])
+    arr = arr * (rows.mean() / rate_rows_s) / max(np.diff(arr).mean(), 1e-12)
+    tickets = [None] * len(reqs)
+    t0 = server.clock() + 0.05
+
+    def client():
+        for k, r in enumerate(reqs):
+            while True:
+                dt = t0 + arr[k] - server.clock()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.002) if dt > 0.0005 else 0)
+            tickets[k] = server.submit(r["scene"], r["spheres"], r["nsigma"])
+
+    th = threading.Thread(target=client)
+    th.start()
+    lat, done_last = [], t0
+    for k in range(len(reqs)):
+        while tickets[k] is None:
+            time.sleep(0.0002)
+        _, tm = server.wait(tickets[k], timeout=600.0)
+        lat.append(tm["completed"] - (t0 + arr[k]))
+        done_last = max(done_last, tm["completed"])
+    th.join()
+    span = done_last - t0
+    return {"offered_rows_per_s": rate_rows_s, "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
+            "mean_ms": 1e3 * float(np.mean(lat)), "queries_per_s": float(rows.sum() / span),
+            "requests": len(reqs)}
+
+
+def per_call_run(cs, scenes, reqs, rate_rows_s=None):
+    """The plain per-call path: one cs_query call per request (host buffers,
+    copies in, compute, copies out, synchronise), serially in arrival order.
+    rate None: back to back (capacity); else Poisson arrivals at that rate."""
+    rows = np.array([r["spheres"].shape[0] for r in reqs], np.float64)
+    arr = np.array([r["arrival"] for r in reqs])
+    if rate_rows_s is not None:
+        arr = arr * (rows.mean() / rate_rows_s) / max(np.diff(arr).mean(), 1e-12)
+    lat = []
+    t0 = time.perf_counter() + 0.01
+    for k, r in enumerate(reqs):
+        if rate_rows_s is not None:
+            while time.perf_counter() < t0 + arr[k]:
+                time.sleep(0.0002)
+        q = r["spheres"]
+        m = np.empty(q.shape[0], np.float32)
+        c = np.empty(q.shape[0], np.uint8)
+        p = cs.QueryParams().to_c()
+        p.host_io = 1
+        cs.check(cs.abi.cs_query(scenes[r["scene"]].handle, 0, q, q.shape[0], r["nsigma"], m, c, p))
+        done = time.perf_counter()
+        lat.append(done - (t0 + (arr[k] if rate_rows_s is not None else 0.0)))
+    span = time.perf_counter() - t0
+    out = {"queries_per_s": float(rows.sum() / span), "requests": len(reqs)}
+    if rate_rows_s is not None:
+        out.update({"offered_rows_per_s": rate_rows_s, "p50_ms": 1e3 * _pct(lat, 50),
+                    "p99_ms": 1e3 * _pct(lat, 99), "mean_ms": 1e3 * float(np.mean(lat))})
+    return out
+
+
+def one_query_per_call(cs, torch, scene, n=2000):
+    """One sphere per cs_query call (device buffers, synchronised): the
+    launch-bound floor of a per-query interface."""
+    import cs_synth as S
+    q = torch.as_tensor(S.serving_requests(seed=1998, count=1, q_lo=n, q_hi=n + 1)[0]["spheres"][:n],
+                        device="cuda")
+    m = torch.empty(1, device="cuda")
+    c = torch.empty(1, dtype=torch.uint8, device="cuda")
+    for j in range(20):
+        scene.query(q[j:j + 1], 1.0, out={"metric": m, "collide": c})
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(n):
+        scene.query(q[j:j + 1], 1.0, out={"metric": m, "collide": c})
+        torch.cuda.synchronize()
+    return n / (time.perf_counter() - t0)
+
+
+def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True):
+    import cs_synth as S
+    scenes_h, scenes, tiles = serve_setup(torch, cs, dev)
+    reqs = S.serving_requests(seed=1007, count=n_requests)
+    warm = S.serving_requests(seed=1008, count=16, q_lo=16, q_hi=65536)
+    srv = cs.Server(scenes, slots=3, slot_rows=1 << 19, tile_config=cs.abi.CS_TILE_TUNED)
+    served_burst(cs, srv, warm)
+    cap, cap_s = served_burst(cs, srv, reqs)
+    runs = [served_poisson(cs, srv, reqs, f * cap) for f in loads]
+    st = srv.stats()
+    srv.close()
+    out = {"workload": SERVE_WORKLOAD, "requests": n_requests,
+           "rows": int(sum(r["spheres"].shape[0] for r in reqs)),
+           "served_capacity_queries_per_s": cap, "loads": [dict(r, load=f) for f, r in zip(loads, runs)],
+           "server": {"slots": 3, "slot_rows": 1 << 19, "tiles": tiles,
+                      "mean_batch_requests": st["requests"] / max(st["batches"], 1),
+                      "max_batch_requests": st["max_batch_requests"]}}
+    if with_per_call:
+        per_call_run(cs, scenes, warm)
+        pc_cap = per_call_run(cs, scenes, reqs)
+        out["per_call"] = {"capacity_queries_per_s": pc_cap["queries_per_s"],
+                           "loads": [dict(per_call_run(cs, scenes, reqs, f * cap), load=f) for f in loads[:1]]}
+        out["one_query_per_call_queries_per_s"] = one_query_per_call(cs, torch, scenes[0])
+    for sc in scenes:
+        sc.close()
+    return out
+
+
+def run_serve_case(args):
+    import torch
+
+    import paper_2609_35619_b300 as cs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    res = run_served(torch, cs, dev, 10_000, loads=(0.25, 0.5, 0.75, 0.9))
+    print(json.dumps({"case": "serve", **res}))
 
 
 # ------------------------------------------------------------- oracle
@@ -441,6 +601,9 @@ def main():
     args = parse()
     if args.case == "eval":
         run_eval_case(args)
+        return
+    if args.case == "serve":
+        run_serve_case(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

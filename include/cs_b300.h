@@ -92,7 +92,9 @@ typedef struct cs_scene_desc {
                                opacity < opacity_min AND max(scale) > extent_max */
     float opacity_min;      /* default 0.05 */
     float extent_max;       /* default 0.1 (scene units) */
-    float cell_size;        /* uniform-grid cell edge; 0 = automatic */
+    float cell_size;        /* extent limit of a chunk (up to 32 Gaussians consecutive in
+                               Morton order); 0 = automatic: twice the edge of a box that
+                               holds 32 Gaussians at the mean density of the scene box */
     float tier_quantile;    /* Gaussians whose largest scale exceeds this quantile go to
                                the separately culled large tier; 0 = default 0.99 */
 } cs_scene_desc;
@@ -150,12 +152,13 @@ typedef struct cs_params {
 typedef struct cs_scene_info {
     int64_t n_input;      /* Gaussians passed in */
     int64_t n_kept;       /* after the floater filter and input validation */
-    int64_t n_grid;       /* kept Gaussians in the uniform grid */
+    int64_t n_grid;       /* kept Gaussians in the main tier */
     int64_t n_large;      /* kept Gaussians in the large tier */
     int64_t n_invalid;    /* rows with non-finite values or negative scales (dropped) */
-    int32_t dims[3];      /* grid cells per axis */
-    float cell_size;      /* grid cell edge */
-    float sigma_tier;     /* largest scale admitted to the grid tier */
+    int32_t dims[3];      /* nodes of the three levels of the chunk tree (each node
+                             bounds 32 chunks or 32 nodes of the level below) */
+    float cell_size;      /* extent limit of a chunk of the main tier */
+    float sigma_tier;     /* largest scale in the main tier */
     float lo[3], hi[3];   /* bounding box of the kept means */
     int64_t device_bytes; /* device memory held by the scene (without query scratch) */
 } cs_scene_info;
@@ -164,9 +167,10 @@ typedef struct cs_scene_info {
  * for p == NULL. */
 CS_API cs_status cs_params_init(cs_params *p);
 
-/* Build a resident scene (Eq. 2 repack, floater filter, uniform grid and
- * large tier) on the current device.  Synchronises `stream` once (the grid
- * shape depends on the scene's extent).  On success *out owns device memory
+/* Build a resident scene (Eq. 2 repack, floater filter, Morton-ordered
+ * chunks of the main and large tiers, the chunk tree) on the current device.
+ * Synchronises `stream` a few times (the layout depends on the scene's extent
+ * and on the chunk count).  On success *out owns device memory
  * until cs_scene_destroy.  n == 0 gives an empty scene (every query returns
  * an empty neighbour set). */
 CS_API cs_status cs_scene_create(const cs_scene_desc *desc, void *stream, cs_scene **out);
@@ -178,7 +182,7 @@ CS_API cs_status cs_scene_destroy(cs_scene *scene);
 
 CS_API cs_status cs_scene_info_get(const cs_scene *scene, cs_scene_info *info);
 
-/* Copy the repacked, grid-sorted scene to caller device buffers (any may be
+/* Copy the repacked, Morton-sorted scene to caller device buffers (any may be
  * NULL): pos [n_kept,4] = (mu, max scale); cov [n_kept,8] = (Sxx, Syy, Szz,
  * 2Sxy, 2Sxz, 2Syz, 0, 0); index [n_kept] = input row of each entry. */
 CS_API cs_status cs_scene_export(const cs_scene *scene, float *pos, float *cov, int32_t *index,

@@ -249,11 +249,11 @@ cs_status cs_scene_info_get(const cs_scene *s, cs_scene_info *info) {
     info->n_large = sc->n_large;
     info->n_invalid = sc->n_invalid;
     for (int k = 0; k < 3; ++k) {
-        info->dims[k] = sc->dev.dims[k];
+        info->dims[k] = sc->dev.nnodes[k];
         info->lo[k] = sc->dev.bb_lo[k];
         info->hi[k] = sc->dev.bb_hi[k];
     }
-    info->cell_size = sc->dev.h;
+    info->cell_size = sc->dev.chunk_extent;
     info->sigma_tier = sc->dev.sigma_tier;
     info->device_bytes = sc->device_bytes;
     return CS_OK;

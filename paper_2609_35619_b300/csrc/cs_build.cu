@@ -1,8 +1,9 @@
-// cs_build.cu -- scene construction: Eq. 2 repack of every Gaussian into the
-// 48-byte record, the floater filter of Section II-C, the uniform grid over
-// the means (the paper's spatial hash, Section II-B) with a separately culled
-// tier of very large Gaussians, and the per-chunk bounding records used by
-// the warp-level cull.
+// cs_build.cu -- scene construction: Eq. 2 repack of every Gaussian, the
+// floater filter of Section II-C, and the spatial index the cull descends (the
+// paper uses a spatial hash, Section II-B): Gaussians in global Morton order
+// of their means, a separate tier for the very large ones, chunks of up to 32
+// consecutive Gaussians within an extent limit, and a fan-out-32 tree of
+// bounding records over the chunks.
 #include <math.h>
 
 #include <algorithm>
@@ -21,7 +22,8 @@ struct BuildStats {
     unsigned n_kept;
     unsigned n_invalid;
     unsigned hist[kSigmaBins];
-    int sigma_grid_max;   // ordered-int max scale over the grid tier
+    int sigma_grid_max;   // ordered-int max scale over the main tier
+    unsigned n_main;      // kept Gaussians in the main tier
 };
 
 __device__ __forceinline__ bool finite3(float a, float b, float c) {
@@ -111,78 +113,102 @@ __global__ void __launch_bounds__(kThreads) k_repack(
     }
 }
 
-struct GridParams {
+struct OrderParams {
     float lo[3];
-    float inv_h;
-    int dims[3];
-    float sigma_tier;
-    float coarse_inv[3];  // coarse cells per unit length for the large tier
-    uint32_t ncells;
+    float inv_cube;     // 2^kSceneMortonBits / (edge of the scene cube)
+    float sigma_tier;   // Gaussians with a larger max scale form the large tier
 };
 
-__device__ __forceinline__ int cell_coord(float x, float lo, float inv_h, int dim) {
-    int c = (int)floorf((x - lo) * inv_h);
-    return min(max(c, 0), dim - 1);
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
 }
 
-// Position of x inside its cell on a 2^kFineBits grid (orders Gaussians inside
-// a cell so that chunks of 32 consecutive ones are spatially compact).
-__device__ __forceinline__ uint32_t fine_coord(float x, float lo, float inv_h, int c) {
-    float f = ((x - lo) * inv_h - (float)c) * (float)(1 << kFineBits);
-    return (uint32_t)min(max((int)floorf(f), 0), (1 << kFineBits) - 1);
+__device__ __forceinline__ uint32_t morton_coord(float x, float lo, float inv) {
+    const float f = (x - lo) * inv;
+    return (uint32_t)min(max((int)floorf(f), 0), (1 << kSceneMortonBits) - 1);
 }
 
-__device__ __forceinline__ uint32_t fine_morton(uint32_t fx, uint32_t fy, uint32_t fz) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int b = 0; b < kFineBits; ++b)
-        m |= (((fx >> b) & 1u) << (3 * b)) | (((fy >> b) & 1u) << (3 * b + 1)) |
-             (((fz >> b) & 1u) << (3 * b + 2));
-    return m;
-}
-
-constexpr int kFineKeyBits = 3 * kFineBits;
-
-// Sort key of each Gaussian: (grid cell, fine position) for the grid tier,
-// (ncells + coarse cell, fine position) for the large tier, and
-// ncells + kCoarse^3 for dropped rows.
+// Sort key of each Gaussian: tier bit above the 30-bit Morton code of its
+// mean; dropped rows sort last.
 __global__ void __launch_bounds__(kThreads) k_keys(const float4 *__restrict__ pos,
                                                    const uint8_t *__restrict__ code, int64_t n,
-                                                   GridParams g, uint32_t *__restrict__ keys,
+                                                   OrderParams g, uint32_t *__restrict__ keys,
                                                    uint32_t *__restrict__ vals,
                                                    BuildStats *__restrict__ st) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
-    const uint32_t ncoarse = kCoarseDim * kCoarseDim * kCoarseDim;
-    uint32_t key = (g.ncells + ncoarse) << kFineKeyBits;
+    uint32_t key = 0xFFFFFFFFu;
     if (code[i] == 1) {
-        float4 p = pos[i];
-        if (p.w <= g.sigma_tier) {
-            int ix = cell_coord(p.x, g.lo[0], g.inv_h, g.dims[0]);
-            int iy = cell_coord(p.y, g.lo[1], g.inv_h, g.dims[1]);
-            int iz = cell_coord(p.z, g.lo[2], g.inv_h, g.dims[2]);
-            uint32_t cell = (uint32_t)ix + (uint32_t)g.dims[0] * ((uint32_t)iy + (uint32_t)g.dims[1] * (uint32_t)iz);
-            uint32_t f = fine_morton(fine_coord(p.x, g.lo[0], g.inv_h, ix), fine_coord(p.y, g.lo[1], g.inv_h, iy),
-                                     fine_coord(p.z, g.lo[2], g.inv_h, iz));
-            key = (cell << kFineKeyBits) | f;
+        const float4 p = pos[i];
+        const uint32_t m = spread10(morton_coord(p.x, g.lo[0], g.inv_cube)) |
+                           (spread10(morton_coord(p.y, g.lo[1], g.inv_cube)) << 1) |
+                           (spread10(morton_coord(p.z, g.lo[2], g.inv_cube)) << 2);
+        const bool large = p.w > g.sigma_tier;
+        key = (large ? 0x40000000u : 0u) | m;
+        if (!large) {
             atomicMax(&st->sigma_grid_max, float_to_ordered(p.w));
-        } else {
-            int cx = cell_coord(p.x, g.lo[0], g.coarse_inv[0], kCoarseDim);
-            int cy = cell_coord(p.y, g.lo[1], g.coarse_inv[1], kCoarseDim);
-            int cz = cell_coord(p.z, g.lo[2], g.coarse_inv[2], kCoarseDim);
-            uint32_t f = fine_morton(fine_coord(p.x, g.lo[0], g.coarse_inv[0], cx),
-                                     fine_coord(p.y, g.lo[1], g.coarse_inv[1], cy),
-                                     fine_coord(p.z, g.lo[2], g.coarse_inv[2], cz));
-            key = ((g.ncells + (uint32_t)(cx + kCoarseDim * (cy + kCoarseDim * cz))) << kFineKeyBits) | f;
+            atomicAdd(&st->n_main, 1u);
         }
     }
     keys[i] = key;
     vals[i] = (uint32_t)i;
 }
 
-__global__ void k_count_keys(const uint32_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ cnt) {
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[keys[i] >> kFineKeyBits], 1u);
+// Means in sorted order (input of the greedy chunking).
+__global__ void k_gather_pos(const uint32_t *__restrict__ perm, const float4 *__restrict__ pos, int n,
+                             float4 *__restrict__ spos) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) spos[p] = pos[perm[p]];
+}
+
+// Greedy chunking, one thread per segment of kSegment sorted Gaussians
+// (segments split the two tiers separately, and every segment starts a new
+// chunk): a chunk takes the next Gaussian unless it already holds 32 or its
+// box would exceed `extent` along an axis.  Without `base`, writes the
+// segment's chunk count; with it (the exclusive scan of the counts), writes
+// each Gaussian's slot = 32 * chunk + lane.
+__global__ void k_chunk_greedy(const float4 *__restrict__ spos, int n_main, int n_kept, int seg_main,
+                               int nseg, float ext_main, float ext_large, const uint32_t *__restrict__ base,
+                               uint32_t *__restrict__ counts, uint32_t *__restrict__ slot) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nseg) return;
+    int p0, p1;
+    if (sg < seg_main) {
+        p0 = sg * kSegment;
+        p1 = min(n_main, p0 + kSegment);
+    } else {
+        p0 = n_main + (sg - seg_main) * kSegment;
+        p1 = min(n_kept, p0 + kSegment);
+    }
+    const float L = sg < seg_main ? ext_main : ext_large;
+    const uint32_t c0 = base ? base[sg] : 0u;
+    uint32_t c = 0;
+    int k = 0;
+    float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+    for (int p = p0; p < p1; ++p) {
+        const float4 P = spos[p];
+        if (k > 0) {
+            const float nlx = fminf(lx, P.x), nly = fminf(ly, P.y), nlz = fminf(lz, P.z);
+            const float nhx = fmaxf(hx, P.x), nhy = fmaxf(hy, P.y), nhz = fmaxf(hz, P.z);
+            if (k == kChunk || fmaxf(fmaxf(nhx - nlx, nhy - nly), nhz - nlz) > L) {
+                ++c;
+                k = 0;
+            } else {
+                lx = nlx; ly = nly; lz = nlz; hx = nhx; hy = nhy; hz = nhz;
+            }
+        }
+        if (k == 0) {
+            lx = hx = P.x; ly = hy = P.y; lz = hz = P.z;
+        }
+        if (base) slot[p] = (c0 + c) * kChunk + (uint32_t)k;
+        ++k;
+    }
+    if (!base) counts[sg] = p1 > p0 ? c + 1 : 0u;
 }
 
 // Every slot starts as padding: a point at 1e18 with zero covariance.
@@ -197,17 +223,15 @@ __global__ void k_fill_padding(ChunkBlock *__restrict__ blocks, int nchunks, flo
     slot_smax[t] = -1.f;  // marks padding for the header pass
 }
 
-// Sorted Gaussian p of cell c goes to slot cell_slot[c] + (p - cell_first[c]).
-__global__ void k_scatter_slots(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ perm, int n_gauss,
-                                const uint32_t *__restrict__ cell_first, const uint32_t *__restrict__ cell_slot,
-                                const float4 *__restrict__ pos, const float4 *__restrict__ covA,
+// Sorted Gaussian p goes to slot[p].
+__global__ void k_scatter_slots(const uint32_t *__restrict__ slot_in, const uint32_t *__restrict__ perm,
+                                int n_gauss, const float4 *__restrict__ pos, const float4 *__restrict__ covA,
                                 const float4 *__restrict__ covB, ChunkBlock *__restrict__ blocks,
                                 float *__restrict__ slot_smax, float *__restrict__ smax,
                                 int32_t *__restrict__ index, int32_t *__restrict__ slot_of) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_gauss) return;
-    const uint32_t c = keys[p] >> kFineKeyBits;
-    const uint32_t slot = cell_slot[c] + ((uint32_t)p - cell_first[c]);
+    const uint32_t slot = slot_in[p];
     const uint32_t i = perm[p];
     const float4 P = pos[i], A = covA[i], B = covB[i];
     ChunkBlock &b = blocks[slot / kChunk];
@@ -221,8 +245,10 @@ __global__ void k_scatter_slots(const uint32_t *__restrict__ keys, const uint32_
     slot_of[p] = (int32_t)slot;
 }
 
-// One warp per chunk: the box of its real slots and their largest scale.
-__global__ void k_chunk_headers(ChunkBlock *__restrict__ blocks, int nchunks, const float *__restrict__ slot_smax) {
+// One warp per chunk: the box of its real slots, their largest scale and
+// their number, into the block header and the compact chunk-box array.
+__global__ void k_chunk_headers(ChunkBlock *__restrict__ blocks, int nchunks, const float *__restrict__ slot_smax,
+                                NodeBox *__restrict__ chead) {
     int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (c >= nchunks) return;
@@ -242,22 +268,38 @@ __global__ void k_chunk_headers(ChunkBlock *__restrict__ blocks, int nchunks, co
         hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
         sg = fmaxf(sg, __shfl_xor_sync(0xffffffffu, sg, o));
     }
+    const int nreal = __popc(__ballot_sync(0xffffffffu, real));
     if (lane == 0) {
-        b.lo = make_float4(lx, ly, lz, sg);
-        b.hi = make_float4(hx, hy, hz, 0.f);
+        const float4 lo = make_float4(lx, ly, lz, sg), hi = make_float4(hx, hy, hz, (float)nreal);
+        b.lo = lo;
+        b.hi = hi;
+        chead[c] = NodeBox{lo, hi};
     }
 }
 
-// Slots per cell: the cell's count rounded up to a multiple of kCellAlign
-// (the dropped bucket, the last one, gets none).  kCellAlign = 32 would start
-// every cell on a chunk boundary (tighter chunk boxes, more chunks); measured
-// on the tabletop workloads, the kernel's cost follows the number of
-// (primitive, chunk) hits, so cells are packed densely.
-constexpr uint32_t kCellAlign = 1;
-__global__ void k_pad_counts(const uint32_t *__restrict__ cnt, uint32_t *__restrict__ pcnt, uint32_t nkeys) {
-    uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > nkeys) return;
-    pcnt[c] = (c + 1 < nkeys) ? ((cnt[c] + kCellAlign - 1) / kCellAlign) * kCellAlign : 0u;
+// One warp per node: the union of its (up to) 32 children.
+__global__ void k_node_level(const NodeBox *__restrict__ child, int nchild, NodeBox *__restrict__ node, int nnode) {
+    int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (k >= nnode) return;
+    const int c = k * 32 + lane;
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, sg = 0.f;
+    if (c < nchild) {
+        const NodeBox b = child[c];
+        lx = b.lo.x; ly = b.lo.y; lz = b.lo.z; sg = b.lo.w;
+        hx = b.hi.x; hy = b.hi.y; hz = b.hi.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        sg = fmaxf(sg, __shfl_xor_sync(0xffffffffu, sg, o));
+    }
+    if (lane == 0) node[k] = NodeBox{make_float4(lx, ly, lz, sg), make_float4(hx, hy, hz, 0.f)};
 }
 
 struct DevBuf {
@@ -316,7 +358,7 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     sc->n_invalid = hs.n_invalid;
     const int64_t kept_est = hs.n_kept;
 
-    // ---- grid shape (host): extent of the kept means, cell size, tier cut
+    // ---- order parameters (host): extent of the kept means, tier cut, chunk extent
     float lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     if (kept_est > 0) {
         for (int k = 0; k < 3; ++k) {
@@ -343,101 +385,104 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
             }
         }
     }
+    // chunk extent limit: twice the edge of a box that holds 32 Gaussians at
+    // the mean density of the bounding box (cell_size overrides); the large
+    // tier, sparse by construction, allows four times that
     float h = d->cell_size;
     if (!(h > 0.f)) {
         double vol = (double)ext[0] * ext[1] * ext[2];
-        h = (float)cbrt(vol * 32.0 / (double)std::max<int64_t>(kept_est, 1));
+        h = 2.f * (float)cbrt(vol * 32.0 / (double)std::max<int64_t>(kept_est, 1));
     }
     h = std::max(h, emax / 1024.f);
-    int dims[3];
-    for (;;) {
-        int64_t tot = 1;
-        for (int k = 0; k < 3; ++k) {
-            dims[k] = std::max(1, (int)ceilf(ext[k] / h));
-            tot *= dims[k];
-        }
-        if (tot <= kMaxCells) break;
-        h *= 1.25f;
-    }
-    GridParams g;
-    for (int k = 0; k < 3; ++k) {
-        g.lo[k] = lo[k];
-        g.dims[k] = dims[k];
-        g.coarse_inv[k] = (float)kCoarseDim / ext[k];
-    }
-    g.inv_h = 1.f / h;
+    OrderParams g;
+    for (int k = 0; k < 3; ++k) g.lo[k] = lo[k];
+    g.inv_cube = (float)(1 << kSceneMortonBits) / emax;
     g.sigma_tier = sigma_tier;
-    g.ncells = (uint32_t)((int64_t)dims[0] * dims[1] * dims[2]);
-    sc->ncells = g.ncells;
-    const uint32_t ncoarse = kCoarseDim * kCoarseDim * kCoarseDim;
-    const uint32_t nkeys = g.ncells + ncoarse + 1;  // + dropped
-    int bits = 1;
-    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)nkeys) ++bits;
-    bits += kFineKeyBits;
-    if (bits > 32) {
-        set_error("internal: grid too large for 32-bit sort keys");
-        return CS_ERR_CUDA;
-    }
 
-    // ---- keys, stable sort, key starts
+    // ---- keys, stable sort
     uint32_t *keys[2] = {(uint32_t *)tmp_kv.p, (uint32_t *)tmp_kv.p + nn};
     uint32_t *vals[2] = {(uint32_t *)tmp_kv.p + 2 * nn, (uint32_t *)tmp_kv.p + 3 * nn};
-    size_t hist_n = std::max(sort_hist_elems((size_t)nn), (size_t)nkeys + 1);
-    size_t scan_n = scan_tmp_elems(hist_n);
-    CS_CUDA(cudaMalloc(&tmp_hist.p, 4 * hist_n));
+    size_t hist_n = sort_hist_elems((size_t)nn);
+    const int64_t nseg_max = 2 + (nn + kSegment - 1) / kSegment;
+    size_t scan_n = scan_tmp_elems(std::max(hist_n, (size_t)nseg_max + 1));
+    CS_CUDA(cudaMalloc(&tmp_hist.p, 4 * std::max(hist_n, (size_t)nseg_max + 1)));
     CS_CUDA(cudaMalloc(&tmp_scan.p, 4 * scan_n));
     int res = 0;
     if (n > 0) {
         k_keys<<<blocks_for(n), kThreads, 0, s>>>(upos, code, n, g, keys[0], vals[0], st);
         count_launches(1);
-        res = radix_sort(keys, vals, (size_t)n, bits, (uint32_t *)tmp_hist.p,
-                         (uint32_t *)tmp_scan.p, s);
+        res = radix_sort(keys, vals, (size_t)n, 32, (uint32_t *)tmp_hist.p, (uint32_t *)tmp_scan.p, s);
     }
-
-    // ---- real and padded (slot) starts of every cell
-    uint32_t *cnt = (uint32_t *)tmp_hist.p;  // nkeys + 1 counters
-    DevBuf tmp_first, tmp_pcnt;
-    CS_CUDA(cudaMalloc(&tmp_first.p, 4 * ((size_t)nkeys + 1)));
-    CS_CUDA(cudaMalloc(&tmp_pcnt.p, 4 * ((size_t)nkeys + 1)));
-    uint32_t *first = (uint32_t *)tmp_first.p, *pcnt = (uint32_t *)tmp_pcnt.p;
-    CS_CUDA(cudaMemsetAsync(cnt, 0, 4 * ((size_t)nkeys + 1), s));
-    if (n > 0) {
-        k_count_keys<<<blocks_for(n), kThreads, 0, s>>>(keys[res], n, cnt);
-        count_launches(1);
-    }
-    scan_exclusive(cnt, first, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
-    k_pad_counts<<<blocks_for((int64_t)nkeys + 1), kThreads, 0, s>>>(cnt, pcnt, nkeys);
-    count_launches(1);
-    DevBuf tmp_slot;
-    CS_CUDA(cudaMalloc(&tmp_slot.p, 4 * ((size_t)nkeys + 1)));
-    uint32_t *slot_first = (uint32_t *)tmp_slot.p;
-    scan_exclusive(pcnt, slot_first, (size_t)nkeys + 1, (uint32_t *)tmp_scan.p, s);
-    uint32_t bounds[4] = {0, 0, 0, 0};
-    CS_CUDA(cudaMemcpyAsync(&bounds[0], first + g.ncells, 4, cudaMemcpyDeviceToHost, s));
-    CS_CUDA(cudaMemcpyAsync(&bounds[1], first + g.ncells + ncoarse, 4, cudaMemcpyDeviceToHost, s));
-    CS_CUDA(cudaMemcpyAsync(&bounds[2], slot_first + g.ncells, 4, cudaMemcpyDeviceToHost, s));
-    CS_CUDA(cudaMemcpyAsync(&bounds[3], slot_first + g.ncells + ncoarse, 4, cudaMemcpyDeviceToHost, s));
+    unsigned n_main_u = 0;
     int sgm = INT_MIN;
+    CS_CUDA(cudaMemcpyAsync(&n_main_u, &st->n_main, 4, cudaMemcpyDeviceToHost, s));
     CS_CUDA(cudaMemcpyAsync(&sgm, &st->sigma_grid_max, 4, cudaMemcpyDeviceToHost, s));
     CS_CUDA(cudaStreamSynchronize(s));
-    const int64_t n_grid = bounds[0], n_kept = bounds[1];
-    const int64_t grid_end = bounds[2], slot_end = bounds[3];
-    if (n_kept != kept_est || slot_end > ((int64_t)1 << 31) - kChunk) {
-        set_error("internal: slot layout mismatch in scene build");
+    const int64_t n_kept = kept_est, n_main = n_main_u;
+    if (n_kept > ((int64_t)1 << 31) / 2) {
+        set_error("scene too large (more than 2^30 kept Gaussians)");
+        return CS_ERR_INVALID_ARG;
+    }
+
+    // ---- greedy chunking in segments, then chunk bases by a scan
+    const int seg_main = (int)((n_main + kSegment - 1) / kSegment);
+    const int nseg = seg_main + (int)((n_kept - n_main + kSegment - 1) / kSegment);
+    DevBuf tmp_spos, tmp_cnt, tmp_base, tmp_slot;
+    CS_CUDA(cudaMalloc(&tmp_spos.p, 16 * (size_t)std::max<int64_t>(n_kept, 1)));
+    CS_CUDA(cudaMalloc(&tmp_cnt.p, 4 * ((size_t)nseg + 1)));
+    CS_CUDA(cudaMalloc(&tmp_base.p, 4 * ((size_t)nseg + 1)));
+    CS_CUDA(cudaMalloc(&tmp_slot.p, 4 * (size_t)std::max<int64_t>(n_kept, 1)));
+    float4 *spos = (float4 *)tmp_spos.p;
+    uint32_t *seg_cnt = (uint32_t *)tmp_cnt.p, *seg_base = (uint32_t *)tmp_base.p, *slot = (uint32_t *)tmp_slot.p;
+    const float ext_main = h, ext_large = 4.f * h;
+    CS_CUDA(cudaMemsetAsync(seg_cnt, 0, 4 * ((size_t)nseg + 1), s));
+    if (n_kept > 0) {
+        k_gather_pos<<<blocks_for(n_kept), kThreads, 0, s>>>(vals[res], upos, (int)n_kept, spos);
+        k_chunk_greedy<<<(nseg + 127) / 128, 128, 0, s>>>(spos, (int)n_main, (int)n_kept, seg_main, nseg, ext_main,
+                                                          ext_large, nullptr, seg_cnt, nullptr);
+        count_launches(2);
+    }
+    scan_exclusive(seg_cnt, seg_base, (size_t)nseg + 1, (uint32_t *)tmp_scan.p, s);
+    uint32_t bounds[2] = {0, 0};  // first chunk of the large tier, number of chunks
+    CS_CUDA(cudaMemcpyAsync(&bounds[0], seg_base + seg_main, 4, cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaMemcpyAsync(&bounds[1], seg_base + nseg, 4, cudaMemcpyDeviceToHost, s));
+    if (n_kept > 0) {
+        k_chunk_greedy<<<(nseg + 127) / 128, 128, 0, s>>>(spos, (int)n_main, (int)n_kept, seg_main, nseg, ext_main,
+                                                          ext_large, seg_base, nullptr, slot);
+        count_launches(1);
+    }
+    CS_CUDA(cudaGetLastError());
+    CS_CUDA(cudaStreamSynchronize(s));
+    const int nchunks = (int)bounds[1];
+    if (nchunks > ((int64_t)1 << 31) / kChunk) {
+        set_error("internal: chunk count overflow in scene build");
         return CS_ERR_CUDA;
     }
-    const int nchunks = (int)((slot_end + kChunk - 1) / kChunk);
+    int nnodes[kLevels];
+    {
+        int m = nchunks;
+        for (int l = 0; l < kLevels; ++l) {
+            m = (m + 31) / 32;
+            nnodes[l] = std::max(m, nchunks > 0 ? 1 : 0);
+        }
+    }
 
-    // owned memory: chunk blocks, slot starts of the cells, and per sorted
+    // owned memory: chunk blocks, chunk boxes, node levels, and per sorted
     // Gaussian its largest scale, input row and slot (export)
     const int64_t kmax = std::max<int64_t>(n_kept, 1);
-    size_t bytes_blocks = sizeof(ChunkBlock) * (size_t)std::max(nchunks, 1);
-    size_t bytes_keys = (size_t)4 * (nkeys + 1);
-    size_t off_keys = (bytes_blocks + 255) & ~(size_t)255;
-    size_t off_smax = (off_keys + bytes_keys + 255) & ~(size_t)255;
-    size_t off_index = (off_smax + 4 * (size_t)kmax + 255) & ~(size_t)255;
-    size_t off_slot = (off_index + 4 * (size_t)kmax + 255) & ~(size_t)255;
-    size_t total = off_slot + 4 * (size_t)kmax;
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = align(sizeof(ChunkBlock) * (size_t)std::max(nchunks, 1));
+    const size_t off_chead = off;
+    off = align(off + sizeof(NodeBox) * (size_t)std::max(nchunks, 1));
+    size_t off_nodes[kLevels];
+    for (int l = 0; l < kLevels; ++l) {
+        off_nodes[l] = off;
+        off = align(off + sizeof(NodeBox) * (size_t)std::max(nnodes[l], 1));
+    }
+    const size_t off_smax = off;
+    const size_t off_index = align(off_smax + 4 * (size_t)kmax);
+    const size_t off_slot = align(off_index + 4 * (size_t)kmax);
+    const size_t total = off_slot + 4 * (size_t)kmax;
     void *blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, total);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation
@@ -447,23 +492,32 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     sc->device_bytes = (int64_t)total;
     char *base = (char *)blk;
     ChunkBlock *blocks = (ChunkBlock *)base;
-    uint32_t *kstart = (uint32_t *)(base + off_keys);
+    NodeBox *chead = (NodeBox *)(base + off_chead);
+    NodeBox *nodes[kLevels];
+    for (int l = 0; l < kLevels; ++l) nodes[l] = (NodeBox *)(base + off_nodes[l]);
     float *smax = (float *)(base + off_smax);
     int32_t *index = (int32_t *)(base + off_index);
     int32_t *slot_of = (int32_t *)(base + off_slot);
-    CS_CUDA(cudaMemcpyAsync(kstart, slot_first, bytes_keys, cudaMemcpyDeviceToDevice, s));
     if (nchunks > 0) {
         DevBuf tmp_ss;
         CS_CUDA(cudaMalloc(&tmp_ss.p, 4 * (size_t)nchunks * kChunk));
         float *slot_smax = (float *)tmp_ss.p;
         k_fill_padding<<<(unsigned)(((int64_t)nchunks * kChunk + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             blocks, nchunks, slot_smax);
-        k_scatter_slots<<<blocks_for(n_kept), kThreads, 0, s>>>(keys[res], vals[res], (int)n_kept, first, slot_first,
-                                                                upos, ucovA, ucovB, blocks, slot_smax, smax,
-                                                                index, slot_of);
+        k_scatter_slots<<<blocks_for(n_kept), kThreads, 0, s>>>(slot, vals[res], (int)n_kept, upos, ucovA, ucovB,
+                                                                blocks, slot_smax, smax, index, slot_of);
         k_chunk_headers<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            blocks, nchunks, slot_smax);
+            blocks, nchunks, slot_smax, chead);
         count_launches(3);
+        const NodeBox *child = chead;
+        int nchild = nchunks;
+        for (int l = 0; l < kLevels; ++l) {
+            k_node_level<<<(unsigned)(((int64_t)nnodes[l] * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+                child, nchild, nodes[l], nnodes[l]);
+            count_launches(1);
+            child = nodes[l];
+            nchild = nnodes[l];
+        }
         CS_CUDA(cudaGetLastError());
         CS_CUDA(cudaStreamSynchronize(s));  // before the temporaries are freed
     }
@@ -471,30 +525,30 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     CS_CUDA(cudaStreamSynchronize(s));
 
     sc->n_kept = n_kept;
-    sc->n_grid = n_grid;
-    sc->n_large = n_kept - n_grid;
+    sc->n_grid = n_main;
+    sc->n_large = n_kept - n_main;
     SceneDev &dv = sc->dev;
     dv.blocks = blocks;
-    dv.cell_start = kstart;
+    dv.chead = chead;
+    for (int l = 0; l < kLevels; ++l) {
+        dv.nodes[l] = nodes[l];
+        dv.nnodes[l] = nchunks > 0 ? nnodes[l] : 0;
+    }
     dv.smax = smax;
     dv.index = index;
     dv.slot_of = slot_of;
     dv.n_gauss = (int)n_kept;
-    dv.grid_end = (int)grid_end;
-    dv.slot_end = (int)slot_end;
     dv.nchunks = nchunks;
+    dv.large_chunk0 = (int)bounds[0];
+    dv.chunk_extent = ext_main;
     for (int k = 0; k < 3; ++k) {
-        dv.dims[k] = dims[k];
-        dv.lo[k] = lo[k];
         dv.bb_lo[k] = lo[k];
         dv.bb_hi[k] = lo[k] + ext[k];
     }
-    dv.h = h;
-    dv.inv_h = g.inv_h;
     float sg = 0.f;
     if (sgm != INT_MIN) sg = __builtin_bit_cast(float, sgm >= 0 ? sgm : sgm ^ 0x7FFFFFFF);
     dv.sigma_tier = sg;
-    // slack for the FP32 rounding of cell coordinates and distances
+    // slack for the FP32 rounding of distances and box gaps
     float amax = 0.f;
     for (int k = 0; k < 3; ++k) amax = std::max({amax, fabsf(lo[k]), fabsf(hi[k])});
     dv.pad_abs = 4e-6f * std::max(amax, emax) + 1e-30f;

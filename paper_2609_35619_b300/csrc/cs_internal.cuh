@@ -16,12 +16,11 @@ namespace cs {
 // ---------------------------------------------------------------- constants
 constexpr int kChunk = 32;             // Gaussians per chunk record (warp-level cull unit)
 constexpr int kMortonBits = 8;         // bits per axis of the query sort key
-constexpr int kFineBits = 3;           // bits per axis of the order inside a grid cell
-constexpr int kCoarseDim = 16;         // coarse grid per axis for ordering the large tier
+constexpr int kSceneMortonBits = 10;   // bits per axis of the scene order
+constexpr int kSegment = 1024;         // Gaussians per greedy chunking segment
 constexpr int kSigmaBins = 512;        // log2 histogram of the largest scale
 constexpr float kSigmaLog2Lo = -32.f;  // histogram covers 2^-32 .. 2^32 in 1/8 octaves
 constexpr float kSigmaBinsPerOctave = 8.f;
-constexpr int64_t kMaxCells = 1ll << 22;
 constexpr float kReachPadRel = 1e-4f;  // relative padding of every cull radius
 
 // device error word bits
@@ -36,11 +35,13 @@ constexpr long long kWaitPolls = 1ll << 27;
 // Repacked Gaussians are stored in chunk blocks of kChunk = 32 slots, one
 // 1184-byte block each, so that a run of chunks is one contiguous 1-D bulk
 // copy and lane l of a warp reads slot l of a chunk with conflict-free 4-byte
-// shared-memory loads.  Slots follow the sort order (grid cell, then a fine
-// Morton code inside the cell), so a chunk's box is small; a cell may be
-// padded to an alignment (see k_pad_counts).
+// shared-memory loads.  Gaussians follow a global Morton order of their means
+// (10 bits per axis over the scene cube), the large tier after the rest; a
+// chunk takes consecutive Gaussians while their box stays within an extent
+// limit (and at most 32), so chunk boxes are compact wherever the scene is
+// dense or sparse.  Unused slots are padding.
 //   lo  = (min mu over the chunk, max scale over the chunk)
-//   hi  = (max mu over the chunk, 0)
+//   hi  = (max mu over the chunk, number of real slots)
 //   x, y, z          the means
 //   sxx, syy, szz    the covariance diagonal (Eq. 2)
 //   sxy2, sxz2, syz2 the off-diagonals, doubled so d^T Sigma d takes 9 FP32 ops
@@ -56,20 +57,30 @@ struct __align__(16) ChunkBlock {
 static_assert(sizeof(ChunkBlock) == 1184, "chunk block layout");
 static_assert(sizeof(ChunkBlock) % 16 == 0, "bulk copies move whole 16-byte units");
 
+// Bounding record of a chunk or of a node of the chunk hierarchy: the box of
+// the means below it and their largest scale (lo.w).  Node k of level 1
+// covers chunks [32k, 32k + 32), node k of level 2 covers level-1 nodes
+// [32k, 32k + 32), and so on: an implicit fan-out-32 tree over the Morton
+// order that the query producer descends one ballot per level.
+struct __align__(16) NodeBox {
+    float4 lo;
+    float4 hi;
+};
+constexpr int kLevels = 3;  // node levels above the chunks
+
 struct SceneDev {
-    const ChunkBlock *blocks = nullptr;    // [nchunks]
-    const uint32_t *cell_start = nullptr;  // [ncells + 1]: first slot of each cell (multiple of 32)
-    const float *smax = nullptr;           // [n_gauss] largest scale per sorted Gaussian (export only)
-    const int32_t *index = nullptr;        // [n_gauss] input row per sorted Gaussian (export only)
-    const int32_t *slot_of = nullptr;      // [n_gauss] slot of each sorted Gaussian (export only)
+    const ChunkBlock *blocks = nullptr;  // [nchunks]
+    const NodeBox *chead = nullptr;      // [nchunks] chunk boxes (copy of the block headers)
+    const NodeBox *nodes[kLevels] = {nullptr, nullptr, nullptr};  // level 1..3
+    int nnodes[kLevels] = {0, 0, 0};
+    const float *smax = nullptr;         // [n_gauss] largest scale per sorted Gaussian (export only)
+    const int32_t *index = nullptr;      // [n_gauss] input row per sorted Gaussian (export only)
+    const int32_t *slot_of = nullptr;    // [n_gauss] slot of each sorted Gaussian (export only)
     int n_gauss = 0;      // kept Gaussians
-    int grid_end = 0;     // slots [0, grid_end) hold the grid tier
-    int slot_end = 0;     // slots [grid_end, slot_end) hold the large tier
-    int nchunks = 0;      // ceil(slot_end / 32)
-    int dims[3] = {1, 1, 1};
-    float lo[3] = {0, 0, 0};   // grid origin
-    float h = 1.f, inv_h = 1.f;
-    float sigma_tier = 0.f;    // max scale over the grid tier
+    int nchunks = 0;      // chunks of both tiers
+    int large_chunk0 = 0; // first chunk of the large tier
+    float chunk_extent = 0.f;  // extent limit of a chunk of the main tier
+    float sigma_tier = 0.f;    // max scale over the main tier
     float pad_abs = 0.f;       // absolute slack added to cull radii
     float bb_lo[3] = {0, 0, 0}, bb_hi[3] = {1, 1, 1};  // box used for query sort keys
 };
@@ -104,7 +115,6 @@ struct Scene {
     std::mutex tune_mu;
     std::unordered_map<uint32_t, int32_t> tuned;
     int64_t n_input = 0, n_kept = 0, n_grid = 0, n_large = 0, n_invalid = 0;
-    int64_t ncells = 0;
     int64_t device_bytes = 0;
     void *blocks[8] = {};            // owned device allocations
     int nblocks = 0;

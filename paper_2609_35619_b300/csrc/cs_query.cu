@@ -67,19 +67,24 @@ struct EvalArgs {
 template <int NCW_, int QW_, int NS_, int CHB_, int MINB_, int GROUP_ = 2, int IL_ = 0>
 struct Cfg {
     static constexpr int NCW = NCW_, QW = QW_, NS = NS_, CHB = CHB_, MINB = MINB_, GROUP = GROUP_;
-    // IL = 1: consumer warp w takes rows w, w + NCW, ... of the tile (its
-    // primitives spread over the tile, so the warps' loads even out);
-    // IL = 0: rows w QW .. w QW + QW - 1 (a compact warp box)
+    // IL = 0: consumer warp w takes rows w QW .. w QW + QW - 1 of the tile (a
+    // compact warp box); IL = 1: rows w, w + NCW, ...; IL = 2: row pairs
+    // (2w, 2w + 1), (2w + 2 NCW, 2w + 2 NCW + 1), ...  Spreading a warp's
+    // primitives over the tile evens out the warps' loads (they share the
+    // stage ring, so the slowest sets the pace); pairs keep the two
+    // primitives evaluated together close.
     static constexpr int IL = IL_;
-    __device__ static int row(int warp, int j) { return IL ? j * NCW + warp : warp * QW + j; }
+    __device__ static int row(int warp, int j) {
+        return IL == 1 ? j * NCW + warp : IL == 2 ? (j >> 1) * 2 * NCW + 2 * warp + (j & 1) : warp * QW + j;
+    }
     static_assert(CHB <= 32, "one lane tests each chunk slot of a stage");
     static_assert(QW == 8 || QW == 16, "primitive masks are tested 32 / QW chunks per round");
 };
 
 struct SlotMeta {
     int chunk;  // global chunk id
-    int lo;     // first valid lane of the chunk in this slot
-    int hi;     // one past the last valid lane
+    int lo;     // 0
+    int hi;     // real slots of the chunk (0: no chunk)
     int pad;
 };
 
@@ -156,10 +161,6 @@ __device__ __noinline__ long long wait_phase(uint64_t *bar, unsigned parity, lon
     return -1;
 }
 
-__device__ __forceinline__ int cell_of(float x, float lo, float inv_h, int dim) {
-    int c = (int)floorf((x - lo) * inv_h);
-    return min(max(c, 0), dim - 1);
-}
 
 // ------------------------------------------------------------- producer
 template <class C>
@@ -203,16 +204,16 @@ struct Producer {
         ++k;
         open_stage();
     }
-    // Stage chunks [c, c + len) (contiguous blocks) covering sorted Gaussians
-    // [s, e) of the stream.
-    __device__ void emit_run(int c, int len, int s, int e) {
+    // Stage chunks [c, c + len) (contiguous blocks); slot metadata carries
+    // each chunk's index and its number of real slots.
+    __device__ void emit_run(int c, int len) {
         while (len > 0 && !failed) {
             const int st = k % C::NS;
             const int take = min(len, C::CHB - nslot);
             if (lane < take) {
-                int cc = c + lane;
-                sm->meta[st][nslot + lane] = SlotMeta{cc, max(s - cc * kChunk, 0),
-                                                      min(e - cc * kChunk, kChunk), 0};
+                const int cc = c + lane;
+                const int nreal = (int)__ldg(&sc->chead[cc].hi.w);
+                sm->meta[st][nslot + lane] = SlotMeta{cc, 0, nreal, 0};
             }
             if (lane == 0) {
                 unsigned bytes = (unsigned)take * (unsigned)sizeof(ChunkBlock);
@@ -226,47 +227,45 @@ struct Producer {
             if (nslot == C::CHB) close_stage();
         }
     }
-    // Every chunk overlapping sorted Gaussians [s, e) (a grid row span: the
-    // row's x-range already follows the tile's reach; the consumers test each
-    // chunk against each primitive).
-    __device__ void append_span(int s, int e) {
-        const int c0 = s / kChunk, c1 = (e - 1) / kChunk;
-        emit_run(c0, c1 - c0 + 1, s, e);
+    // Does the tile box + reach meet a chunk or tree node?
+    __device__ bool meets(const NodeBox &b) const {
+        const float R = reach(al, be, b.lo.w, sc->pad_abs);
+        return box_gap2(lx, ly, lz, hx, hy, hz, b.lo, b.hi) <= R * R;
     }
-    // The large tier [s, e): its chunks are spread over the scene, so each is
-    // tested against the tile box first (four header loads in flight per lane).
-    __device__ void append_tested(int s, int e) {
-        const int c0 = s / kChunk, c1 = (e - 1) / kChunk;
-        for (int cb = c0; cb <= c1 && !failed; cb += 128) {
-            bool pass[4];
-            float4 blo[4], bhi[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = cb + 32 * u + lane;
-                if (c <= c1) {
-                    blo[u] = __ldg(&sc->blocks[c].lo);
-                    bhi[u] = __ldg(&sc->blocks[c].hi);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = cb + 32 * u + lane;
-                pass[u] = false;
-                if (c <= c1) {
-                    const float R = reach(al, be, blo[u].w, sc->pad_abs);
-                    pass[u] = box_gap2(lx, ly, lz, hx, hy, hz, blo[u], bhi[u]) <= R * R;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                unsigned m = __ballot_sync(0xffffffffu, pass[u]);
-                const int base = cb + 32 * u;
-                while (m && !failed) {
-                    const int first = __ffs(m) - 1;
-                    const unsigned rest = ~(m >> first);
-                    const int len = rest ? __ffs(rest) - 1 : 32 - first;
-                    emit_run(base + first, len, s, e);
-                    m = (first + len >= 32) ? 0u : (m & ~((1u << (first + len)) - 1u));
+    // Lane-parallel test of the up to 32 records [base, base + 32) of `recs`.
+    __device__ unsigned test32(const NodeBox *recs, int base, int count) const {
+        const int i = base + lane;
+        bool hit = false;
+        if (i < count) hit = meets(recs[i]);
+        return __ballot_sync(0xffffffffu, hit);
+    }
+    // Descend the chunk tree from the top level and stage every chunk whose
+    // box + reach meets the tile box, in increasing chunk order (runs of
+    // consecutive passing chunks are one bulk copy each).
+    __device__ void descend() {
+        const int n3 = sc->nnodes[2], n2 = sc->nnodes[1], n1 = sc->nnodes[0], nc = sc->nchunks;
+        for (int b3 = 0; b3 < n3 && !failed; b3 += 32) {
+            unsigned m3 = test32(sc->nodes[2], b3, n3);
+            while (m3 && !failed) {
+                const int i3 = b3 + __ffs(m3) - 1;
+                m3 &= m3 - 1;
+                unsigned m2 = test32(sc->nodes[1], 32 * i3, n2);
+                while (m2 && !failed) {
+                    const int i2 = 32 * i3 + __ffs(m2) - 1;
+                    m2 &= m2 - 1;
+                    unsigned m1 = test32(sc->nodes[0], 32 * i2, n1);
+                    while (m1 && !failed) {
+                        const int i1 = 32 * i2 + __ffs(m1) - 1;
+                        m1 &= m1 - 1;
+                        unsigned mc = test32(sc->chead, 32 * i1, nc);
+                        while (mc && !failed) {
+                            const int first = __ffs(mc) - 1;
+                            const unsigned rest = ~(mc >> first);
+                            const int len = rest ? __ffs(rest) - 1 : 32 - first;
+                            emit_run(32 * i1 + first, len);
+                            mc = (first + len >= 32) ? 0u : (mc & ~((1u << (first + len)) - 1u));
+                        }
+                    }
                 }
             }
         }
@@ -338,74 +337,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile) {
     pr.lane = lane;
     pr.t0 = t_start;
     const bool any = lx <= hx;  // at least one valid primitive
-    if (any && sc.grid_end > 0) {
-        // ---- grid rows within reach of the tile box (sigma = grid-tier max)
-        const float R = reach(al, be, sc.sigma_tier, sc.pad_abs);
-        const float R2 = R * R;
-        const int iy0 = cell_of(ly - R, sc.lo[1], sc.inv_h, sc.dims[1]);
-        const int iy1 = cell_of(hy + R, sc.lo[1], sc.inv_h, sc.dims[1]);
-        const int iz0 = cell_of(lz - R, sc.lo[2], sc.inv_h, sc.dims[2]);
-        const int iz1 = cell_of(hz + R, sc.lo[2], sc.inv_h, sc.dims[2]);
-        const int ny = iy1 - iy0 + 1;
-        const int nrows = ny * (iz1 - iz0 + 1);
-        const float slack = sc.pad_abs;
-        for (int rb = 0; rb < nrows && !pr.failed; rb += 64) {
-            int start[2] = {0, 0}, cnt[2] = {0, 0};
-            uint32_t kb[2] = {0, 0}, ke[2] = {0, 0};
-            bool want[2] = {false, false};
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int r = rb + 32 * u + lane;
-                if (r < nrows) {
-                    const int iz = iz0 + r / ny, iy = iy0 + r % ny;
-                    float y0 = sc.lo[1] + (float)iy * sc.h - slack, y1 = sc.lo[1] + (float)(iy + 1) * sc.h + slack;
-                    float z0 = sc.lo[2] + (float)iz * sc.h - slack, z1 = sc.lo[2] + (float)(iz + 1) * sc.h + slack;
-                    // first and last rows extend to infinity (clamped cell coordinates)
-                    if (iy == 0) y0 = -INFINITY;
-                    if (iy == sc.dims[1] - 1) y1 = INFINITY;
-                    if (iz == 0) z0 = -INFINITY;
-                    if (iz == sc.dims[2] - 1) z1 = INFINITY;
-                    const float gy = fmaxf(0.f, fmaxf(y0 - hy, ly - y1));
-                    const float gz = fmaxf(0.f, fmaxf(z0 - hz, lz - z1));
-                    const float d2 = fmaf(gy, gy, gz * gz);
-                    if (d2 <= R2) {
-                        const float half = sqrtf(R2 - d2);
-                        const int ix0 = cell_of(lx - half, sc.lo[0], sc.inv_h, sc.dims[0]);
-                        const int ix1 = cell_of(hx + half, sc.lo[0], sc.inv_h, sc.dims[0]);
-                        const uint32_t rowkey =
-                            (uint32_t)sc.dims[0] * ((uint32_t)iy + (uint32_t)sc.dims[1] * (uint32_t)iz);
-                        kb[u] = rowkey + ix0;
-                        ke[u] = rowkey + ix1 + 1;
-                        want[u] = true;
-                    }
-                }
-            }
-            // all four cell-start loads in flight before any is used
-            uint32_t vb[2], ve[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                vb[u] = want[u] ? __ldg(sc.cell_start + kb[u]) : 0u;
-                ve[u] = want[u] ? __ldg(sc.cell_start + ke[u]) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                start[u] = (int)vb[u];
-                cnt[u] = (int)(ve[u] - vb[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                unsigned m = __ballot_sync(0xffffffffu, cnt[u] > 0);
-                while (m && !pr.failed) {
-                    const int src = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int s0 = __shfl_sync(0xffffffffu, start[u], src);
-                    const int c0 = __shfl_sync(0xffffffffu, cnt[u], src);
-                    pr.append_span(s0, s0 + c0);
-                }
-            }
-        }
-    }
-    if (any && sc.slot_end > sc.grid_end && !pr.failed) pr.append_tested(sc.grid_end, sc.slot_end);  // large tier
+    if (any && sc.nchunks > 0) pr.descend();
     pr.finish();
     if (pr.failed) {
         if (lane == 0) atomicOr(a.err, kErrTimeout);
@@ -614,24 +546,18 @@ __device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, c
     A.sum[j] += nb1 ? dc1 : 0.f;
 }
 
-// Lane l of a chunk slot: Gaussian l when the slot's range holds it, else a
-// point that meets no primitive.
+// Lane l of a staged chunk: its slot l (padding slots already hold a point
+// that meets no primitive); an absent chunk (mt.hi == 0) gives that point on
+// every lane.
 __device__ __forceinline__ void lane_gaussian(const ChunkBlock &B, const SlotMeta mt, int lane, LaneG &g) {
-    if (mt.lo == 0 && mt.hi == kChunk) {
+    if (mt.hi > 0) {
         g.x = B.x[lane]; g.y = B.y[lane]; g.z = B.z[lane];
         g.sxx = B.sxx[lane]; g.syy = B.syy[lane]; g.szz = B.szz[lane];
         g.sxy2 = B.sxy2[lane]; g.sxz2 = B.sxz2[lane]; g.syz2 = B.syz2[lane];
     } else {
-        const bool lv = lane >= mt.lo && lane < mt.hi;
-        g.x = lv ? B.x[lane] : 1e18f;
-        g.y = lv ? B.y[lane] : 1e18f;
-        g.z = lv ? B.z[lane] : 1e18f;
-        g.sxx = lv ? B.sxx[lane] : 0.f;
-        g.syy = lv ? B.syy[lane] : 0.f;
-        g.szz = lv ? B.szz[lane] : 0.f;
-        g.sxy2 = lv ? B.sxy2[lane] : 0.f;
-        g.sxz2 = lv ? B.sxz2[lane] : 0.f;
-        g.syz2 = lv ? B.syz2[lane] : 0.f;
+        g.x = 1e18f; g.y = 1e18f; g.z = 1e18f;
+        g.sxx = 0.f; g.syy = 0.f; g.szz = 0.f;
+        g.sxy2 = 0.f; g.sxz2 = 0.f; g.syz2 = 0.f;
     }
 }
 
@@ -689,22 +615,7 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
         }
     }
     LaneG g;
-    if (mt.lo == 0 && mt.hi == kChunk) {  // whole chunk (the common case)
-        g.x = B.x[lane]; g.y = B.y[lane]; g.z = B.z[lane];
-        g.sxx = B.sxx[lane]; g.syy = B.syy[lane]; g.szz = B.szz[lane];
-        g.sxy2 = B.sxy2[lane]; g.sxz2 = B.sxz2[lane]; g.syz2 = B.syz2[lane];
-    } else {
-        const bool lv = lane >= mt.lo && lane < mt.hi;
-        g.x = lv ? B.x[lane] : 1e18f;
-        g.y = lv ? B.y[lane] : 1e18f;
-        g.z = lv ? B.z[lane] : 1e18f;
-        g.sxx = lv ? B.sxx[lane] : 0.f;
-        g.syy = lv ? B.syy[lane] : 0.f;
-        g.szz = lv ? B.szz[lane] : 0.f;
-        g.sxy2 = lv ? B.sxy2[lane] : 0.f;
-        g.sxz2 = lv ? B.sxz2[lane] : 0.f;
-        g.syz2 = lv ? B.syz2[lane] : 0.f;
-    }
+    lane_gaussian(B, mt, lane, g);
     cand += (unsigned long long)__popc(qmask) * (unsigned long long)(mt.hi - mt.lo);
     {
 #pragma unroll
@@ -1003,10 +914,11 @@ __device__ __forceinline__ uint32_t spread8(uint32_t v) {
     return v;
 }
 
-// Sort key of each primitive: its size class (half-octaves of the radius or
-// largest semi-axis, from 1/1024 up) above the Morton code of its centre over
-// the scene box (8 bits per axis).  Tiles of consecutive keys then hold
-// primitives of similar size and position, so their shared cull is tight.
+// Sort key of each primitive: the Morton code of its centre over the scene
+// box (8 bits per axis) above its size class (half-octaves of the radius or
+// largest semi-axis, from 1/1024 up).  Tiles of consecutive keys then hold
+// primitives close together, so the tile box the producer culls with stays
+// small even when a batch is sparse and mixes many sizes.
 __global__ void k_prep_keys(const float *__restrict__ prims, int prim_type, int Q, SceneDev sc,
                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1028,7 +940,7 @@ __global__ void k_prep_keys(const float *__restrict__ prims, int prim_type, int 
         const int half_oct = 2 * ((bits >> 23) & 0xFF) + ((bits >> 22) & 1) - 2 * (127 - 10);
         cls = (uint32_t)min(max(half_oct, 0), 31);
     }
-    keys[j] = (cls << 24) | code;
+    keys[j] = (code << 5) | cls;
     vals[j] = (uint32_t)j;
 }
 
@@ -1131,6 +1043,7 @@ QueryConsts make_consts(const cs_params &p) {
 //   14: 4 x 16, 4 stages x 12 chunks, 3 CTAs/SM
 //   15: 8 x 8, 2 stages x 32 chunks, 2 CTAs/SM
 //   16: shape 1 with the tile's rows interleaved over the consumer warps
+//   17-19: shapes 1, 15, 13 with row pairs interleaved over the consumer warps
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1147,8 +1060,11 @@ using Cfg13 = Cfg<4, 16, 3, 16, 3>;
 using Cfg14 = Cfg<4, 16, 4, 12, 3>;
 using Cfg15 = Cfg<8, 8, 2, 32, 2>;
 using Cfg16 = Cfg<8, 8, 4, 16, 2, 2, 1>;
+using Cfg17 = Cfg<8, 8, 4, 16, 2, 2, 2>;
+using Cfg18 = Cfg<8, 8, 2, 32, 2, 2, 2>;
+using Cfg19 = Cfg<4, 16, 3, 16, 3, 2, 2>;
 using CfgGrad = Cfg<4, 8, 3, 8, 3>;  // the adjoint keeps three gradient sums per primitive
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19};
 constexpr int kDefaultTile = 1;
 
 int tile_configs(int32_t *ids, int32_t cap) {
@@ -1206,6 +1122,9 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 14: return launch_mode<PRIM, Cfg14>(a, s);
         case 15: return launch_mode<PRIM, Cfg15>(a, s);
         case 16: return launch_mode<PRIM, Cfg16>(a, s);
+        case 17: return launch_mode<PRIM, Cfg17>(a, s);
+        case 18: return launch_mode<PRIM, Cfg18>(a, s);
+        case 19: return launch_mode<PRIM, Cfg19>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }
