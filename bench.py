@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 
 NSIGMAS = (0.0, 0.5, 1.0, 2.0)
 OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes)
+# DRAM bytes (read + write) of one forward launch of the fused kernel, from the
+# ncu capture of that case summarised under profiles/, valid for the library
+# version it was taken with (reported as null otherwise)
+TRAFFIC = {"version": "cs_b300 0.2 (sm_103a)", "bytes": 46.037e6 + 0.230e6,
+           "case": "262,144 arm spheres, tile 18, n_sigma 1"}
 WORKLOAD = "tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres fwd+adjoint"
 
 
@@ -47,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiles", default="",
+                    help="ARM,EDGE tile ids for the step (default: chosen by the autotuner before timing)")
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="requests of the serving measurement in the default run")
     ap.add_argument("--no-serve", action="store_true")
@@ -160,19 +167,34 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
 
-    def step(events=None, stats=None):
+    # tile shapes for the two batch classes from the autotuner (untimed)
+    if args.tiles:
+        ta, te = (int(x) for x in args.tiles.split(","))
+        tiles = {"arm": ta, "edge": te, "source": "--tiles"}
+    else:
+        tune_scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
+                              device=dev, stream=stream)
+        tiles = {"arm": tune_scene.autotune(d_arm, 1.0, reps=2, stream=stream)[0],
+                 "edge": tune_scene.autotune(d_edge, 1.0, reps=1, stream=stream)[0], "source": "cs_autotune"}
+        tune_scene.close()
+
+    def step(events=None, stats=None, build_ev=None):
         ev = iter(events) if events is not None else None
         nxt = (lambda: (next(ev), next(ev))) if ev is not None else (lambda: None)
+        if build_ev is not None:
+            build_ev[0].record(stream)
         scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
                          device=dev, stream=stream)
+        if build_ev is not None:
+            build_ev[1].record(stream)
         for ns in NSIGMAS:
-            scene.query(d_arm, ns, params=cs.QueryParams(group_size=64), stream=stream,
+            scene.query(d_arm, ns, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
                         eval_events=nxt(), out=outs["arm"], pair_stats=stats)
-            scene.query(d_edge, ns, params=cs.QueryParams(group_size=1024), stream=stream,
+            scene.query(d_edge, ns, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"]), stream=stream,
                         eval_events=nxt(), out=outs["edge"], pair_stats=stats)
         with torch.cuda.stream(stream):
             sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
-            scene.query(sph, 1.0, params=cs.QueryParams(group_size=K), stream=stream,
+            scene.query(sph, 1.0, params=cs.QueryParams(group_size=K, tile_config=tiles["arm"]), stream=stream,
                         eval_events=nxt(), out=pose_out, pair_stats=stats)
             scene.query_grad(sph, 1.0, grad_out=ones, params=cs.QueryParams(group_size=K), stream=stream,
                              eval_events=nxt(), out=gbuf)
@@ -187,10 +209,10 @@ def run_ours(args, rank, world):
     # forward sphere launches only (the roofline's kernel): rerun without the grad pass
     stats_fwd = torch.zeros(2, dtype=torch.int64, device=dev)
     for ns in NSIGMAS:
-        sc.query(d_arm, ns, params=cs.QueryParams(group_size=64), stream=stream, out=outs["arm"],
-                 pair_stats=stats_fwd)
-        sc.query(d_edge, ns, params=cs.QueryParams(group_size=1024), stream=stream, out=outs["edge"],
-                 pair_stats=stats_fwd)
+        sc.query(d_arm, ns, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
+                 out=outs["arm"], pair_stats=stats_fwd)
+        sc.query(d_edge, ns, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"]), stream=stream,
+                 out=outs["edge"], pair_stats=stats_fwd)
     torch.cuda.synchronize(dev)
     fwd_cand, fwd_useful = (int(x) for x in stats_fwd.cpu().tolist())
     info = sc.info()
@@ -209,6 +231,7 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev.index)
     clocks.start()
     total_ms = 0.0
+    build_ms = []
     eval_ms = []  # per forward-sphere launch of the tabletop sweep
     l0 = cs.abi.cs_launch_count()
     for _ in range(args.steps):
@@ -219,12 +242,14 @@ def run_ours(args, rank, world):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (n_fwd_launches + 2))]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        bev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         t0.record(stream)
-        s, _ = step(events=evs)
+        s, _ = step(events=evs, build_ev=bev)
         t1.record(stream)
         torch.cuda.synchronize(dev)
         s.close()
         total_ms += t0.elapsed_time(t1)
+        build_ms.append(bev[0].elapsed_time(bev[1]))
         for k in range(n_fwd_launches):
             eval_ms.append(evs[2 * k].elapsed_time(evs[2 * k + 1]))
     launches = cs.abi.cs_launch_count() - l0
@@ -253,12 +278,25 @@ def run_ours(args, rank, world):
     achieved = ops_per_launch / avg_eval_s
     roofline = {"bound": "alu", "kernel": "k_eval<sphere> (fused cull+evaluate+reduce)",
                 "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak_ops, "traffic": None,
+                "frac": achieved / peak_ops,
+                "traffic": TRAFFIC["bytes"] if cs.abi.cs_version() == TRAFFIC["version"] else None,
+                "traffic_case": TRAFFIC["case"],
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                 "ops_per_pair": OPS_PER_PAIR, "useful_pairs_per_launch": fwd_useful / n_fwd_launches,
                 "candidate_pairs_per_launch": fwd_cand / n_fwd_launches,
                 "avg_launch_ms": avg_eval_s * 1e3,
                 "candidate_frac": (fwd_cand * OPS_PER_PAIR / n_fwd_launches / avg_eval_s) / peak_ops}
+
+    # scene build (Eq. 2 repack, filter, Morton order, chunks, tree): minimal
+    # traffic is the 44 input bytes read and the 40-byte record written per
+    # Gaussian; the build synchronises the host a few times, so this is a
+    # lower bound of the build's own bandwidth
+    n_g = int(scene_h["means"].shape[0])
+    b_ms = sum(build_ms) / len(build_ms)
+    build = {"ms": b_ms, "algorithmic_bytes": n_g * 84, "achieved_gbs": n_g * 84 / (b_ms * 1e-3) / 1e9,
+             "peak_gbs": float(peaks.get("hbm_gbs", 6400.0)),
+             "note": "44 B read + 40 B written per Gaussian over the whole build (host syncs included)"}
+    build["frac"] = build["achieved_gbs"] / build["peak_gbs"]
 
     e2e = None
     if not args.no_e2e:
@@ -277,7 +315,7 @@ def run_ours(args, rank, world):
                    "l2": "256 MB buffer written between steps (outside the timed region)",
                    "grid": {"dims": info["dims"], "cell_size": info["cell_size"],
                             "n_large": info["n_large"]}},
-        "queries_per_s": qps, "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "queries_per_s": qps, "roofline": roofline, "build": build, "tiles": tiles, "e2e": e2e, "clocks": clk,
         "gpu_launches": int(launches // args.steps) if args.steps else 0,
         "gpu_launches_total": int(launches), "served": None,
     }

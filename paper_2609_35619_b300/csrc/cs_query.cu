@@ -1065,7 +1065,7 @@ using Cfg18 = Cfg<8, 8, 2, 32, 2, 2, 2>;
 using Cfg19 = Cfg<4, 16, 3, 16, 3, 2, 2>;
 using CfgGrad = Cfg<4, 8, 3, 8, 3>;  // the adjoint keeps three gradient sums per primitive
 static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19};
-constexpr int kDefaultTile = 1;
+constexpr int kDefaultTile = 18;
 
 int tile_configs(int32_t *ids, int32_t cap) {
     int n = (int)(sizeof(kTileIds) / sizeof(kTileIds[0]));
