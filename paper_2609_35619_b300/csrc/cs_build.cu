@@ -190,23 +190,32 @@ __global__ void k_chunk_greedy(const float4 *__restrict__ spos, int n_main, int 
     uint32_t c = 0;
     int k = 0;
     float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
-    for (int p = p0; p < p1; ++p) {
-        const float4 P = spos[p];
-        if (k > 0) {
-            const float nlx = fminf(lx, P.x), nly = fminf(ly, P.y), nlz = fminf(lz, P.z);
-            const float nhx = fmaxf(hx, P.x), nhy = fmaxf(hy, P.y), nhz = fmaxf(hz, P.z);
-            if (k == kChunk || fmaxf(fmaxf(nhx - nlx, nhy - nly), nhz - nlz) > L) {
-                ++c;
-                k = 0;
-            } else {
-                lx = nlx; ly = nly; lz = nlz; hx = nhx; hy = nhy; hz = nhz;
+    for (int p8 = p0; p8 < p1; p8 += 8) {
+        float4 P8[8];  // the next eight means in flight at once
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (p8 + u < p1) P8[u] = spos[p8 + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int p = p8 + u;
+            if (p >= p1) break;
+            const float4 P = P8[u];
+            if (k > 0) {
+                const float nlx = fminf(lx, P.x), nly = fminf(ly, P.y), nlz = fminf(lz, P.z);
+                const float nhx = fmaxf(hx, P.x), nhy = fmaxf(hy, P.y), nhz = fmaxf(hz, P.z);
+                if (k == kChunk || fmaxf(fmaxf(nhx - nlx, nhy - nly), nhz - nlz) > L) {
+                    ++c;
+                    k = 0;
+                } else {
+                    lx = nlx; ly = nly; lz = nlz; hx = nhx; hy = nhy; hz = nhz;
+                }
             }
+            if (k == 0) {
+                lx = hx = P.x; ly = hy = P.y; lz = hz = P.z;
+            }
+            if (base) slot[p] = (c0 + c) * kChunk + (uint32_t)k;
+            ++k;
         }
-        if (k == 0) {
-            lx = hx = P.x; ly = hy = P.y; lz = hz = P.z;
-        }
-        if (base) slot[p] = (c0 + c) * kChunk + (uint32_t)k;
-        ++k;
     }
     if (!base) counts[sg] = p1 > p0 ? c + 1 : 0u;
 }

@@ -189,6 +189,38 @@ __device__ __forceinline__ float ordered_to_float(int i) {
     return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF);
 }
 
+// Group outputs (Section II-D/E): sum of the metric and OR of the flag over
+// the rows [b, e) of one group.  Groups of 32 rows or more are reduced by a
+// warp: lane l sums rows b + l, b + l + 32, ... in order, then a fixed xor
+// tree; shorter groups by one thread in row order.  The order depends only on
+// the group size, so a group's bits do not depend on the launch it is in.
+constexpr int kGroupWarpMin = 32;
+__device__ __forceinline__ void group_rows_warp(const float *__restrict__ metric,
+                                                const uint8_t *__restrict__ collide, int b, int e,
+                                                int lane, float &s, unsigned &c) {
+    s = 0.f;
+    c = 0u;
+    for (int j = b + lane; j < e; j += 32) {
+        if (metric) s += metric[j];
+        if (collide) c |= collide[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c |= __shfl_xor_sync(0xffffffffu, c, o);
+    }
+}
+__device__ __forceinline__ void group_rows_serial(const float *__restrict__ metric,
+                                                  const uint8_t *__restrict__ collide, int b, int e,
+                                                  float &s, unsigned &c) {
+    s = 0.f;
+    c = 0u;
+    for (int j = b; j < e; ++j) {
+        if (metric) s += metric[j];
+        if (collide) c |= collide[j];
+    }
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

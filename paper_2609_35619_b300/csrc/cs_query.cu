@@ -3,16 +3,19 @@
 // adjoint), and the group epilogue.
 //
 // Fused kernel layout (one CTA per tile of TQ consecutive sorted primitives):
-//   warps 0..NCW-1  consumers: each lane holds QB primitives in registers and
-//                   streams the staged Gaussians from shared memory, updating
-//                   its per-primitive reductions (no cross-lane traffic);
 //   warp NCW        producer: computes the tile's bounding box and reach,
-//                   walks the grid rows it can reach (the cull) and the
-//                   large-tier chunks, and stages the reachable Gaussian
-//                   spans into a ring of NS shared-memory stages with 1-D bulk
-//                   copies completing on per-stage mbarriers.
-// Before evaluating a staged chunk of 32 Gaussians each consumer warp tests
-// the chunk's bounding record against its own primitives (warp-level cull).
+//                   descends the chunk tree to the chunks within reach (the
+//                   cull), stages each run of them into a ring of NS
+//                   shared-memory stages with one 1-D bulk copy completing on
+//                   the stage's mbarrier, and while the copy flies tests every
+//                   staged chunk against every primitive of the tile (lane =
+//                   primitive, one ballot per 32), leaving a hit mask per slot;
+//   warps 0..NCW-1  consumers: each owns QW primitives; per stage it takes the
+//                   slots its bits of the hit masks mark, lane l evaluating
+//                   slot l of a chunk (two chunks at once in packed FP32x2 for
+//                   sphere cost reductions) against the primitives that reach
+//                   it, with per-lane reductions reduced across lanes at the
+//                   end by fixed shuffle trees.
 #include <math.h>
 
 #include <algorithm>
@@ -569,7 +572,7 @@ template <int QW, int GROUP>
 __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, const SlotMeta mt0,
                                                 const ChunkBlock &B1, const SlotMeta mt1, unsigned qmask,
                                                 float4 (*wqd)[3], const QueryConsts &k, int lane,
-                                                unsigned long long &cand, unsigned long long &c_hits) {
+                                                unsigned &cand, unsigned &c_hits) {
     if (qmask == 0u) return;
     LaneG g0, g1;
     lane_gaussian(B0, mt0, lane, g0);
@@ -579,13 +582,16 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
     g2.sxx = pk2(g0.sxx, g1.sxx); g2.syy = pk2(g0.syy, g1.syy); g2.szz = pk2(g0.szz, g1.szz);
     g2.sxy2 = pk2(g0.sxy2, g1.sxy2); g2.sxz2 = pk2(g0.sxz2, g1.sxz2); g2.syz2 = pk2(g0.syz2, g1.syz2);
     const f32x2 nG2 = pk2(-k.G, -k.G), Gs2 = pk2(k.Gsmin, k.Gsmin);
-    constexpr unsigned GMASK = (1u << GROUP) - 1u;
-    unsigned gm = 0u;  // bit j0: group j0 .. j0 + GROUP - 1 has a member reaching a chunk
+    // bit j0 of gm: group j0 .. j0 + GROUP - 1 has a member reaching a chunk
+    unsigned gm = qmask;
 #pragma unroll
-    for (int j0 = 0; j0 < QW; j0 += GROUP) gm |= ((qmask >> j0) & GMASK) ? (1u << j0) : 0u;
+    for (int sh = 1; sh < GROUP; sh <<= 1) gm |= gm >> sh;
+    constexpr unsigned LEAD = GROUP == 1 ? 0xFFFFFFFFu : GROUP == 2 ? 0x55555555u : GROUP == 4 ? 0x11111111u
+                                                                               : 0x01010101u;
+    gm &= LEAD;
     const unsigned ng = (unsigned)__popc(gm) * (unsigned)GROUP;
     c_hits += ng;
-    cand += (unsigned long long)(ng * (unsigned)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo)));
+    cand += ng * (unsigned)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo));
 #pragma unroll
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
         if ((gm >> j0) & 1u) {
@@ -601,9 +607,9 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 template <int PRIM, int QW, int MODE, bool GRAD>
 __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const ChunkBlock &B, const SlotMeta &mt,
                                            unsigned qmask, float4 (*wq)[kQRec], const QueryConsts &k, int lane,
-                                           int &group, unsigned long long &cand, unsigned long long &c_hits) {
+                                           int &group, unsigned &cand, unsigned &c_hits) {
     if (qmask == 0u) return;
-    c_hits += (unsigned long long)__popc(qmask);
+    c_hits += (unsigned)__popc(qmask);
     if (MODE == 0 && !GRAD && PRIM == 1) {
         // fixed grouping of the cost partials (16 chunks) keeps the
         // summation order independent of the tile
@@ -616,7 +622,7 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
     }
     LaneG g;
     lane_gaussian(B, mt, lane, g);
-    cand += (unsigned long long)__popc(qmask) * (unsigned long long)(mt.hi - mt.lo);
+    cand += (unsigned)__popc(qmask) * (unsigned)(mt.hi - mt.lo);
     {
 #pragma unroll
         for (int j = 0; j < QW; j += 2) {
@@ -718,8 +724,8 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if (MODE == 2) { A.sm_m[j] = k.S_cut; A.sm_acc[j] = 0.f; }
         if (GRAD) { A.gx[j] = 0.f; A.gy[j] = 0.f; A.gz[j] = 0.f; }
     }
-    unsigned long long cand = 0;  // (primitive, Gaussian) pairs evaluated
-    unsigned long long c_stages = 0, c_tested = 0, c_pass = 0, c_hits = 0, c_polls = 0;
+    unsigned cand = 0, c_hits = 0;  // (primitive, Gaussian) pairs and (primitive, chunk) hits evaluated
+    unsigned long long c_stages = 0, c_tested = 0, c_pass = 0, c_polls = 0;
     unsigned long long c_wait = 0, c_first = 0;
     const long long c_start = clock64();
     int group = -1;               // chunk group of the cost partials
@@ -750,47 +756,58 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 const float R = reach(wal, wbe, blo.w, sc.pad_abs);
                 wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
             }
-            unsigned cmask = __ballot_sync(0xffffffffu, wpass);
-            c_pass += (unsigned long long)__popc(cmask);
-            constexpr int CPR = 32 / QW;  // chunks whose primitive tests share one round
+            unsigned pmask = __ballot_sync(0xffffffffu, wpass);
+            c_pass += (unsigned long long)__popc(pmask);
+            // then (primitive, chunk) tests, 32 / QW chunks per round (lane l:
+            // primitive l % QW, chunk l / QW of the round); myq of lane t
+            // collects slot t's mask of the primitives that reach it
+            constexpr int CPR = 32 / QW;
             constexpr unsigned QMASK = (1u << QW) - 1u;
-            while (cmask) {
-                const int s0 = __ffs(cmask) - 1;
-                cmask &= cmask - 1;
-                int s1 = -1, s2 = -1, s3 = -1;
-                if (CPR > 1 && cmask) { s1 = __ffs(cmask) - 1; cmask &= cmask - 1; }
-                if (CPR > 2 && cmask) { s2 = __ffs(cmask) - 1; cmask &= cmask - 1; }
-                if (CPR > 3 && cmask) { s3 = __ffs(cmask) - 1; cmask &= cmask - 1; }
-                // lane l tests primitive l % QW against the chunk of round slot l / QW
+            unsigned myq = 0u;
+            while (pmask) {
+                int sl[CPR];
+#pragma unroll
+                for (int r = 0; r < CPR; ++r) {
+                    sl[r] = pmask ? __ffs(pmask) - 1 : -1;
+                    pmask &= pmask - 1;
+                }
                 const int part = lane / QW;
-                const int my = part == 0 ? s0 : part == 1 ? s1 : part == 2 ? s2 : s3;
+                int my = sl[0];
+#pragma unroll
+                for (int r = 1; r < CPR; ++r) my = part == r ? sl[r] : my;
                 bool qp = false;
                 if (my >= 0) qp = reaches<PRIM>(wq[lane % QW], sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs);
                 const unsigned hits = __ballot_sync(0xffffffffu, qp);
-                if constexpr (PRIM == 0 && MODE == 0 && !GRAD) {
-                    // spheres, cost reductions: chunks of the round in pairs, two
-                    // Gaussians per lane in packed registers
-#pragma unroll 1
-                    for (int r = 0; r < CPR; r += 2) {
-                        const int sa = r == 0 ? s0 : s2, sb = r == 0 ? s1 : s3;
-                        if (sa < 0) break;
-                        const unsigned qa = (hits >> (r * QW)) & QMASK;
-                        const unsigned qb = sb >= 0 ? (hits >> ((r + 1) * QW)) & QMASK : 0u;
-                        eval_chunk_pair<QW, C::GROUP>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
-                                                      sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd,
-                                                      k, lane, cand,
-                                                      c_hits);
+#pragma unroll
+                for (int r = 0; r < CPR; ++r)
+                    if (lane == sl[r]) myq = (hits >> (r * QW)) & QMASK;
+            }
+            unsigned cmask = __ballot_sync(0xffffffffu, myq != 0u);
+            if constexpr (PRIM == 0 && MODE == 0 && !GRAD) {
+                // spheres, cost reductions: chunks with hits in pairs, two
+                // Gaussians per lane in packed registers
+                while (cmask) {
+                    const int sa = __ffs(cmask) - 1;
+                    cmask &= cmask - 1;
+                    int sb = -1;
+                    if (cmask) {
+                        sb = __ffs(cmask) - 1;
+                        cmask &= cmask - 1;
                     }
-                } else {
-                    // one inlined copy of the chunk body for the CPR chunks of the round
+                    const unsigned qa = __shfl_sync(0xffffffffu, myq, sa);
+                    const unsigned qb = sb >= 0 ? __shfl_sync(0xffffffffu, myq, sb) : 0u;
+                    eval_chunk_pair<QW, C::GROUP>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
+                                                  sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd, k,
+                                                  lane, cand, c_hits);
+                }
+            } else {
 #pragma unroll 1
-                    for (int r = 0; r < CPR; ++r) {
-                        const int sl = r == 0 ? s0 : r == 1 ? s1 : r == 2 ? s2 : s3;
-                        if (sl < 0) break;
-                        eval_chunk<PRIM, QW, MODE, GRAD>(A, sm->blk[s][sl], sm->meta[s][sl],
-                                                         (hits >> (r * QW)) & QMASK, wq, k, lane, group, cand,
-                                                         c_hits);
-                    }
+                while (cmask) {
+                    const int sl = __ffs(cmask) - 1;
+                    cmask &= cmask - 1;
+                    const unsigned q = __shfl_sync(0xffffffffu, myq, sl);
+                    eval_chunk<PRIM, QW, MODE, GRAD>(A, sm->blk[s][sl], sm->meta[s][sl], q, wq, k, lane, group, cand,
+                                                     c_hits);
                 }
             }
         }
@@ -865,14 +882,14 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if (vq) nb_total += (unsigned long long)cntj;
     }
     if (a.stats && lane == 0) {
-        atomicAdd(a.stats + 0, cand);
+        atomicAdd(a.stats + 0, (unsigned long long)cand);
         atomicAdd(a.stats + 1, nb_total);
     }
     if (a.kstats && lane == 0) {
         atomicAdd(a.kstats + 0, c_stages);
         atomicAdd(a.kstats + 1, c_tested);
         atomicAdd(a.kstats + 2, c_pass);
-        atomicAdd(a.kstats + 3, c_hits);
+        atomicAdd(a.kstats + 3, (unsigned long long)c_hits);
         atomicAdd(a.kstats + 6, c_polls);
         const long long c_end = clock64();
         atomicAdd(a.kstats + 8, (unsigned long long)(c_end - c_start));
@@ -991,21 +1008,29 @@ __global__ void k_prep_recs(const float *__restrict__ prims, int prim_type, int 
     if (!ok) atomicOr(err, kErrInvalidQuery);
 }
 
-// Section II-D/E group outputs: metric summed, flag OR-ed over runs of G rows.
+// Section II-D/E group outputs: metric summed, flag OR-ed over runs of G rows
+// (a warp per group from kGroupWarpMin rows, else a thread per group).
 __global__ void k_group(const float *__restrict__ metric, const uint8_t *__restrict__ collide,
                         int Q, int G, float *__restrict__ gm, uint8_t *__restrict__ gc) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    int ng = (Q + G - 1) / G;
-    if (g >= ng) return;
-    int b = g * G, e = min(Q, b + G);
-    float s = 0.f;
-    uint8_t c = 0;
-    for (int j = b; j < e; ++j) {
-        if (metric) s += metric[j];
-        if (collide) c |= collide[j];
+    const int ng = (Q + G - 1) / G;
+    float sum;
+    unsigned c;
+    if (G >= kGroupWarpMin) {
+        const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+        if (g >= ng) return;  // whole warps leave together
+        const int b = g * G, e = min(Q, b + G);
+        group_rows_warp(metric, collide, b, e, threadIdx.x & 31, sum, c);
+        if ((threadIdx.x & 31) != 0) return;
+        if (gm) gm[g] = sum;
+        if (gc) gc[g] = (uint8_t)c;
+    } else {
+        const int g = blockIdx.x * blockDim.x + threadIdx.x;
+        if (g >= ng) return;
+        const int b = g * G, e = min(Q, b + G);
+        group_rows_serial(metric, collide, b, e, sum, c);
+        if (gm) gm[g] = sum;
+        if (gc) gc[g] = (uint8_t)c;
     }
-    if (gm) gm[g] = s;
-    if (gc) gc[g] = c;
 }
 
 // ---------------------------------------------------------- host launchers
@@ -1196,8 +1221,9 @@ void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, f
 
 void launch_group(const float *metric, const uint8_t *collide, int Q, int G, float *gm, uint8_t *gc,
                   cudaStream_t s) {
-    int ng = (Q + G - 1) / G;
-    k_group<<<(ng + 255) / 256, 256, 0, s>>>(metric, collide, Q, G, gm, gc);
+    const int64_t ng = (Q + G - 1) / G;
+    const int64_t threads = G >= kGroupWarpMin ? ng * 32 : ng;
+    k_group<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(metric, collide, Q, G, gm, gc);
     count_launches(1);
 }
 

@@ -37,8 +37,8 @@ namespace cs {
 
 // Group outputs of the requests of one batch: segment s covers batch rows
 // [row, row + rows) reduced in runs of G into group outputs [out, out +
-// ceil(rows / G)).  Sum of the metric and OR of the flag over each run, in
-// row order (the order of k_group, so the bits equal a cs_query call).
+// ceil(rows / G)).  One warp per group output; each group is reduced in the
+// order k_group uses for its size, so the bits equal a cs_query call.
 struct GroupSeg {
     int32_t row, rows, G, out;
 };
@@ -46,8 +46,9 @@ struct GroupSeg {
 __global__ void k_group_segments(const float *__restrict__ metric, const uint8_t *__restrict__ collide,
                                  const GroupSeg *__restrict__ segs, int nseg, int ngroups,
                                  float *__restrict__ gm, uint8_t *__restrict__ gc) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= ngroups) return;  // whole warps leave together
     int lo = 0, hi = nseg - 1;  // last segment with out <= g
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -56,14 +57,18 @@ __global__ void k_group_segments(const float *__restrict__ metric, const uint8_t
     }
     const GroupSeg sg = segs[lo];
     const int b = sg.row + (g - sg.out) * sg.G, e = min(sg.row + sg.rows, b + sg.G);
-    float s = 0.f;
-    uint8_t c = 0;
-    for (int j = b; j < e; ++j) {
-        s += metric[j];
-        c |= collide[j];
+    float s;
+    unsigned c;
+    if (sg.G >= kGroupWarpMin) {
+        group_rows_warp(metric, collide, b, e, lane, s, c);
+    } else {
+        if (lane != 0) return;
+        group_rows_serial(metric, collide, b, e, s, c);
     }
-    gm[g] = s;
-    gc[g] = c;
+    if (lane == 0) {
+        gm[g] = s;
+        gc[g] = (uint8_t)c;
+    }
 }
 
 constexpr uint32_t kServerMagic = 0xC5B300A5u;
@@ -281,8 +286,8 @@ static void launch_batch(Server *srv, Slot &s, std::unique_lock<std::mutex> &lk)
         cst = query_common(reinterpret_cast<cs_scene *>(srv->scenes[scene]), prim, s.d_prims, rows, 0.f, &p,
                            false, s.d_metric, s.d_collide, nullptr, nullptr, s.ws);
     if (ok() && nseg > 0) {
-        k_group_segments<<<(int)((g0 + 255) / 256), 256, 0, st>>>(s.d_metric, s.d_collide, s.d_segs, nseg, (int)g0,
-                                                                  s.d_gm, s.d_gc);
+        k_group_segments<<<(unsigned)((g0 * 32 + 255) / 256), 256, 0, st>>>(s.d_metric, s.d_collide, s.d_segs,
+                                                                           nseg, (int)g0, s.d_gm, s.d_gc);
         count_launches(1);
         e = cudaGetLastError();
     }
