@@ -39,7 +39,7 @@ OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes
 # DRAM bytes (read + write) of one forward launch of the fused kernel, from the
 # ncu capture of that case summarised under profiles/, valid for the library
 # version it was taken with (reported as null otherwise)
-TRAFFIC = {"version": "cs_b300 0.2 (sm_103a)", "bytes": 46.037e6 + 0.230e6,
+TRAFFIC = {"version": "cs_b300 0.3 (sm_103a)", "bytes": 45.752e6 + 0.117e6,
            "case": "262,144 arm spheres, tile 18, n_sigma 1"}
 WORKLOAD = "tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres fwd+adjoint"
 
@@ -557,11 +557,12 @@ def oracle_sample(target_s: float, seed: int = 0):
     import oracle
     scene, arm, edge, poses, offs, radius = make_inputs()
     rng = np.random.default_rng(seed)
-    probe = np.concatenate([arm[rng.choice(arm.shape[0], 2)], edge[rng.choice(edge.shape[0], 2)]])
+    probe = np.concatenate([arm[rng.choice(arm.shape[0], 32)], edge[rng.choice(edge.shape[0], 32)]])
+    oracle.query(scene, probe[:2], 0, 1.0)  # thread pool start-up
     t0 = time.perf_counter()
     oracle.query(scene, probe, 0, 1.0)
     per_row = (time.perf_counter() - t0) / probe.shape[0]
-    rows = int(max(4, min(4096, target_s / max(per_row, 1e-6))))
+    rows = int(max(4, min(65536, target_s / max(per_row, 1e-7))))
     rows -= rows % 2
     sample = np.concatenate([arm[rng.choice(arm.shape[0], rows // 2, replace=False)],
                              edge[rng.choice(edge.shape[0], rows // 2, replace=False)]])

@@ -1069,6 +1069,7 @@ QueryConsts make_consts(const cs_params &p) {
 //   15: 8 x 8, 2 stages x 32 chunks, 2 CTAs/SM
 //   16: shape 1 with the tile's rows interleaved over the consumer warps
 //   17-19: shapes 1, 15, 13 with row pairs interleaved over the consumer warps
+//   20, 21: shape 18 evaluating sphere primitives one at a time / in groups of 4
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1088,8 +1089,10 @@ using Cfg16 = Cfg<8, 8, 4, 16, 2, 2, 1>;
 using Cfg17 = Cfg<8, 8, 4, 16, 2, 2, 2>;
 using Cfg18 = Cfg<8, 8, 2, 32, 2, 2, 2>;
 using Cfg19 = Cfg<4, 16, 3, 16, 3, 2, 2>;
+using Cfg20 = Cfg<8, 8, 2, 32, 2, 1, 2>;
+using Cfg21 = Cfg<8, 8, 2, 32, 2, 4, 2>;
 using CfgGrad = Cfg<4, 8, 3, 8, 3>;  // the adjoint keeps three gradient sums per primitive
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21};
 constexpr int kDefaultTile = 18;
 
 int tile_configs(int32_t *ids, int32_t cap) {
@@ -1150,6 +1153,8 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 17: return launch_mode<PRIM, Cfg17>(a, s);
         case 18: return launch_mode<PRIM, Cfg18>(a, s);
         case 19: return launch_mode<PRIM, Cfg19>(a, s);
+        case 20: return launch_mode<PRIM, Cfg20>(a, s);
+        case 21: return launch_mode<PRIM, Cfg21>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }
