@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="tile configuration for --case eval (0 = auto)")
     ap.add_argument("--batch", default="arm", choices=["arm", "edge"], help="query batch for --case eval")
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
+    ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
     return ap.parse_args()
 
 
@@ -618,6 +619,15 @@ def run_eval_case(args):
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
     kstats = torch.zeros(16, dtype=torch.int64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if args.grad:
+        up = torch.ones(arm.shape[0] // G + (arm.shape[0] % G > 0), device=dev)
+        scene.query_grad(arm, ns, grad_out=up, params=qp)
+        scene.query_grad(arm, ns, grad_out=up, params=qp, eval_events=ev)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        print(json.dumps({"case": "eval", "grad": True, "batch": args.batch, "tile": args.tile, "nsigma": ns,
+                          "queries": arm.shape[0], "eval_ms": ms}))
+        return
     scene.query(arm, ns, params=qp)
     scene.query(arm, ns, params=qp, pair_stats=stats, eval_events=ev)
     torch.cuda.synchronize()

@@ -120,7 +120,8 @@ typedef struct cs_params {
     int32_t tile_config;       /* 0 = the default shape; CS_TILE_TUNED = the shape cs_autotune
                                   chose for this scene, primitive type, mode and batch-size
                                   class (the default when none was tuned); otherwise a value
-                                  from cs_tile_configs */
+                                  from cs_tile_configs.  cs_query_grad has its own shapes:
+                                  1..4 select one, any other value the default */
     const float *nsigma_per_query; /* [Q] n_sigma per row (overrides the scalar), each >= 0 */
     void *stream;              /* cudaStream_t */
     int32_t *out_count;        /* [Q] |N_j| per row */

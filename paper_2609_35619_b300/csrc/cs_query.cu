@@ -1091,7 +1091,17 @@ using Cfg18 = Cfg<8, 8, 2, 32, 2, 2, 2>;
 using Cfg19 = Cfg<4, 16, 3, 16, 3, 2, 2>;
 using Cfg20 = Cfg<8, 8, 2, 32, 2, 1, 2>;
 using Cfg21 = Cfg<8, 8, 2, 32, 2, 4, 2>;
-using CfgGrad = Cfg<4, 8, 3, 8, 3>;  // the adjoint keeps three gradient sums per primitive
+// Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
+// three gradient sums per primitive, so its tiles hold fewer primitives
+//   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
+//   2: 4 x 8, 3 stages x 16 chunks, 3 CTAs/SM, row pairs interleaved
+//   3: 4 x 8, 2 stages x 24 chunks, 3 CTAs/SM, row pairs interleaved
+//   4: 8 x 8, 2 stages x 16 chunks, 2 CTAs/SM, row pairs interleaved
+using CfgGrad1 = Cfg<4, 8, 3, 8, 3>;
+using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
+using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
+using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
+constexpr int kDefaultGradTile = 2;
 static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21};
 constexpr int kDefaultTile = 18;
 
@@ -1126,13 +1136,22 @@ static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
     return launch_eval_t<PRIM, C, 2, false>(a, s);
 }
 
+template <int PRIM, class C>
+static cudaError_t launch_grad(const EvalArgs &a, int mode, cudaStream_t s) {
+    if (mode == 0) return launch_eval_t<PRIM, C, 0, true>(a, s);
+    if (mode == 1) return launch_eval_t<PRIM, C, 1, true>(a, s);
+    return launch_eval_t<PRIM, C, 2, true>(a, s);
+}
+
 template <int PRIM>
 static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStream_t s) {
     if (grad) {
         const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
-        if (mode == 0) return launch_eval_t<PRIM, CfgGrad, 0, true>(a, s);
-        if (mode == 1) return launch_eval_t<PRIM, CfgGrad, 1, true>(a, s);
-        return launch_eval_t<PRIM, CfgGrad, 2, true>(a, s);
+        const int gt = (tile >= 1 && tile <= 4) ? tile : kDefaultGradTile;
+        if (gt == 1) return launch_grad<PRIM, CfgGrad1>(a, mode, s);
+        if (gt == 3) return launch_grad<PRIM, CfgGrad3>(a, mode, s);
+        if (gt == 4) return launch_grad<PRIM, CfgGrad4>(a, mode, s);
+        return launch_grad<PRIM, CfgGrad2>(a, mode, s);
     }
     switch (tile) {
         case 2: return launch_mode<PRIM, Cfg2>(a, s);
@@ -1162,7 +1181,7 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
 cudaError_t launch_eval(int prim_type, const EvalArgs &a, bool grad, int tile_cfg, int num_sms,
                         cudaStream_t s) {
     (void)num_sms;
-    const int tile = tile_cfg ? tile_cfg : kDefaultTile;
+    const int tile = tile_cfg > 0 ? tile_cfg : grad ? 0 : kDefaultTile;
     return prim_type == CS_PRIM_SPHERE ? launch_prim<0>(a, grad, tile, s) : launch_prim<1>(a, grad, tile, s);
 }
 

@@ -76,6 +76,29 @@ def test_adjoint_matches_oracle(cs, mode, prim_type):
                wrel=_weight_rel(mode, orc["cond"]))
 
 
+@pytest.mark.parametrize("mode,prim_type", [(0, 0), (3, 1), (2, 0)])
+def test_adjoint_tile_shapes_give_the_same_bits(cs, mode, prim_type):
+    """Every adjoint tile shape sums each lane's Gaussians in chunk order, so
+    all shapes return the same bits; the default also matches the oracle."""
+    sc = S.tiny_scene(n=3000)
+    rng = np.random.default_rng(9)
+    Q = 1500
+    c = rng.uniform(0, 2, (Q, 3))
+    prims = (np.c_[c, rng.uniform(0.05, 0.25, Q)] if prim_type == 0
+             else S.ellipsoid_queries(9, c)).astype(np.float32)
+    scene = _scene(cs, sc)
+    up = torch.as_tensor(rng.normal(size=Q).astype(np.float32))
+    outs = [scene.query_grad(torch.as_tensor(prims), 1.0, grad_out=up, prim_type=prim_type,
+                             params=cs.QueryParams(mode=mode, tile_config=t)).cpu().numpy() for t in (1, 2, 3, 4)]
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    go, scale = oracle.grad(sc, prims, prim_type, 1.0, mode, grad_out=up.numpy().astype(np.float64),
+                            return_scale=True)
+    orc = oracle.query(sc, prims, prim_type, 1.0)
+    _check(outs[1], go, scale, (orc["band_cut"] > 0) | (orc["band_kink"] > 0), f"shapes mode={mode}",
+           wrel=_weight_rel(mode, orc["cond"]))
+
+
 def test_adjoint_group_upstream(cs):
     sc = S.tiny_scene()
     q = S.tiny_queries(q=640)
