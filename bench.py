@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="requests of the serving measurement in the default run")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests-sweep", type=int, default=10_000, help="requests per load in --case serve")
+    ap.add_argument("--serve-slots", type=int, default=3, help="server batch slots in --case serve")
+    ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
+    ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
     ap.add_argument("--case", default="step", choices=["step", "eval", "serve"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
@@ -512,12 +516,12 @@ def one_query_per_call(cs, torch, scene, n=2000):
     return n / (time.perf_counter() - t0)
 
 
-def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True):
+def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True, slots=3, slot_rows=1 << 19):
     import cs_synth as S
     scenes_h, scenes, tiles = serve_setup(torch, cs, dev)
     reqs = S.serving_requests(seed=1007, count=n_requests)
     warm = S.serving_requests(seed=1008, count=16, q_lo=16, q_hi=65536)
-    srv = cs.Server(scenes, slots=3, slot_rows=1 << 19, tile_config=cs.abi.CS_TILE_TUNED)
+    srv = cs.Server(scenes, slots=slots, slot_rows=slot_rows, tile_config=cs.abi.CS_TILE_TUNED)
     served_burst(cs, srv, warm)
     cap, cap_s = served_burst(cs, srv, reqs)
     runs = [served_poisson(cs, srv, reqs, f * cap) for f in loads]
@@ -526,7 +530,7 @@ def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True):
     out = {"workload": SERVE_WORKLOAD, "requests": n_requests,
            "rows": int(sum(r["spheres"].shape[0] for r in reqs)),
            "served_capacity_queries_per_s": cap, "loads": [dict(r, load=f) for f, r in zip(loads, runs)],
-           "server": {"slots": 3, "slot_rows": 1 << 19, "tiles": tiles,
+           "server": {"slots": slots, "slot_rows": slot_rows, "tiles": tiles,
                       "mean_batch_requests": st["requests"] / max(st["batches"], 1),
                       "max_batch_requests": st["max_batch_requests"]}}
     if with_per_call:
@@ -546,7 +550,8 @@ def run_serve_case(args):
     import paper_2609_35619_b300 as cs
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    res = run_served(torch, cs, dev, 10_000, loads=(0.25, 0.5, 0.75, 0.9))
+    res = run_served(torch, cs, dev, args.serve_requests_sweep, loads=(0.25, 0.5, 0.75, 0.9),
+                     with_per_call=not args.no_per_call, slots=args.serve_slots, slot_rows=args.serve_rows)
     print(json.dumps({"case": "serve", **res}))
 
 
