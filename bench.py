@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=3, help="server batch slots in --case serve")
     ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
     ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
-    ap.add_argument("--case", default="step", choices=["step", "eval", "serve"],
+    ap.add_argument("--case", default="step", choices=["step", "eval", "serve", "mppi"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
                          "(two fused-kernel launches); prints a short JSON summary. "
@@ -326,6 +326,7 @@ def run_ours(args, rank, world):
     }
     if not args.no_serve and world == 1:
         result["served"] = run_served(torch, cs, dev, args.serve_requests)
+        result["mppi"] = run_mppi(torch, cs, dev)
     return result
 
 
@@ -555,6 +556,70 @@ def run_serve_case(args):
     print(json.dumps({"case": "serve", **res}))
 
 
+# --------------------------------------------------------------- MPPI
+MPPI_WORKLOAD = "drone room 500k Gaussians; MPPI iteration with 1,024 rollouts x 32 steps x 1 sphere (r = 0.15 m)"
+
+
+def run_mppi(torch, cs, dev, iters=20, K=1024, T=32, with_oracle=False):
+    """One MPPI iteration (rollouts, metric, costs, Eq. 10 weights, update)
+    timed with CUDA events over `iters` back-to-back iterations, each
+    starting from the previous nominal sequence, inputs resident on the device."""
+    import cs_synth as S
+    sc = S.drone_scene()
+    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    rng = np.random.default_rng(1002)
+    x0 = torch.tensor([3.0, 2.5, 1.5], device=dev)
+    U = torch.as_tensor(np.tile([0.4, -0.2, 0.05], (T, 1)).astype(np.float32), device=dev)
+    eps = torch.as_tensor(rng.normal(0, 0.6, (iters + 3, K, T, 3)).astype(np.float32), device=dev)
+    out = {"U": torch.empty((T, 3), device=dev), "cost": torch.empty(K, device=dev),
+           "weights": torch.empty(K, device=dev), "collide": torch.empty(K, dtype=torch.uint8, device=dev)}
+    kw = dict(dt=0.1, radius=0.15, nsigma=1.0, lam=1.0, goal=(4.5, 1.0, 1.25))
+    eps_buf = torch.empty_like(eps[0])
+
+    def timed(one_iteration):
+        for i in range(3):
+            eps_buf.copy_(eps[i])
+            one_iteration()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = cs.abi.cs_launch_count()
+        e0.record()
+        for i in range(iters):
+            eps_buf.copy_(eps[3 + i])
+            one_iteration()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / iters, (cs.abi.cs_launch_count() - l0) / iters
+
+    U0 = U.clone()
+
+    def eager():
+        cs.mppi_step(scene, x0, U, eps_buf, out=out, **kw)
+        U.copy_(out["U"])
+
+    ms, kernels = timed(eager)
+    U.copy_(U0)
+    graph = cs.MppiGraph(scene, x0, U, eps_buf, in_place=True, **kw)
+    ms_graph, _ = timed(graph.launch)
+    res = {"workload": MPPI_WORKLOAD, "K": K, "T": T, "ms_per_iteration": ms, "iterations_per_s": 1e3 / ms,
+           "queries_per_s": K * T * 1e3 / ms, "kernels_per_iteration": kernels,
+           "graph_ms_per_iteration": ms_graph, "graph_iterations_per_s": 1e3 / ms_graph,
+           "mean_cost": float(graph.out["cost"].mean()), "collide_frac": float(graph.out["collide"].float().mean()),
+           "note": "each iteration also copies its perturbations into the buffer the call reads"}
+    graph.close()
+    scene.close()
+    return res
+
+
+def run_mppi_case(args):
+    import torch
+
+    import paper_2609_35619_b300 as cs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"case": "mppi", **run_mppi(torch, cs, dev, iters=max(args.steps, 1) * 10)}))
+
+
 # ------------------------------------------------------------- oracle
 def oracle_sample(target_s: float, seed: int = 0):
     """Time the FP64 oracle on a bounded sample of the workload: rows drawn
@@ -658,6 +723,9 @@ def main():
         return
     if args.case == "serve":
         run_serve_case(args)
+        return
+    if args.case == "mppi":
+        run_mppi_case(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

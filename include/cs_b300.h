@@ -312,6 +312,54 @@ CS_API cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *pr
                              int32_t *best, float *ms, int32_t cap);
 
 /* ------------------------------------------------------------------------
+ * One MPPI iteration (Section II-D) for a robot that is one sphere under
+ * single-integrator (velocity) control, fused on the device: rollouts of K
+ * sampled control sequences over T steps, the conservative metric of every
+ * rollout position (Eq. 8, Eq. 11 averaged over the neighbour set, summed
+ * over the horizon), the per-rollout cost (the sum of collision, task and
+ * control terms; the paper's image term is not modelled), the Eq. 10 softmin
+ * weights with temperature lambda, and the update of the nominal sequence:
+ *   u[k,t] = U[t] + eps[k,t],  x[k,t+1] = x[k,t] + dt u[k,t],  x[k,0] = x0,
+ *   C^k = w_collision sum_t mc(x[k,t+1]) + w_goal sum_t |x[k,t+1] - goal|^2
+ *         + w_terminal |x[k,T] - goal|^2 + w_control sum_t |u[k,t]|^2,
+ *   w^k = exp(-C^k / lambda) / sum_l exp(-C^l / lambda),
+ *   U_out[t] = U[t] + sum_k w^k eps[k,t].
+ * The perturbations eps are drawn by the caller. */
+typedef struct cs_mppi_desc {
+    int32_t K;            /* rollouts, 1 .. 2^20 */
+    int32_t T;            /* horizon steps, 1 .. 1024 (K * T <= 2^26) */
+    float dt;             /* step, > 0 */
+    float radius;         /* robot sphere radius, > 0 */
+    float nsigma;         /* conservatism n_sigma, >= 0 */
+    float lambda;         /* Eq. 10 temperature, > 0 */
+    float w_collision, w_goal, w_terminal, w_control;  /* cost weights, >= 0 */
+    float goal[3];
+} cs_mppi_desc;
+
+/* Device pointers: x0 [3], U [T,3], eps [K,T,3] (row-major), U_out [T,3] (may
+ * equal U), and optionally cost [K], weights [K] and collide [K] (a rollout
+ * collides if any of its positions does, as cs_query's flag).  params gives
+ * the metric parameters, the stream and the tile shape (NULL = defaults);
+ * its mode, group and output members are ignored (the collision term is the
+ * mean cost) and host_io must be 0.  Asynchronous on the stream; scratch is
+ * the stream's pooled query scratch (grown once).  Non-finite inputs give
+ * NaN costs.  Errors: CS_ERR_INVALID_ARG for bad sizes, weights or NULL
+ * buffers, and those of cs_query. */
+CS_API cs_status cs_mppi_step(const cs_scene *scene, const cs_mppi_desc *desc, const float *x0, const float *U,
+                              const float *eps, float *U_out, float *cost, float *weights, uint8_t *collide,
+                              const cs_params *params);
+
+/* The same iteration captured into a query graph (see cs_graph_create):
+ * every cs_graph_launch runs it again on the buffers given here, reading the
+ * x0, U and eps they hold at that time (an MPPI loop writes the next
+ * perturbations into eps and copies U_out to U, or passes U_out == U).
+ * Launch, sync and free it with cs_graph_launch / cs_graph_sync /
+ * cs_graph_destroy.  Errors: those of cs_mppi_step and cs_graph_create. */
+CS_API cs_status cs_mppi_graph_create(const cs_scene *scene, const cs_mppi_desc *desc, const float *x0,
+                                      const float *U, const float *eps, float *U_out, float *cost, float *weights,
+                                      uint8_t *collide, const cs_params *params, cs_graph **out);
+
+/* ------------------------------------------------------------------------
  * Serving loop.  The paper has no counterpart: this is the runtime that keeps
  * scenes resident and answers collision-query requests of uneven size (one
  * RRT edge to a whole MPPI batch) for many clients.

@@ -13,6 +13,8 @@ the metric runs in the library's CUDA kernels):
   Scene.autotune(prims, nsigma, ...)           cs_autotune (tile shape per batch class)
   QueryGraph(scene, prims, ...)                cs_graph_create / launch / destroy
   Server(scenes, ...)                          cs_server_* (continuous batching)
+  mppi_step(scene, x0, U, eps, ...)            cs_mppi_step (one fused MPPI iteration)
+  MppiGraph(scene, x0, U, eps, ...)            cs_mppi_graph_create (the iteration as a CUDA graph)
 The raw one-to-one binding is `paper_2609_35619_b300.abi`.
 """
 from __future__ import annotations
@@ -24,7 +26,7 @@ from . import abi
 from .abi import (CS_METRIC_MEAN_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_SUM_COST,
                   CS_PRIM_ELLIPSOID, CS_PRIM_SPHERE, CsError, check)
 
-__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
+__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "mppi_step", "MppiGraph", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
            "CS_PRIM_SPHERE", "CS_PRIM_ELLIPSOID", "CS_METRIC_MEAN_COST", "CS_METRIC_SUM_COST",
            "CS_METRIC_MIN_S2", "CS_METRIC_SOFTMIN_S2", "CsError"]
 
@@ -325,6 +327,86 @@ class Server:
             check(abi.cs_server_destroy(self._h))
             self._h = ctypes.c_void_p()
             self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _mppi_desc(K, T, dt, radius, nsigma, lam, w_collision, w_goal, w_terminal, w_control, goal):
+    d = abi.cs_mppi_desc()
+    d.K, d.T, d.dt, d.radius, d.nsigma, d.lambda_ = K, T, dt, radius, nsigma, lam
+    d.w_collision, d.w_goal, d.w_terminal, d.w_control = w_collision, w_goal, w_terminal, w_control
+    for a in range(3):
+        d.goal[a] = goal[a]
+    return d
+
+
+def mppi_step(scene: Scene, x0, U, eps, *, dt=0.1, radius=0.15, nsigma=1.0, lam=1.0, w_collision=10.0,
+              w_goal=0.1, w_terminal=1.0, w_control=0.01, goal=(0.0, 0.0, 0.0),
+              params: QueryParams | None = None, stream=None, out=None) -> dict:
+    """cs_mppi_step on device tensors: x0 [3], U [T,3], eps [K,T,3].
+    Returns the updated nominal sequence, per-rollout cost, Eq. 10 weights
+    and collision flags (device tensors)."""
+    torch = _torch()
+    dev = scene.device
+    x0 = _as_f32(x0, dev).reshape(3)
+    U = _as_f32(U, dev).reshape(-1, 3)
+    T = U.shape[0]
+    eps = _as_f32(eps, dev).reshape(-1, T, 3)
+    K = eps.shape[0]
+    if out is None:
+        out = {"U": torch.empty((T, 3), dtype=torch.float32, device=dev),
+               "cost": torch.empty(K, dtype=torch.float32, device=dev),
+               "weights": torch.empty(K, dtype=torch.float32, device=dev),
+               "collide": torch.empty(K, dtype=torch.uint8, device=dev)}
+    d = _mppi_desc(K, T, dt, radius, nsigma, lam, w_collision, w_goal, w_terminal, w_control, goal)
+    p = (params or QueryParams()).to_c()
+    p.stream = abi.stream_handle(stream)
+    check(abi.cs_mppi_step(scene.handle, d, x0, U, eps, out["U"], out.get("cost"), out.get("weights"),
+                           out.get("collide"), p))
+    return out
+
+
+class MppiGraph:
+    """One MPPI iteration captured into a CUDA graph (cs_mppi_graph_create)
+    over fixed device tensors x0 [3], U [T,3], eps [K,T,3]; each launch()
+    reads what they hold then and writes `out` (U_out = U updates in place
+    when in_place=True)."""
+
+    def __init__(self, scene: Scene, x0, U, eps, *, in_place=False, dt=0.1, radius=0.15, nsigma=1.0, lam=1.0,
+                 w_collision=10.0, w_goal=0.1, w_terminal=1.0, w_control=0.01, goal=(0.0, 0.0, 0.0),
+                 params: QueryParams | None = None):
+        torch = _torch()
+        for t in (x0, U, eps):
+            assert t.is_cuda and t.is_contiguous() and t.dtype == torch.float32
+        self.x0, self.U, self.eps = x0, U, eps
+        T, K = U.shape[0], eps.shape[0]
+        dev = U.device
+        self.out = {"U": U if in_place else torch.empty((T, 3), dtype=torch.float32, device=dev),
+                    "cost": torch.empty(K, dtype=torch.float32, device=dev),
+                    "weights": torch.empty(K, dtype=torch.float32, device=dev),
+                    "collide": torch.empty(K, dtype=torch.uint8, device=dev)}
+        d = _mppi_desc(K, T, dt, radius, nsigma, lam, w_collision, w_goal, w_terminal, w_control, goal)
+        p = (params or QueryParams()).to_c()
+        self._h = ctypes.c_void_p()
+        check(abi.cs_mppi_graph_create(scene.handle, d, x0, U, eps, self.out["U"], self.out["cost"],
+                                       self.out["weights"], self.out["collide"], p, self._h))
+        self.kernels = abi.cs_graph_kernels(self._h)
+
+    def launch(self, stream=None):
+        check(abi.cs_graph_launch(self._h, stream))
+        return self.out
+
+    def sync(self, stream=None):
+        check(abi.cs_graph_sync(self._h, stream))
+
+    def close(self):
+        if self._h:
+            check(abi.cs_graph_destroy(self._h))
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -128,6 +128,22 @@ class cs_server_stats(ctypes.Structure):
     ]
 
 
+class cs_mppi_desc(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("dt", ctypes.c_float),
+        ("radius", ctypes.c_float),
+        ("nsigma", ctypes.c_float),
+        ("lambda_", ctypes.c_float),
+        ("w_collision", ctypes.c_float),
+        ("w_goal", ctypes.c_float),
+        ("w_terminal", ctypes.c_float),
+        ("w_control", ctypes.c_float),
+        ("goal", ctypes.c_float * 3),
+    ]
+
+
 CS_TILE_TUNED = -1
 
 _P = ctypes.c_void_p
@@ -148,6 +164,8 @@ _SIGNATURES = {
     "cs_sync": (ctypes.c_int, [_P, _P]),
     "cs_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P,
                                        ctypes.POINTER(cs_params), ctypes.POINTER(_P)]),
+    "cs_mppi_graph_create": (ctypes.c_int, [_P, ctypes.POINTER(cs_mppi_desc), _P, _P, _P, _P, _P, _P, _P,
+                                            ctypes.POINTER(cs_params), ctypes.POINTER(_P)]),
     "cs_graph_launch": (ctypes.c_int, [_P, _P]),
     "cs_graph_sync": (ctypes.c_int, [_P, _P]),
     "cs_graph_kernels": (ctypes.c_int64, [_P]),
@@ -155,6 +173,8 @@ _SIGNATURES = {
     "cs_autotune": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float,
                                    ctypes.POINTER(cs_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                    _P, ctypes.c_int32]),
+    "cs_mppi_step": (ctypes.c_int, [_P, ctypes.POINTER(cs_mppi_desc), _P, _P, _P, _P, _P, _P, _P,
+                                    ctypes.POINTER(cs_params)]),
     "cs_server_config_init": (ctypes.c_int, [ctypes.POINTER(cs_server_config)]),
     "cs_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cs_server_config), ctypes.POINTER(_P)]),
     "cs_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(cs_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -296,6 +316,13 @@ def cs_graph_create(scene, prim_type, prims, Q, conservatism, out_metric, out_co
                                   None if params is None else ctypes.byref(params), ctypes.byref(out))
 
 
+def cs_mppi_graph_create(scene, desc, x0, U, eps, U_out, cost, weights, collide, params,
+                         out: ctypes.c_void_p) -> int:
+    return load().cs_mppi_graph_create(scene, ctypes.byref(desc), ptr(x0), ptr(U), ptr(eps), ptr(U_out), ptr(cost),
+                                       ptr(weights), ptr(collide), None if params is None else ctypes.byref(params),
+                                       ctypes.byref(out))
+
+
 def cs_graph_launch(graph, stream) -> int:
     return load().cs_graph_launch(graph, stream_handle(stream))
 
@@ -316,6 +343,11 @@ def cs_autotune(scene, prim_type, prims, Q, conservatism, params, reps, best: ct
     return load().cs_autotune(scene, prim_type, ptr(prims), int(Q), float(conservatism),
                               None if params is None else ctypes.byref(params), int(reps), ctypes.byref(best),
                               ptr(ms), int(cap))
+
+
+def cs_mppi_step(scene, desc: cs_mppi_desc, x0, U, eps, U_out, cost, weights, collide, params) -> int:
+    return load().cs_mppi_step(scene, ctypes.byref(desc), ptr(x0), ptr(U), ptr(eps), ptr(U_out), ptr(cost),
+                               ptr(weights), ptr(collide), None if params is None else ctypes.byref(params))
 
 
 def cs_server_config_init(cfg: cs_server_config) -> int:

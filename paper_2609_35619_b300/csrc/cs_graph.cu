@@ -46,43 +46,22 @@ static cs_status check_graph(const cs_graph *h) {
     return CS_OK;
 }
 
-}  // namespace cs
-
-using namespace cs;
-
-extern "C" {
-
-cs_status cs_graph_create(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
-                          float conservatism, float *out_metric, uint8_t *out_collide,
-                          const float *grad_out, float *grad_centres, const cs_params *params,
-                          cs_graph **out) {
-    if (!out) return invalid("out is NULL");
-    *out = nullptr;
-    cs_status st = check_scene(scene);
-    if (st != CS_OK) return st;
-    cs_params p;
-    if (params) p = *params;
-    else cs_params_init(&p);
-    if (p.host_io) return invalid("a query graph takes device buffers only (host_io must be 0)");
-    if (Q <= 0) return invalid("a query graph needs Q > 0");
-    const bool grad = grad_centres != nullptr;
-    if (grad && (out_metric || out_collide))
-        return invalid("an adjoint graph takes grad_centres only (out_metric, out_collide NULL)");
-    p.eval_events[0] = p.eval_events[1] = nullptr;
-
+// Capture `enqueue(stream, workspace)` on a private stream with private
+// scratch (already grown by `reserve`) into an instantiated graph.
+template <class Reserve, class Enqueue>
+static cs_status capture_graph(Reserve reserve, Enqueue enqueue, cs_graph **out) {
     Graph *g = new Graph();
     cudaError_t e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_graph(g);
         return cuda_fail(e, "cudaStreamCreateWithFlags");
     }
-    p.stream = g->capture;
-    if ((st = new_workspace(g->capture, &g->ws)) != CS_OK ||
-        (st = grow_workspace(g->ws, (size_t)Q, false)) != CS_OK) {
+    cs_status st;
+    if ((st = new_workspace(g->capture, &g->ws)) != CS_OK || (st = reserve(g->ws)) != CS_OK) {
         free_graph(g);
         return st;
     }
-    // argument errors surface here, before anything is captured
+    // the scratch is ready and argument errors surface before anything is captured
     e = cudaStreamSynchronize(g->capture);
     if (e != cudaSuccess) {
         free_graph(g);
@@ -94,8 +73,7 @@ cs_status cs_graph_create(const cs_scene *scene, int32_t prim_type, const float 
         free_graph(g);
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
-    st = query_common(scene, prim_type, prims, Q, conservatism, &p, grad, out_metric, out_collide,
-                      grad_out, grad_centres, g->ws);
+    st = enqueue(g->capture, g->ws);
     const int64_t k1 = launch_total();
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->capture, &graph);
@@ -119,6 +97,58 @@ cs_status cs_graph_create(const cs_scene *scene, int32_t prim_type, const float 
     g->magic = kGraphMagic;
     *out = reinterpret_cast<cs_graph *>(g);
     return CS_OK;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+cs_status cs_graph_create(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
+                          float conservatism, float *out_metric, uint8_t *out_collide,
+                          const float *grad_out, float *grad_centres, const cs_params *params,
+                          cs_graph **out) {
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    cs_status st = check_scene(scene);
+    if (st != CS_OK) return st;
+    cs_params p;
+    if (params) p = *params;
+    else cs_params_init(&p);
+    if (p.host_io) return invalid("a query graph takes device buffers only (host_io must be 0)");
+    if (Q <= 0) return invalid("a query graph needs Q > 0");
+    const bool grad = grad_centres != nullptr;
+    if (grad && (out_metric || out_collide))
+        return invalid("an adjoint graph takes grad_centres only (out_metric, out_collide NULL)");
+    p.eval_events[0] = p.eval_events[1] = nullptr;
+    return capture_graph([&](Workspace *w) { return grow_workspace(w, (size_t)Q, false); },
+                         [&](cudaStream_t s, Workspace *w) {
+                             p.stream = s;
+                             return query_common(scene, prim_type, prims, Q, conservatism, &p, grad, out_metric,
+                                                 out_collide, grad_out, grad_centres, w);
+                         },
+                         out);
+}
+
+cs_status cs_mppi_graph_create(const cs_scene *scene, const cs_mppi_desc *desc, const float *x0, const float *U,
+                               const float *eps, float *U_out, float *cost, float *weights, uint8_t *collide,
+                               const cs_params *params, cs_graph **out) {
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    cs_status st = mppi_check(scene, desc, x0, U, eps, U_out);
+    if (st != CS_OK) return st;
+    cs_params p;
+    if (params) p = *params;
+    else cs_params_init(&p);
+    if (p.host_io) return invalid("an MPPI graph takes device buffers only (host_io must be 0)");
+    p.eval_events[0] = p.eval_events[1] = nullptr;
+    return capture_graph([&](Workspace *w) { return mppi_reserve(w, desc->K, desc->T); },
+                         [&](cudaStream_t s, Workspace *w) {
+                             p.stream = s;
+                             return mppi_common(scene, desc, x0, U, eps, U_out, cost, weights, collide, &p, w);
+                         },
+                         out);
 }
 
 cs_status cs_graph_launch(cs_graph *h, void *stream) {

@@ -106,6 +106,9 @@ struct Workspace {
     float *io_gout = nullptr;
     float *io_gm = nullptr;
     uint8_t *io_gc = nullptr;
+    // MPPI iteration scratch (cs_mppi_step): sphere centres of the rollouts
+    // [K*T,4], then per rollout the collision cost and the task + control cost
+    float *mppi = nullptr;           size_t cap_mppi = 0;  // floats
     unsigned *err = nullptr;         // device error word
 };
 
@@ -150,6 +153,14 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
                        Workspace *own_ws);
 int tile_configs(int32_t *ids, int32_t cap);
 int64_t launch_total();
+
+// One MPPI iteration (cs_mppi_step); own_ws = scratch owned by a graph.
+cs_status mppi_common(const cs_scene *scene, const cs_mppi_desc *d, const float *x0, const float *U,
+                      const float *eps, float *U_out, float *cost, float *weights, uint8_t *collide,
+                      const cs_params *params, Workspace *own_ws);
+cs_status mppi_reserve(Workspace *w, int64_t K, int64_t T);
+cs_status mppi_check(const cs_scene *scene, const cs_mppi_desc *d, const float *x0, const float *U,
+                     const float *eps, const float *U_out);
 
 // ------------------------------------------------------- launch accounting
 // Host-side count of kernel launches (cs_launch_count); every launcher adds
