@@ -416,9 +416,16 @@ def serve_setup(torch, cs, dev):
     scenes_h = [S.apartment_scene(seed=1005), S.apartment_scene(seed=1006)]
     scenes = [cs.Scene(s["means"], s["scales"], s["quats"], s["opacity"], device=dev) for s in scenes_h]
     # tile shape per scene from the autotuner, on a full-size request mix
-    tune = S.serving_requests(seed=1999, count=24, q_lo=4096, q_hi=262_144)
-    big = torch.as_tensor(np.concatenate([r["spheres"] for r in tune])[:1 << 19], device=dev)
-    tiles = [sc.autotune(big, 1.0, reps=2)[0] for sc in scenes]
+    # tile shapes per batch-size class from the autotuner, on request mixes
+    tune = S.serving_requests(seed=1999, count=48, q_lo=16, q_hi=262_144)
+    rows = np.concatenate([r["spheres"] for r in tune])
+    tiles = []
+    for sc in scenes:
+        per = {}
+        for lg in (9, 12, 15, 17, 19):
+            batch = torch.as_tensor(rows[: 1 << lg], device=dev)
+            per[1 << lg] = sc.autotune(batch, 1.0, reps=2)[0]
+        tiles.append(per)
     torch.cuda.synchronize(dev)
     return scenes_h, scenes, tiles
 
@@ -640,6 +647,14 @@ def oracle_sample(target_s: float, seed: int = 0):
     t0 = time.perf_counter()
     res = oracle.query(scene, sample, 0, 1.0)
     dt = time.perf_counter() - t0
+    if dt < 0.5 * target_s and rows < 65536:  # the probe overestimated the cost of a row: once more, larger
+        rows = int(min(65536, rows * target_s / max(dt, 1e-3)))
+        rows -= rows % 2
+        sample = np.concatenate([arm[rng.choice(arm.shape[0], rows // 2, replace=False)],
+                                 edge[rng.choice(edge.shape[0], rows // 2, replace=False)]])
+        t0 = time.perf_counter()
+        res = oracle.query(scene, sample, 0, 1.0)
+        dt = time.perf_counter() - t0
     useful = int(res["count_nbr"].sum())
     n = scene["means"].shape[0]
     return {"value": useful / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",

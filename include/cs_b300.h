@@ -117,7 +117,8 @@ typedef struct cs_params {
     int32_t host_io;           /* 1: prims, nsigma_per_query, grad_out and every output are
                                   host pointers; the call copies in, computes, copies out and
                                   returns after the stream has finished */
-    int32_t tile_config;       /* 0 = the default shape; CS_TILE_TUNED = the shape cs_autotune
+    int32_t tile_config;       /* 0 = the default shape (23 for up to 2^17 rows, else 18);
+                                  CS_TILE_TUNED = the shape cs_autotune
                                   chose for this scene, primitive type, mode and batch-size
                                   class (the default when none was tuned); otherwise a value
                                   from cs_tile_configs.  cs_query_grad has its own shapes:

@@ -124,7 +124,7 @@ cs_status grow_workspace(Workspace *w, size_t Q, bool host_io) {
         CS_CUDA(cudaMalloc(&w->keys[1], 4 * cap));
         CS_CUDA(cudaMalloc(&w->vals[0], 4 * cap));
         CS_CUDA(cudaMalloc(&w->vals[1], 4 * cap));
-        w->cap_hist = sort_hist_elems(cap);
+        w->cap_hist = std::max(sort_hist_elems(cap), kPrepHistElems);
         CS_CUDA(cudaMalloc(&w->sort_hist, 4 * w->cap_hist));
         w->cap_scan_tmp = scan_tmp_elems(w->cap_hist);
         CS_CUDA(cudaMalloc(&w->scan_tmp, 4 * w->cap_scan_tmp));

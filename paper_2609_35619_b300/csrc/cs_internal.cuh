@@ -126,6 +126,10 @@ struct Scene {
     uint32_t magic = 0;
 };
 
+// Histogram entries the query preparation needs beyond the radix sort's
+// (the small-batch counting sort over 2^16 buckets, plus its total).
+constexpr size_t kPrepHistElems = (1u << 16) + 1;
+
 // Query scratch is pooled per (device, stream) and shared by every scene
 // used on that stream; it lives until cs_release_scratch or process exit.
 cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io, Workspace **out);

@@ -18,6 +18,8 @@
 // other and must be serialised by the caller.
 #include <mutex>
 
+#include <algorithm>
+
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -40,7 +42,8 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // scan partials, prepared rows (up to three float4 per row), n_sigma per row,
 // per-row metric and flag for group-only requests, the error word
 constexpr size_t kKeyBytes = align256(4 * kRows);
-constexpr size_t kHistElems = 256 * (kRows / 4096 + 1);
+constexpr size_t kHistElems = 256 * (kRows / 4096 + 1) > kPrepHistElems ? 256 * (kRows / 4096 + 1)
+                                                                          : kPrepHistElems;
 constexpr size_t kHistBytes = align256(4 * kHistElems);
 constexpr size_t kScanElems = 1024;
 constexpr size_t kScanBytes = align256(4 * kScanElems);
@@ -103,7 +106,8 @@ extern "C" cs_status cs_query_noalloc(const cs_scene *scene, int32_t prim_type, 
     if (dev != sc->device) return invalid("the scene's device must be the current device");
     unsigned char *base = nullptr;
     if ((st = scratch_base(dev, &base)) != CS_OK) return st;
-    if (sort_hist_elems((size_t)Q) > kHistElems || scan_tmp_elems(kHistElems) > kScanElems)
+    if (std::max(sort_hist_elems((size_t)Q), kPrepHistElems) > kHistElems ||
+        scan_tmp_elems(kHistElems) > kScanElems)
         return invalid("internal: no-allocation scratch layout too small");
 
     // carve the area (no allocation): the same buffers cs_query takes from its pool

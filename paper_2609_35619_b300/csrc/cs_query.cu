@@ -95,6 +95,7 @@ struct SlotMeta {
 //   sphere:    (c, 1/r^2) (2n, alpha, beta, live) - -
 //   ellipsoid: (c, 2n) (Axx, Ayy, Azz, Axy) (Axz, Ayz, alpha, beta) (live, - - -)
 constexpr int kQRec = 4;
+constexpr int kSub = 8;  // sub-boxes of a tile in the producer's cull
 
 template <class C>
 struct __align__(16) EvalSmem {
@@ -106,6 +107,9 @@ struct __align__(16) EvalSmem {
     uint64_t full[C::NS];
     uint64_t empty[C::NS];
     float4 q[C::NCW * C::QW][kQRec];
+    // the producer's sub-boxes: rows [k TQ/kSub, (k + 1) TQ/kSub) of the tile,
+    // (min centre, max alpha) (max centre, max beta)
+    float4 sub[kSub][2];
     // spheres, each value duplicated for packed evaluation against two
     // Gaussians at once: (-cx, -cx, -cy, -cy) (-cz, -cz, 1/r^2, 1/r^2) (-2n, -2n, 0, 0)
     float4 qd[C::NCW * C::QW][3];
@@ -231,9 +235,19 @@ struct Producer {
         }
     }
     // Does the tile box + reach meet a chunk or tree node?
+    // The tile box first, then its kSub sub-boxes of consecutive rows: a
+    // sparse tile (primitives scattered over the scene) stages only what
+    // some group of its rows can reach.
     __device__ bool meets(const NodeBox &b) const {
         const float R = reach(al, be, b.lo.w, sc->pad_abs);
-        return box_gap2(lx, ly, lz, hx, hy, hz, b.lo, b.hi) <= R * R;
+        if (box_gap2(lx, ly, lz, hx, hy, hz, b.lo, b.hi) > R * R) return false;
+#pragma unroll 1
+        for (int k = 0; k < kSub; ++k) {
+            const float4 lo = sm->sub[k][0], hi = sm->sub[k][1];
+            const float Rk = reach(lo.w, hi.w, b.lo.w, sc->pad_abs);
+            if (box_gap2(lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, b.lo, b.hi) <= Rk * Rk) return true;
+        }
+        return false;
     }
     // Lane-parallel test of the up to 32 records [base, base + 32) of `recs`.
     __device__ unsigned test32(const NodeBox *recs, int base, int count) const {
@@ -312,19 +326,43 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile) {
     float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY,
           hz = -INFINITY, al = 0.f, be = 0.f;
     const int q0 = tile * TQ;
-    for (int t = lane; t < TQ; t += 32) {
-        int q = q0 + t;
-        if (q >= a.Q) break;
-        const float4 *rec = a.qrec + (size_t)q * RECS;
-        float4 r0 = rec[0];
-        if (!rec_valid(r0)) continue;
-        float alpha, beta;
-        prim_reach<PRIM>(rec, a.qns[q], a.k.S_reach, alpha, beta);
-        lx = fminf(lx, r0.x); ly = fminf(ly, r0.y); lz = fminf(lz, r0.z);
-        hx = fmaxf(hx, r0.x); hy = fmaxf(hy, r0.y); hz = fmaxf(hz, r0.z);
+    constexpr int RS = TQ / kSub;  // rows per sub-box (4, 8 or 16: within one pass of 32 lanes)
+    static_assert(TQ % kSub == 0 && RS <= 32 && 32 % RS == 0, "sub-boxes split the tile's rows evenly");
+#pragma unroll
+    for (int t0 = 0; t0 < TQ; t0 += 32) {
+        const int t = t0 + lane, q = q0 + t;
+        float cx = INFINITY, cy = INFINITY, cz = INFINITY, dx = -INFINITY, dy = -INFINITY, dz = -INFINITY;
+        float alpha = 0.f, beta = 0.f;
+        if (t < TQ && q < a.Q) {
+            const float4 *rec = a.qrec + (size_t)q * RECS;
+            const float4 r0 = rec[0];
+            if (rec_valid(r0)) {
+                prim_reach<PRIM>(rec, a.qns[q], a.k.S_reach, alpha, beta);
+                cx = dx = r0.x; cy = dy = r0.y; cz = dz = r0.z;
+            }
+        }
+        lx = fminf(lx, cx); ly = fminf(ly, cy); lz = fminf(lz, cz);
+        hx = fmaxf(hx, dx); hy = fmaxf(hy, dy); hz = fmaxf(hz, dz);
         al = fmaxf(al, alpha);
         be = fmaxf(be, beta);
+        // sub-box of the RS consecutive rows of this lane's group
+#pragma unroll
+        for (int o = RS / 2; o > 0; o >>= 1) {
+            cx = fminf(cx, __shfl_xor_sync(0xffffffffu, cx, o));
+            cy = fminf(cy, __shfl_xor_sync(0xffffffffu, cy, o));
+            cz = fminf(cz, __shfl_xor_sync(0xffffffffu, cz, o));
+            dx = fmaxf(dx, __shfl_xor_sync(0xffffffffu, dx, o));
+            dy = fmaxf(dy, __shfl_xor_sync(0xffffffffu, dy, o));
+            dz = fmaxf(dz, __shfl_xor_sync(0xffffffffu, dz, o));
+            alpha = fmaxf(alpha, __shfl_xor_sync(0xffffffffu, alpha, o));
+            beta = fmaxf(beta, __shfl_xor_sync(0xffffffffu, beta, o));
+        }
+        if (t < TQ && lane % RS == 0) {
+            sm->sub[t / RS][0] = make_float4(cx, cy, cz, alpha);
+            sm->sub[t / RS][1] = make_float4(dx, dy, dz, beta);
+        }
     }
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
@@ -923,6 +961,10 @@ __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalA
 }
 
 // ------------------------------------------------------ preparation kernels
+constexpr int kBucketBits = 16;            // buckets of the small-batch counting sort
+constexpr int kBucketShift = 29 - kBucketBits;  // keys have 29 bits (24 Morton + 5 size class)
+constexpr int kBucketMaxQ = 1 << 17;       // batches up to this size take the counting sort
+constexpr uint32_t kBuckets() { return 1u << kBucketBits; }
 __device__ __forceinline__ uint32_t spread8(uint32_t v) {
     v &= 0xFFu;
     v = (v | (v << 8)) & 0x0300F00Fu;
@@ -937,7 +979,8 @@ __device__ __forceinline__ uint32_t spread8(uint32_t v) {
 // primitives close together, so the tile box the producer culls with stays
 // small even when a batch is sparse and mixes many sizes.
 __global__ void k_prep_keys(const float *__restrict__ prims, int prim_type, int Q, SceneDev sc,
-                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                            uint32_t *__restrict__ bucket_hist) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Q) return;
     const int stride = prim_type == CS_PRIM_SPHERE ? 4 : 10;
@@ -957,8 +1000,31 @@ __global__ void k_prep_keys(const float *__restrict__ prims, int prim_type, int 
         const int half_oct = 2 * ((bits >> 23) & 0xFF) + ((bits >> 22) & 1) - 2 * (127 - 10);
         cls = (uint32_t)min(max(half_oct, 0), 31);
     }
-    keys[j] = (code << 5) | cls;
+    const uint32_t key = (code << 5) | cls;
+    keys[j] = key;
     vals[j] = (uint32_t)j;
+    if (bucket_hist) atomicAdd(&bucket_hist[key >> kBucketShift], 1u);
+}
+
+// Counting sort of the rows by the bucket of their key (the top 16 Morton
+// bits: cells of 1/40 of the scene box per axis), for batches small enough
+// that the key's full radix sort is launch-bound.  The order inside a bucket
+// follows the atomics; that changes which rows share a tile, never a row's
+// result (each row's reductions run in a fixed order whatever its tile).
+// Warp-aggregated: lanes with the same bucket take one atomic.
+__global__ void k_bucket_scatter(const uint32_t *__restrict__ keys, int Q, uint32_t *__restrict__ offs,
+                                 uint32_t *__restrict__ perm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned active = __ballot_sync(0xffffffffu, j < Q);
+    if (j >= Q) return;
+    const uint32_t b = keys[j] >> kBucketShift;
+    const unsigned peers = __match_any_sync(active, b);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&offs[b], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    perm[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)j;
 }
 
 // Prepared records in sorted order.  Sphere: (c, r).  Ellipsoid:
@@ -1070,6 +1136,8 @@ QueryConsts make_consts(const cs_params &p) {
 //   16: shape 1 with the tile's rows interleaved over the consumer warps
 //   17-19: shapes 1, 15, 13 with row pairs interleaved over the consumer warps
 //   20, 21: shape 18 evaluating sphere primitives one at a time / in groups of 4
+//   22: 2 x 8, 2 stages x 12 chunks, 6 CTAs/SM (small or sparse batches: more, tighter tiles)
+//   23: 1 x 8, 2 stages x 10 chunks, 8 CTAs/SM
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1091,6 +1159,8 @@ using Cfg18 = Cfg<8, 8, 2, 32, 2, 2, 2>;
 using Cfg19 = Cfg<4, 16, 3, 16, 3, 2, 2>;
 using Cfg20 = Cfg<8, 8, 2, 32, 2, 1, 2>;
 using Cfg21 = Cfg<8, 8, 2, 32, 2, 4, 2>;
+using Cfg22 = Cfg<2, 8, 2, 12, 6, 2, 2>;
+using Cfg23 = Cfg<1, 8, 2, 10, 8, 2, 0>;
 // Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
 // three gradient sums per primitive, so its tiles hold fewer primitives
 //   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
@@ -1102,8 +1172,10 @@ using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
 constexpr int kDefaultGradTile = 2;
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23};
 constexpr int kDefaultTile = 18;
+constexpr int kSmallBatchTile = 23;
+constexpr int kSmallBatchQ = 1 << 17;
 
 int tile_configs(int32_t *ids, int32_t cap) {
     int n = (int)(sizeof(kTileIds) / sizeof(kTileIds[0]));
@@ -1174,6 +1246,8 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 19: return launch_mode<PRIM, Cfg19>(a, s);
         case 20: return launch_mode<PRIM, Cfg20>(a, s);
         case 21: return launch_mode<PRIM, Cfg21>(a, s);
+        case 22: return launch_mode<PRIM, Cfg22>(a, s);
+        case 23: return launch_mode<PRIM, Cfg23>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }
@@ -1181,7 +1255,10 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
 cudaError_t launch_eval(int prim_type, const EvalArgs &a, bool grad, int tile_cfg, int num_sms,
                         cudaStream_t s) {
     (void)num_sms;
-    const int tile = tile_cfg > 0 ? tile_cfg : grad ? 0 : kDefaultTile;
+    // default forward shape: one primitive row of eight per tile for batches
+    // up to 2^17 rows (more, tighter tiles: small or sparse batches fill the
+    // GPU and stage less), shape 18 above
+    const int tile = tile_cfg > 0 ? tile_cfg : grad ? 0 : (a.Q <= kSmallBatchQ ? kSmallBatchTile : kDefaultTile);
     return prim_type == CS_PRIM_SPHERE ? launch_prim<0>(a, grad, tile, s) : launch_prim<1>(a, grad, tile, s);
 }
 
@@ -1233,10 +1310,23 @@ cudaError_t run_wait_selftest(long long polls, unsigned *err, cudaStream_t s) {
 void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, float ns_scalar,
                  const float *ns_rows, Workspace &ws, uint32_t **perm_out, cudaStream_t s) {
     const int thr = 256, blk = (Q + thr - 1) / thr;
-    k_prep_keys<<<blk, thr, 0, s>>>(prims, prim_type, Q, sc, ws.keys[0], ws.vals[0]);
-    count_launches(1);
-    int res = radix_sort(ws.keys, ws.vals, (size_t)Q, 32, ws.sort_hist, ws.scan_tmp, s);
-    uint32_t *perm = ws.vals[res];
+    uint32_t *perm;
+    if (Q <= kBucketMaxQ) {
+        // small batch: keys with the bucket histogram, scan, one scatter
+        uint32_t *hist = ws.sort_hist;
+        cudaMemsetAsync(hist, 0, 4 * ((size_t)kBuckets() + 1), s);
+        k_prep_keys<<<blk, thr, 0, s>>>(prims, prim_type, Q, sc, ws.keys[0], ws.vals[0], hist);
+        count_launches(1);
+        scan_exclusive(hist, hist, (size_t)kBuckets() + 1, ws.scan_tmp, s);
+        perm = ws.vals[1];
+        k_bucket_scatter<<<blk, thr, 0, s>>>(ws.keys[0], Q, hist, perm);
+        count_launches(1);
+    } else {
+        k_prep_keys<<<blk, thr, 0, s>>>(prims, prim_type, Q, sc, ws.keys[0], ws.vals[0], nullptr);
+        count_launches(1);
+        int res = radix_sort(ws.keys, ws.vals, (size_t)Q, 32, ws.sort_hist, ws.scan_tmp, s);
+        perm = ws.vals[res];
+    }
     k_prep_recs<<<blk, thr, 0, s>>>(prims, prim_type, Q, perm, ns_scalar, ns_rows, ws.qrec,
                                     ws.qns, ws.err);
     count_launches(1);

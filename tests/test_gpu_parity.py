@@ -52,7 +52,7 @@ def test_tiny_scene_all_modes(cs, nsigma, mode):
     assert rep["checked"] > 0.9 * rep["Q"]
 
 
-@pytest.mark.parametrize("cfg", list(range(1, 22)))
+@pytest.mark.parametrize("cfg", list(range(1, 24)))
 @pytest.mark.parametrize("Q", [1, 37, 1000, 5000])
 def test_tile_configs_and_ragged_batches(cs, cfg, Q):
     """Every tile shape, batch sizes spanning one to many tiles with a ragged tail."""
