@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--batch", default="arm", choices=["arm", "edge"], help="query batch for --case eval")
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
+    ap.add_argument("--flags", action="store_true", help="--case eval: collision flags only (early exit)")
     return ap.parse_args()
 
 
@@ -699,7 +700,8 @@ def run_eval_case(args):
     arm = torch.as_tensor(S.arm_queries() if args.batch == "arm" else S.edge_queries(), device=dev)
     scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
     G = 64 if args.batch == "arm" else 1024
-    qp = cs.QueryParams(group_size=G, tile_config=args.tile)
+    qp = cs.QueryParams(group_size=G, tile_config=args.tile,
+                        mode=cs.CS_METRIC_FLAGS if args.flags else cs.CS_METRIC_MEAN_COST)
     ns = args.nsigma
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
     kstats = torch.zeros(16, dtype=torch.int64, device=dev)

@@ -77,7 +77,14 @@ typedef enum cs_metric_mode {
     CS_METRIC_MEAN_COST = 0,  /* Eq. 11 averaged over N_j (MPPI, Section II-D) */
     CS_METRIC_SUM_COST = 1,   /* Eq. 11 summed over N_j */
     CS_METRIC_MIN_S2 = 2,     /* min over N_j of Eq. 8 */
-    CS_METRIC_SOFTMIN_S2 = 3  /* softmin over N_j of Eq. 8 (Section II-B) */
+    CS_METRIC_SOFTMIN_S2 = 3, /* softmin over N_j of Eq. 8 (Section II-B) */
+    CS_METRIC_FLAGS = 4       /* collision flags only (Section II-E), with early exit: a row
+                                 stops once its in-collision count exceeds k_thr, and with
+                                 group_size > 0 the rows of a group stop once one of them
+                                 collides.  out_collide per row: 1 in collision, 0 free,
+                                 2 not finished because its group collides; the group flag
+                                 is exact.  out_metric, out_count, out_group_metric are not
+                                 written; cs_query_grad rejects this mode. */
 } cs_metric_mode;
 
 /* Scene description for cs_scene_create (Section II-A, Eq. 1-2). */

@@ -53,6 +53,7 @@ class _Params(ctypes.Structure):
         ("extent_max", ctypes.c_double),
         ("use_filter", ctypes.c_int32),
         ("nthreads", ctypes.c_int32),
+        ("band", ctypes.c_double),
     ]
 
 
@@ -77,6 +78,7 @@ class Params:
     extent_max: float = 0.1
     use_filter: bool = True
     nthreads: int = 0
+    band: float = 1e-5  # width of the reporting bands (band_cut, band_in, band_kink)
 
     @property
     def s_cut(self) -> float:
@@ -85,7 +87,7 @@ class Params:
     def _c(self) -> _Params:
         return _Params(self.gamma, self.d_max, self.s_min, self.eps, self.tau, int(self.k_thr),
                        self.opacity_min, self.extent_max, int(bool(self.use_filter)),
-                       int(self.nthreads))
+                       int(self.nthreads), float(self.band))
 
 
 _lib = None

@@ -53,6 +53,7 @@ typedef struct {
     double extent_max;
     int32_t use_filter;
     int32_t nthreads;   /* <= 0: OpenMP default */
+    double band;        /* width of the reporting bands below (<= 0: 1e-5) */
 } orc_params;
 
 /* Per-query outputs.  Any pointer may be NULL. */
@@ -65,12 +66,12 @@ typedef struct {
     double *min_s2;     /* min over N_j of st^2 (+inf if empty) */
     double *softmin;    /* -tau ln sum exp(-st^2/tau) (+inf if empty) */
     /* diagnostics used by the parity tests */
-    int64_t *band_cut;  /* pairs with |st^2 - S_cut| <= 1e-5 S_cut */
-    int64_t *band_in;   /* pairs with |st^2 - 1| <= 1e-5 */
+    int64_t *band_cut;  /* pairs with |st^2 - S_cut| <= band S_cut (band = 1e-5 by default) */
+    int64_t *band_in;   /* pairs with |st^2 - 1| <= band */
     double *cond;       /* max over N_j of s^2 + n_sigma sqrt(sigma^2) */
     double *min_cond;   /* s^2 + n_sigma sqrt(sigma^2) of the argmin pair */
-    int64_t *band_kink; /* pairs near a kink of the gradient: |st^2 - s_min| <= 1e-5 or
-                           the Eq. 8 clamp within 1e-5 of its switching point */
+    int64_t *band_kink; /* pairs near a kink of the gradient: |st^2 - s_min| <= band or
+                           the Eq. 8 clamp within band of its switching point */
 } orc_outputs;
 
 /* ---- geometry -------------------------------------------------------- */
@@ -231,6 +232,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
 {
     const int stride = prim_type == 0 ? 4 : 10;
     const double S_cut = cutoff(prm);
+    const double band = prm->band > 0.0 ? prm->band : 1e-5;
     double *Sig = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
     uint8_t *keep = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     if (!Sig || !keep) { free(Sig); free(keep); return -2; }
@@ -255,11 +257,11 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
             double Sg[3][3] = {{S[0], S[1], S[2]}, {S[3], S[4], S[5]}, {S[6], S[7], S[8]}};
             double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
             pair_terms t = evaluate_pair(mu, Sg, c, A, ns);
-            if (fabs(t.st2 - S_cut) <= 1e-5 * S_cut) ++bcut;
-            if (fabs(t.st2 - 1.0) <= 1e-5) ++bin;
-            if (t.st2 <= S_cut * (1.0 + 1e-5) &&
-                (fabs(t.st2 - prm->s_min) <= 1e-5 * fmax(1.0, fabs(prm->s_min)) ||
-                 fabs(t.raw) <= 1e-5 * (t.s2 + ns * sqrt(t.var))))
+            if (fabs(t.st2 - S_cut) <= band * S_cut) ++bcut;
+            if (fabs(t.st2 - 1.0) <= band) ++bin;
+            if (t.st2 <= S_cut * (1.0 + band) &&
+                (fabs(t.st2 - prm->s_min) <= band * fmax(1.0, fabs(prm->s_min)) ||
+                 fabs(t.raw) <= band * (t.s2 + ns * sqrt(t.var))))
                 ++bkink;
             if (!(t.st2 <= S_cut)) continue;
             ++cnt;

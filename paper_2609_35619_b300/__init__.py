@@ -23,12 +23,12 @@ import ctypes
 from dataclasses import dataclass
 
 from . import abi
-from .abi import (CS_METRIC_MEAN_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_SUM_COST,
+from .abi import (CS_METRIC_FLAGS, CS_METRIC_MEAN_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_SUM_COST,
                   CS_PRIM_ELLIPSOID, CS_PRIM_SPHERE, CsError, check)
 
 __all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "mppi_step", "MppiGraph", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
            "CS_PRIM_SPHERE", "CS_PRIM_ELLIPSOID", "CS_METRIC_MEAN_COST", "CS_METRIC_SUM_COST",
-           "CS_METRIC_MIN_S2", "CS_METRIC_SOFTMIN_S2", "CsError"]
+           "CS_METRIC_MIN_S2", "CS_METRIC_SOFTMIN_S2", "CS_METRIC_FLAGS", "CsError"]
 
 
 @dataclass

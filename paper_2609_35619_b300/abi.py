@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libcs_b300.so")
 CS_OK, CS_ERR_INVALID_ARG, CS_ERR_NO_MEMORY, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_BAD_HANDLE, \
     CS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 CS_PRIM_SPHERE, CS_PRIM_ELLIPSOID = 0, 1
-CS_METRIC_MEAN_COST, CS_METRIC_SUM_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2 = 0, 1, 2, 3
+CS_METRIC_MEAN_COST, CS_METRIC_SUM_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_FLAGS = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "CS_OK", -1: "CS_ERR_INVALID_ARG", -2: "CS_ERR_NO_MEMORY", -3: "CS_ERR_CUDA",
                 -4: "CS_ERR_TIMEOUT", -5: "CS_ERR_BAD_HANDLE", -6: "CS_ERR_UNSUPPORTED"}

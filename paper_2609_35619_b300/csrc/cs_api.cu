@@ -27,7 +27,7 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
                      const uint32_t *perm, int Q, const cs_params &p, float *out_metric,
                      uint8_t *out_collide, int32_t *out_count, const float *grad_out,
                      float *grad_centres, unsigned *err, int num_sms, long long polls,
-                     cudaStream_t s);
+                     cudaStream_t s, unsigned *gflags = nullptr);
 cudaError_t run_wait_selftest(long long polls, unsigned *err, cudaStream_t s);
 void launch_export(const SceneDev &sc, float *pos, float *cov, int32_t *index, cudaStream_t s);
 
@@ -167,7 +167,7 @@ cs_status check_params(const cs_params &p) {
     if (!(p.eps > 0.f && p.eps < 1.f)) return invalid("eps must lie in (0, 1)");
     if (!(p.tau > 0.f) || !isfinite(p.tau)) return invalid("tau must be finite and > 0");
     if (p.k_thr < 0) return invalid("k_thr must be >= 0");
-    if (p.mode < 0 || p.mode > 3) return invalid("mode must be a cs_metric_mode");
+    if (p.mode < 0 || p.mode > 4) return invalid("mode must be a cs_metric_mode");
     if (p.group_size < 0) return invalid("group_size must be >= 0");
     if (p.host_io != 0 && p.host_io != 1) return invalid("host_io must be 0 or 1");
     if (p.tile_config != 0 && p.tile_config != CS_TILE_TUNED) {
@@ -295,6 +295,13 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     }
     if (!p.nsigma_per_query && (!(conservatism >= 0.f) || !isfinite(conservatism)))
         return invalid("conservatism (n_sigma) must be finite and >= 0");
+    const bool flags = p.mode == CS_METRIC_FLAGS;
+    if (flags && grad) return invalid("the flags mode has no gradient");
+    if (flags) {  // only collision flags are computed
+        out_metric = nullptr;
+        p.out_count = nullptr;
+        p.out_group_metric = nullptr;
+    }
     if (Q == 0) return CS_OK;
     if (!prims) return invalid("prims is NULL");
     const bool has_group = p.group_size > 0 && (p.out_group_metric || p.out_group_collide);
@@ -355,9 +362,14 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     uint32_t *perm = nullptr;
     launch_prep(d_prims, prim_type, (int)Q, sc->dev, conservatism, d_ns, *ws, &perm, stream);
     CS_CUDA(cudaGetLastError());
+    unsigned *gflags = nullptr;  // flags mode: a row of the group collides (early exit of the others)
+    if (flags && p.group_size > 0) {
+        gflags = reinterpret_cast<unsigned *>(ws->io_metric);
+        CS_CUDA(cudaMemsetAsync(gflags, 0, 4 * (size_t)ng, stream));
+    }
     CS_CUDA(run_eval(prim_type, sc->dev, ws->qrec, ws->qns, perm, (int)Q, p, grad ? nullptr : d_metric,
                      grad ? nullptr : d_col, grad ? nullptr : d_cnt, d_gout, grad ? d_grad : nullptr,
-                     ws->err, sc->num_sms, kWaitPolls, stream));
+                     ws->err, sc->num_sms, kWaitPolls, stream, gflags));
     if (!grad && has_group) {
         launch_group(d_metric, d_col, (int)Q, p.group_size, d_gm, d_gc, stream);
         CS_CUDA(cudaGetLastError());

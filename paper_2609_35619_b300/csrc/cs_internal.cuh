@@ -224,6 +224,7 @@ __device__ __forceinline__ void group_rows_warp(const float *__restrict__ metric
         s += __shfl_xor_sync(0xffffffffu, s, o);
         c |= __shfl_xor_sync(0xffffffffu, c, o);
     }
+    c = c != 0u;  // a group collides if a row does (rows may hold 2: unfinished, group colliding)
 }
 __device__ __forceinline__ void group_rows_serial(const float *__restrict__ metric,
                                                   const uint8_t *__restrict__ collide, int b, int e,
@@ -234,6 +235,7 @@ __device__ __forceinline__ void group_rows_serial(const float *__restrict__ metr
         if (metric) s += metric[j];
         if (collide) c |= collide[j];
     }
+    c = c != 0u;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {

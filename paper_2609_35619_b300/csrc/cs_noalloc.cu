@@ -32,7 +32,7 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
                      const uint32_t *perm, int Q, const cs_params &p, float *out_metric,
                      uint8_t *out_collide, int32_t *out_count, const float *grad_out,
                      float *grad_centres, unsigned *err, int num_sms, long long polls,
-                     cudaStream_t s);
+                     cudaStream_t s, unsigned *gflags = nullptr);
 
 namespace {
 

@@ -16,6 +16,7 @@
 //                   sphere cost reductions) against the primitives that reach
 //                   it, with per-lane reductions reduced across lanes at the
 //                   end by fixed shuffle trees.
+#include <float.h>
 #include <math.h>
 
 #include <algorithm>
@@ -57,6 +58,7 @@ struct EvalArgs {
     unsigned long long *stats;
     unsigned long long *kstats;  // optional kernel counters (see cs_params.out_kernel_stats)
     long long wait_polls;
+    unsigned *gflags;        // flags mode with groups: per group, set once a row of it collides
 };
 
 // Kernel shape: NCW consumer warps, each owning QW primitives of the tile,
@@ -103,7 +105,8 @@ struct __align__(16) EvalSmem {
     SlotMeta meta[C::NS][C::CHB];
     int count[C::NS];
     int abort;  // an earlier launch on this stream timed out: skip the work
-    int pad[3];
+    int active; // flags mode: consumer warps with an unsettled primitive
+    int pad[2];
     uint64_t full[C::NS];
     uint64_t empty[C::NS];
     float4 q[C::NCW * C::QW][kQRec];
@@ -179,6 +182,8 @@ struct Producer {
     int k = 0;       // stage sequence number
     int nslot = 0;   // chunk slots filled in the open stage
     bool failed = false;
+    bool early = false;   // flags mode: stop staging once every consumer warp is settled
+    bool halted = false;
     int lane;
     unsigned long long n_chunks = 0, n_polls = 0, n_wait_cycles = 0, t_first = 0;
     long long t0 = 0;
@@ -214,7 +219,8 @@ struct Producer {
     // Stage chunks [c, c + len) (contiguous blocks); slot metadata carries
     // each chunk's index and its number of real slots.
     __device__ void emit_run(int c, int len) {
-        while (len > 0 && !failed) {
+        if (early && !halted) halted = __shfl_sync(0xffffffffu, *(volatile int *)&sm->active == 0, 0);
+        while (len > 0 && !failed && !halted) {
             const int st = k % C::NS;
             const int take = min(len, C::CHB - nslot);
             if (lane < take) {
@@ -261,21 +267,21 @@ struct Producer {
     // consecutive passing chunks are one bulk copy each).
     __device__ void descend() {
         const int n3 = sc->nnodes[2], n2 = sc->nnodes[1], n1 = sc->nnodes[0], nc = sc->nchunks;
-        for (int b3 = 0; b3 < n3 && !failed; b3 += 32) {
+        for (int b3 = 0; b3 < n3 && !failed && !halted; b3 += 32) {
             unsigned m3 = test32(sc->nodes[2], b3, n3);
-            while (m3 && !failed) {
+            while (m3 && !failed && !halted) {
                 const int i3 = b3 + __ffs(m3) - 1;
                 m3 &= m3 - 1;
                 unsigned m2 = test32(sc->nodes[1], 32 * i3, n2);
-                while (m2 && !failed) {
+                while (m2 && !failed && !halted) {
                     const int i2 = 32 * i3 + __ffs(m2) - 1;
                     m2 &= m2 - 1;
                     unsigned m1 = test32(sc->nodes[0], 32 * i2, n1);
-                    while (m1 && !failed) {
+                    while (m1 && !failed && !halted) {
                         const int i1 = 32 * i2 + __ffs(m1) - 1;
                         m1 &= m1 - 1;
                         unsigned mc = test32(sc->chead, 32 * i1, nc);
-                        while (mc && !failed) {
+                        while (mc && !failed && !halted) {
                             const int first = __ffs(mc) - 1;
                             const unsigned rest = ~(mc >> first);
                             const int len = rest ? __ffs(rest) - 1 : 32 - first;
@@ -317,7 +323,7 @@ struct Producer {
 };
 
 template <int PRIM, class C>
-__device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile) {
+__device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool early) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int TQ = C::NCW * C::QW;
     const int lane = threadIdx.x & 31;
@@ -375,6 +381,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile) {
         be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
     }
     Producer<C> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
+    pr.early = early;
     pr.lane = lane;
     pr.t0 = t_start;
     const bool any = lx <= hx;  // at least one valid primitive
@@ -396,7 +403,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile) {
 }
 
 // ------------------------------------------------------------- consumers
-// MODE: 0 = cost (mean/sum), 1 = min, 2 = softmin.
+// MODE: 0 = cost (mean/sum), 1 = min, 2 = softmin, 3 = collision flags only.
 // A consumer warp owns QW primitives.  Lane l takes Gaussian l of every
 // staged chunk (global sorted index 32c + l), so each lane's partial
 // reductions run over a fixed subsequence of the scene in increasing order,
@@ -410,7 +417,7 @@ struct Acc {
     float sm_m[(MODE == 2) ? QW : 1];
     float sm_acc[(MODE == 2) ? QW : 1];
     float gx[GRAD ? QW : 1], gy[GRAD ? QW : 1], gz[GRAD ? QW : 1];
-    int cnt[QW];
+    int cnt[MODE == 3 ? 1 : QW];
     int cin[GRAD ? 1 : QW];
 };
 
@@ -473,60 +480,69 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
     // Eq. 8: st2 = max(0, s^2 - n sqrt(sigma^2)); for a sphere s^2 and
     // sqrt(sigma^2) = 2 sqrt(d^T Sigma d)/r^2 share the factor 1/r^2.
     const float raw = fmaf(-ns2, sq, s2);
-    const float st2 = fmaxf(raw, 0.f) * ir2;
-    // Eq. 11 without d_max (applied once per primitive): 2^min(-G (st2 - s_min), 0)
-    const float dc = ex2_approx(fminf(fmaf(st2, -k.G, k.Gsmin), 0.f));
-    const bool nb = st2 <= k.S_cut;
-    A.cnt[j] += nb ? 1 : 0;
-    if (!GRAD) {
+    // Eq. 8 clamp.  For an ellipsoid with a large A, d^T A d of a padding
+    // point (at 1e18) overflows: a first product of either sign becomes +-inf
+    // (or NaN), which the clamp would turn into 0, a colliding neighbour.
+    // d^T A d >= 0, so a non-finite value can only be an overflow: it counts
+    // as +inf (beyond every threshold), and padding still adds nothing.
+    const float st2 = (PRIM == 0 ? fmaxf(raw, 0.f) : (fabsf(raw) <= FLT_MAX ? fmaxf(raw, 0.f) : INFINITY)) * ir2;
+    if constexpr (MODE == 3) {  // flags only: the in-collision count (Section II-E)
         A.cin[j] += (st2 < k.T_in) ? 1 : 0;
-        if (MODE == 0) {
-            if (PRIM == 1) A.sumb[j] += nb ? dc : 0.f;
-            else A.sum[j] += nb ? dc : 0.f;
-        }
-        if (MODE == 1) A.mn[j] = fminf(A.mn[j], st2);
-        if (MODE == 2) {
-            const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
-            const float f = ex2_approx((nm - A.sm_m[j]) * k.K);
-            const float e = nb ? ex2_approx((nm - st2) * k.K) : 0.f;
-            A.sm_acc[j] = fmaf(A.sm_acc[j], f, e);
-            A.sm_m[j] = nm;
-        }
     } else {
-        // d st2 / d c = (-2 w + 2 n A Sigma w / sqrt(w^T Sigma w)) * ir2 where raw > 0
-        float px = vx, py = vy, pz = vz;
-        if (PRIM == 1) {
-            const float axx = qd[1].x, ayy = qd[1].y, azz = qd[1].z, axy = qd[1].w, axz = qd[2].x, ayz = qd[2].y;
-            px = fmaf(axz, vz, fmaf(axy, vy, axx * vx));
-            py = fmaf(ayz, vz, fmaf(ayy, vy, axy * vx));
-            pz = fmaf(azz, vz, fmaf(ayz, vy, axz * vx));
-        }
-        const float rs = ns2 * rsq;
-        const float live = raw > 0.f ? ir2 : 0.f;
-        const float ex = fmaf(rs, px, -2.f * wx) * live;
-        const float ey = fmaf(rs, py, -2.f * wy) * live;
-        const float ez = fmaf(rs, pz, -2.f * wz) * live;
-        if (MODE == 0) {
-            // Eq. 11 is flat (zero gradient) below s_min
-            const float w = (nb && st2 > k.s_min) ? dc : 0.f;
-            A.gx[j] = fmaf(w, ex, A.gx[j]);
-            A.gy[j] = fmaf(w, ey, A.gy[j]);
-            A.gz[j] = fmaf(w, ez, A.gz[j]);
-        } else if (MODE == 1) {
-            const bool take = nb && st2 < A.mn[j];
-            A.mn[j] = take ? st2 : A.mn[j];
-            A.gx[j] = take ? ex : A.gx[j];
-            A.gy[j] = take ? ey : A.gy[j];
-            A.gz[j] = take ? ez : A.gz[j];
+        // Eq. 11 without d_max (applied once per primitive): 2^min(-G (st2 - s_min), 0)
+        const float dc = ex2_approx(fminf(fmaf(st2, -k.G, k.Gsmin), 0.f));
+        const bool nb = st2 <= k.S_cut;
+        A.cnt[j] += nb ? 1 : 0;
+        if (!GRAD) {
+            A.cin[j] += (st2 < k.T_in) ? 1 : 0;
+            if (MODE == 0) {
+                if (PRIM == 1) A.sumb[j] += nb ? dc : 0.f;
+                else A.sum[j] += nb ? dc : 0.f;
+            }
+            if (MODE == 1) A.mn[j] = fminf(A.mn[j], st2);
+            if (MODE == 2) {
+                const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
+                const float f = ex2_approx((nm - A.sm_m[j]) * k.K);
+                const float e = nb ? ex2_approx((nm - st2) * k.K) : 0.f;
+                A.sm_acc[j] = fmaf(A.sm_acc[j], f, e);
+                A.sm_m[j] = nm;
+            }
         } else {
-            const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
-            const float f = ex2_approx((nm - A.sm_m[j]) * k.K);
-            const float e = nb ? ex2_approx((nm - st2) * k.K) : 0.f;
-            A.sm_acc[j] = fmaf(A.sm_acc[j], f, e);
-            A.gx[j] = fmaf(A.gx[j], f, e * ex);
-            A.gy[j] = fmaf(A.gy[j], f, e * ey);
-            A.gz[j] = fmaf(A.gz[j], f, e * ez);
-            A.sm_m[j] = nm;
+            // d st2 / d c = (-2 w + 2 n A Sigma w / sqrt(w^T Sigma w)) * ir2 where raw > 0
+            float px = vx, py = vy, pz = vz;
+            if (PRIM == 1) {
+                const float axx = qd[1].x, ayy = qd[1].y, azz = qd[1].z, axy = qd[1].w, axz = qd[2].x, ayz = qd[2].y;
+                px = fmaf(axz, vz, fmaf(axy, vy, axx * vx));
+                py = fmaf(ayz, vz, fmaf(ayy, vy, axy * vx));
+                pz = fmaf(azz, vz, fmaf(ayz, vy, axz * vx));
+            }
+            const float rs = ns2 * rsq;
+            const float live = raw > 0.f ? ir2 : 0.f;
+            const float ex = fmaf(rs, px, -2.f * wx) * live;
+            const float ey = fmaf(rs, py, -2.f * wy) * live;
+            const float ez = fmaf(rs, pz, -2.f * wz) * live;
+            if (MODE == 0) {
+                // Eq. 11 is flat (zero gradient) below s_min
+                const float w = (nb && st2 > k.s_min) ? dc : 0.f;
+                A.gx[j] = fmaf(w, ex, A.gx[j]);
+                A.gy[j] = fmaf(w, ey, A.gy[j]);
+                A.gz[j] = fmaf(w, ez, A.gz[j]);
+            } else if (MODE == 1) {
+                const bool take = nb && st2 < A.mn[j];
+                A.mn[j] = take ? st2 : A.mn[j];
+                A.gx[j] = take ? ex : A.gx[j];
+                A.gy[j] = take ? ey : A.gy[j];
+                A.gz[j] = take ? ez : A.gz[j];
+            } else {
+                const float nm = nb ? fminf(A.sm_m[j], st2) : A.sm_m[j];
+                const float f = ex2_approx((nm - A.sm_m[j]) * k.K);
+                const float e = nb ? ex2_approx((nm - st2) * k.K) : 0.f;
+                A.sm_acc[j] = fmaf(A.sm_acc[j], f, e);
+                A.gx[j] = fmaf(A.gx[j], f, e * ex);
+                A.gy[j] = fmaf(A.gy[j], f, e * ey);
+                A.gz[j] = fmaf(A.gz[j], f, e * ez);
+                A.sm_m[j] = nm;
+            }
         }
     }
 }
@@ -716,7 +732,18 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         wq[lane][2] = d2;
         wq[lane][3] = d3;
     }
+    constexpr unsigned QBITS = (1u << QW) - 1u;
+    const unsigned wvalid = __ballot_sync(0xffffffffu, nvalid != 0) & QBITS;  // bit j: primitive j is valid
     nvalid = __reduce_add_sync(0xffffffffu, nvalid);
+    // flags mode: primitives still open (bit j), those settled by their group,
+    // and lane j's group index (-1: no group)
+    unsigned wlive = wvalid, wgset = 0u;
+    int mygrp = -1;
+    if (MODE == 3 && a.gflags && k.group_size > 0 && lane < QW && ((wvalid >> lane) & 1u)) {
+        const int q = tile * TQ + C::row(warp, lane);
+        mygrp = (int)(a.perm[q] / (uint32_t)k.group_size);
+    }
+    if (MODE == 3 && wlive == 0u && lane == 0) atomicSub(&sm->active, 1);
     __syncwarp();
     float4(*wqd)[3] = &sm->qd[warp * QW];
     if (PRIM == 0 && lane < QW) {
@@ -755,7 +782,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     Acc<PRIM, QW, MODE, GRAD> A;
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
-        A.cnt[j] = 0;
+        if constexpr (MODE != 3) A.cnt[j] = 0;
         if (!GRAD) A.cin[j] = 0;
         if (MODE == 0 && !GRAD) { A.sum[j] = 0.f; if (PRIM == 1) A.sumb[j] = 0.f; }
         if (MODE == 1) A.mn[j] = INFINITY;
@@ -786,7 +813,39 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if (nslots == 0) break;
         ++c_stages;
         c_tested += (unsigned long long)nslots;
-        if (nvalid > 0) {
+        if constexpr (MODE == 3) {
+            // settle primitives whose in-count already exceeds k_thr (their
+            // flag cannot change) or whose group already collides
+            if (wlive) {
+                unsigned still = wlive;
+#pragma unroll
+                for (int j = 0; j < QW; ++j) {
+                    if ((wlive >> j) & 1u) {
+                        const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
+                        const int g = __shfl_sync(0xffffffffu, mygrp, j);
+                        const bool own = tot > k.k_thr;
+                        bool grp = false;
+                        if (own) {
+                            if (lane == 0 && g >= 0) atomicOr(&a.gflags[g], 1u);
+                        } else if (g >= 0) {
+                            grp = __shfl_sync(0xffffffffu, *(volatile unsigned *)&a.gflags[g] != 0u, 0);
+                        }
+                        if (own || grp) still &= ~(1u << j);
+                        if (grp) wgset |= 1u << j;
+                    }
+                }
+                if (still != wlive) {
+                    if (lane < QW && (((wlive & ~still) >> lane) & 1u)) {
+                        if (PRIM == 0) wq[lane][1].w = 0.f;  // the live flag the reach tests read
+                        else wq[lane][3].x = 0.f;
+                    }
+                    __syncwarp();
+                    wlive = still;
+                    if (wlive == 0u && lane == 0) atomicSub(&sm->active, 1);
+                }
+            }
+        }
+        if ((MODE == 3) ? (wlive != 0u) : (nvalid > 0)) {
             // lane t tests chunk slot t against the warp's box + reach
             bool wpass = false;
             if (lane < nslots) {
@@ -860,7 +919,16 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
         const int q = tile * TQ + C::row(warp, j);
-        const bool vq = wq[j][PRIM == 0 ? 1 : 3].w != 0.f || (PRIM == 1 && wq[j][3].x != 0.f);
+        const bool vq = (wvalid >> j) & 1u;
+        if constexpr (MODE == 3) {
+            // 1: in collision; 0: free; 2: not finished because its group collides
+            const int cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
+            if (lane == 0 && q < a.Q && a.out_collide) {
+                const uint32_t row = a.perm[q];
+                a.out_collide[row] = (vq && ok) ? (cinj > k.k_thr ? 1 : ((wgset >> j) & 1u) ? 2 : 0) : 0;
+            }
+            continue;
+        } else {
         const int cntj = __reduce_add_sync(0xffffffffu, (unsigned)A.cnt[j]);
         if (!GRAD) {
             const int cinj = __reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
@@ -918,6 +986,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             }
         }
         if (vq) nb_total += (unsigned long long)cntj;
+        }  // MODE != 3
     }
     if (a.stats && lane == 0) {
         atomicAdd(a.stats + 0, (unsigned long long)cand);
@@ -949,12 +1018,13 @@ __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalA
         }
         fence_mbar_init();
         sm->abort = (*(volatile unsigned *)a.err & kErrTimeout) ? 1 : 0;
+        sm->active = C::NCW;
     }
     __syncthreads();
     const int tile = blockIdx.x;
     const bool abort = sm->abort != 0;
     if (warp == C::NCW) {
-        if (!abort) producer_warp<PRIM, C>(a, sm, tile);
+        if (!abort) producer_warp<PRIM, C>(a, sm, tile, MODE == 3);
     } else {
         consumer_warp<PRIM, C, MODE, GRAD>(a, sm, tile, warp, abort);
     }
@@ -1202,6 +1272,10 @@ static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
 
 template <int PRIM, class C>
 static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
+    if (a.k.mode == CS_METRIC_FLAGS) {  // one small and one large shape serve the flags mode
+        if (a.Q <= kSmallBatchQ) return launch_eval_t<PRIM, Cfg23, 3, false>(a, s);
+        return launch_eval_t<PRIM, Cfg18, 3, false>(a, s);
+    }
     const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
     if (mode == 0) return launch_eval_t<PRIM, C, 0, false>(a, s);
     if (mode == 1) return launch_eval_t<PRIM, C, 1, false>(a, s);
@@ -1266,7 +1340,7 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
                      const uint32_t *perm, int Q, const cs_params &p, float *out_metric,
                      uint8_t *out_collide, int32_t *out_count, const float *grad_out,
                      float *grad_centres, unsigned *err, int num_sms, long long polls,
-                     cudaStream_t s) {
+                     cudaStream_t s, unsigned *gflags) {
     EvalArgs a;
     a.sc = sc;
     a.qrec = qrec;
@@ -1283,6 +1357,7 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
     a.stats = p.out_pair_stats;
     a.kstats = p.out_kernel_stats;
     a.wait_polls = polls;
+    a.gflags = gflags;
     cudaError_t e;
     if (p.eval_events[0] && (e = cudaEventRecord((cudaEvent_t)p.eval_events[0], s)) != cudaSuccess) return e;
     e = launch_eval(prim_type, a, grad_centres != nullptr, p.tile_config, num_sms, s);

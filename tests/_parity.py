@@ -14,6 +14,12 @@ metric/count checks; queries with a pair inside the collision band
 whose Eq. 8 terms cancel strongly (cond = max over N_j of s^2 + n sqrt(sigma^2)
 above 50) are held to the derived bound 1e-5 + 16 u gamma cond instead.  Every
 exclusion is counted and returned.
+
+Thin ellipsoids: evaluating s^2 = d^T (A d) in FP32 with A = R P R^T rounds with
+an error up to 8 u d^T|A|d <= 24 u kappa s^2, kappa = (a_max / a_min)^2 the
+condition number of A, so a caller passing kappa per row gets the bound
+24 u kappa cond (times gamma |metric| for the cost modes) added, and should
+widen the oracle's bands by the same amount (oracle.Params.band).
 """
 import numpy as np
 
@@ -22,7 +28,7 @@ REL = 1e-5
 COND_STRICT = 50.0
 
 
-def compare(gpu: dict, orc: dict, mode: int, params, label: str = "", check_count=True):
+def compare(gpu: dict, orc: dict, mode: int, params, label: str = "", check_count=True, kappa=None):
     import oracle
     metric_o = oracle.metric(orc, mode)
     g_metric = gpu["metric"].astype(np.float64)
@@ -48,6 +54,14 @@ def compare(gpu: dict, orc: dict, mode: int, params, label: str = "", check_coun
         tol = REL * np.abs(o) + 8 * U32 * orc["min_cond"][live] + 1e-30
     else:
         tol = REL * np.abs(o) + 8 * U32 * orc["cond"][live] + 1e-30
+    if kappa is not None:
+        kap = np.asarray(kappa, np.float64)[live]
+        if mode in (oracle.MODE_MEAN, oracle.MODE_SUM):
+            tol = tol + 24 * U32 * kap * params.gamma * orc["cond"][live] * np.abs(o)
+        elif mode == oracle.MODE_MIN:
+            tol = tol + 24 * U32 * kap * orc["min_cond"][live]
+        else:
+            tol = tol + 24 * U32 * kap * orc["cond"][live]
     err = np.abs(g - o)
     bad = err > tol
     assert not bad.any(), (

@@ -76,16 +76,27 @@ def test_per_query_nsigma_and_k_thr(cs):
         compare(out, orc, 0, oracle.Params(), f"per-row n_sigma k_thr={k_thr}")
 
 
+@pytest.mark.parametrize("axes", [(0.03, 0.2), (0.008, 0.06)])
 @pytest.mark.parametrize("mode", [0, 2, 3])
-def test_ellipsoids(cs, mode):
+def test_ellipsoids(cs, mode, axes):
+    """Ellipsoids, including thin ones (semi-axes down to 8 mm: entries of A
+    near 1.6e4, so d^T A d of a chunk's padding point overflows and must not
+    turn into a neighbour)."""
     sc = S.tiny_scene()
     rng = np.random.default_rng(4)
     centres = rng.uniform(0, 2, (600, 3))
-    e = S.ellipsoid_queries(5, centres)
+    e = S.ellipsoid_queries(5, centres, semi_lo=axes[0], semi_hi=axes[1])
+    kappa = (e[:, 7:10].max(1) / e[:, 7:10].min(1)).astype(np.float64) ** 2
+    # the FP32 rounding of d^T A d (24 u kappa cond) widens the bands in which a
+    # neighbour or collision decision may flip
+    cond = oracle.query(sc, e, 1, 1.0)["cond"]
+    band = max(1e-5, 24 * 2.0 ** -24 * kappa.max() * max(cond.max(), 4.0))
+    orc = oracle.query(sc, e, 1, 1.0, oracle.Params(band=band))
     scene = _scene(cs, sc)
-    for cfg in (1, 2, 3, 4):
+    for cfg in (1, 2, 3, 4, 18, 23):
         out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode, tile_config=cfg)
-        compare(out, oracle.query(sc, e, 1, 1.0), mode, oracle.Params(), f"ellipsoid mode={mode}")
+        rep = compare(out, orc, mode, oracle.Params(), f"ellipsoid mode={mode}", kappa=kappa)
+        assert rep["checked"] > 0.5 * rep["Q"], rep
 
 
 def test_nondefault_metric_parameters(cs):
@@ -329,3 +340,46 @@ def _tabletop_data():
     _TABLE["queries"] = np.concatenate([S.arm_queries(), S.edge_queries()])
     yield
     _TABLE.clear()
+
+
+# ------------------------------------------------------ flags-only mode
+@pytest.mark.parametrize("k_thr", [0, 3])
+@pytest.mark.parametrize("prim_type", [0, 1])
+def test_flags_mode_matches_full_evaluation_and_oracle(cs, k_thr, prim_type):
+    """Flags mode (early exit): finished rows carry the same flag as the full
+    evaluation (same FP32 decision), unfinished rows (2) only occur in
+    colliding groups, group flags equal the full evaluation's and the
+    oracle's (outside the collision band)."""
+    sc = S.tiny_scene(n=3000)
+    rng = np.random.default_rng(40 + k_thr)
+    Q, G = 4000, 4
+    c = rng.uniform(0, 2, (Q, 3))
+    prims = (np.c_[c, rng.uniform(0.02, 0.06, Q)] if prim_type == 0
+             else S.ellipsoid_queries(41, c, semi_lo=0.02, semi_hi=0.06)).astype(np.float32)
+    scene = _scene(cs, sc)
+    full = scene.query(torch.as_tensor(prims), 1.0, prim_type=prim_type,
+                       params=cs.QueryParams(k_thr=k_thr, group_size=G))
+    fl = scene.query(torch.as_tensor(prims), 1.0, prim_type=prim_type,
+                     params=cs.QueryParams(k_thr=k_thr, group_size=G, mode=cs.CS_METRIC_FLAGS))
+    torch.cuda.synchronize()
+    f_row, g_row = fl["collide"].cpu().numpy(), full["collide"].cpu().numpy()
+    done = f_row != 2
+    np.testing.assert_array_equal(f_row[done], g_row[done])
+    gf, gg = fl["group_collide"].cpu().numpy(), full["group_collide"].cpu().numpy()
+    np.testing.assert_array_equal(gf, gg)
+    assert (gg[np.flatnonzero(~done) // G] == 1).all(), "unfinished rows only in colliding groups"
+    assert (~done).sum() > 0 and gg.sum() > 0 and (gg == 0).sum() > 0
+    orc = oracle.query(sc, prims, prim_type, 1.0, oracle.Params(k_thr=k_thr))
+    og = oracle.group_reduce(orc["mean_cost"], orc["collide"], G)[1]
+    band = oracle.group_reduce(orc["mean_cost"], orc["band_in"] > 0, G)[1].astype(bool)
+    np.testing.assert_array_equal(gf[~band], og[~band])
+
+
+def test_flags_mode_without_groups_equals_full_flags(cs):
+    sc = S.drone_scene(n=200_000)
+    q = S.drone_queries(rollouts=512, horizon=32)
+    scene = _scene(cs, sc)
+    full = scene.query(torch.as_tensor(q), 1.0)
+    fl = scene.query(torch.as_tensor(q), 1.0, params=cs.QueryParams(mode=cs.CS_METRIC_FLAGS))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(fl["collide"].cpu().numpy(), full["collide"].cpu().numpy())
