@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=3, help="server batch slots in --case serve")
     ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
     ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
-    ap.add_argument("--case", default="step", choices=["step", "eval", "serve", "mppi"],
+    ap.add_argument("--case", default="step", choices=["step", "eval", "serve", "mppi", "rrt"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
                          "(two fused-kernel launches); prints a short JSON summary. "
@@ -328,6 +328,7 @@ def run_ours(args, rank, world):
     if not args.no_serve and world == 1:
         result["served"] = run_served(torch, cs, dev, args.serve_requests)
         result["mppi"] = run_mppi(torch, cs, dev)
+        result["rrt"] = run_rrt(torch, cs, dev)
     return result
 
 
@@ -619,6 +620,51 @@ def run_mppi(torch, cs, dev, iters=20, K=1024, T=32, with_oracle=False):
     return res
 
 
+RRT_WORKLOAD = ("drone room 500k Gaussians; batched RRT extensions of 32 samples, 8 checked points per edge, "
+                "sphere r = 0.05 m, step 0.3 m, n_sigma 1")
+
+
+def run_rrt(torch, cs, dev, iters=200, B=32, M=8):
+    """Batched RRT from the room centre: `iters` extensions (nearest, steer,
+    flags-mode edge check with early exit, insertion), timed with CUDA events
+    back to back, samples resident on the device."""
+    import cs_synth as S
+    sc = S.drone_scene()
+    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    rng = np.random.default_rng(1010)
+    samples = torch.as_tensor(rng.uniform([0.1, 0.1, 0.1], [5.9, 4.9, 2.9], (iters + 5, B, 3)).astype(np.float32),
+                              device=dev)
+    tree = cs.RrtTree(scene, [3.0, 2.5, 1.5], capacity=1 << 16, step=0.3, radius=0.05, nsigma=1.0, M=M)
+    for i in range(5):
+        tree.extend(samples[i])
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = int(tree.count.item())
+    l0 = cs.abi.cs_launch_count()
+    e0.record()
+    for i in range(iters):
+        tree.extend(samples[5 + i])
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / iters
+    n1 = int(tree.count.item())
+    res = {"workload": RRT_WORKLOAD, "B": B, "M": M, "extensions": iters, "ms_per_extension": ms,
+           "edges_per_s": B * 1e3 / ms, "points_per_s": B * M * 1e3 / ms,
+           "kernels_per_extension": (cs.abi.cs_launch_count() - l0) / iters,
+           "nodes_before": n0, "nodes_after": n1, "free_frac": (n1 - n0) / (B * iters)}
+    scene.close()
+    return res
+
+
+def run_rrt_case(args):
+    import torch
+
+    import paper_2609_35619_b300 as cs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"case": "rrt", **run_rrt(torch, cs, dev)}))
+
+
 def run_mppi_case(args):
     import torch
 
@@ -743,6 +789,9 @@ def main():
         return
     if args.case == "mppi":
         run_mppi_case(args)
+        return
+    if args.case == "rrt":
+        run_rrt_case(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

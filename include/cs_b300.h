@@ -368,6 +368,47 @@ CS_API cs_status cs_mppi_graph_create(const cs_scene *scene, const cs_mppi_desc 
                                       uint8_t *collide, const cs_params *params, cs_graph **out);
 
 /* ------------------------------------------------------------------------
+ * One batched RRT extension (Section II-E) for a robot that is one sphere of
+ * radius `radius`, the tree resident in caller device buffers.  The paper
+ * grows its tree 32 nodes at a time and checks every candidate edge with the
+ * metric; here, for the B samples of one call:
+ *   1. nearest: the closest of nodes[0, *count) to each sample (squared
+ *      distance in FP32, the lowest index on ties);
+ *   2. steer: the new node is the sample when it lies within `step`, else
+ *      the point `step` away from the nearest node towards it;
+ *   3. edge: M points from the nearest node to the new node,
+ *      p_m = x_near + (new - x_near) (m + 1) / M, the last one the new node;
+ *   4. check: the edge collides when one of its points does (more than
+ *      params->k_thr Gaussians with st^2 < 1), evaluated in CS_METRIC_FLAGS
+ *      mode, so an edge stops at its first colliding point;
+ *   5. insert: the new nodes of the free edges are appended in sample order
+ *      at nodes[*count ..] with parent = their nearest node, while
+ *      `capacity` lasts, and *count advances.
+ * Steps 1-3 use correctly rounded FP32 operations in that order (no fused
+ * multiply-add), so they are exactly reproducible. */
+typedef struct cs_rrt_desc {
+    int32_t B;          /* samples per extension, 1 .. 1024 */
+    int32_t M;          /* checked points per edge, 2 .. 1024 (B * M <= 2^20) */
+    float step;         /* longest edge, > 0 */
+    float radius;       /* robot sphere radius, > 0 */
+    float nsigma;       /* conservatism n_sigma, >= 0 */
+    int32_t capacity;   /* node capacity of nodes / parent, >= 1 */
+} cs_rrt_desc;
+
+/* Device pointers: nodes [capacity,3] and parent [capacity] (the tree, in
+ * and out), count [1] (in and out; the tree needs its root, *count >= 1),
+ * samples [B,3], and optionally nearest [B] (the node each sample extended)
+ * and edge_free [B] (1: the edge is free and its node was offered to the
+ * tree; 0: it collides).  params gives the metric parameters, k_thr, the
+ * stream and the tile shape (NULL = defaults); its mode, group and output
+ * members are ignored and host_io must be 0.  Asynchronous on the stream;
+ * scratch is the stream's pooled query scratch.  Errors: CS_ERR_INVALID_ARG
+ * for bad sizes or NULL buffers, and those of cs_query. */
+CS_API cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *desc, float *nodes, int32_t *parent,
+                               int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
+                               const cs_params *params);
+
+/* ------------------------------------------------------------------------
  * Serving loop.  The paper has no counterpart: this is the runtime that keeps
  * scenes resident and answers collision-query requests of uneven size (one
  * RRT edge to a whole MPPI batch) for many clients.

@@ -15,6 +15,7 @@ the metric runs in the library's CUDA kernels):
   Server(scenes, ...)                          cs_server_* (continuous batching)
   mppi_step(scene, x0, U, eps, ...)            cs_mppi_step (one fused MPPI iteration)
   MppiGraph(scene, x0, U, eps, ...)            cs_mppi_graph_create (the iteration as a CUDA graph)
+  RrtTree(scene, root, ...).extend(samples)    cs_rrt_extend (batched RRT, tree on the device)
 The raw one-to-one binding is `paper_2609_35619_b300.abi`.
 """
 from __future__ import annotations
@@ -26,7 +27,7 @@ from . import abi
 from .abi import (CS_METRIC_FLAGS, CS_METRIC_MEAN_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_SUM_COST,
                   CS_PRIM_ELLIPSOID, CS_PRIM_SPHERE, CsError, check)
 
-__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "mppi_step", "MppiGraph", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
+__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "mppi_step", "MppiGraph", "RrtTree", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
            "CS_PRIM_SPHERE", "CS_PRIM_ELLIPSOID", "CS_METRIC_MEAN_COST", "CS_METRIC_SUM_COST",
            "CS_METRIC_MIN_S2", "CS_METRIC_SOFTMIN_S2", "CS_METRIC_FLAGS", "CsError"]
 
@@ -413,6 +414,41 @@ class MppiGraph:
             self.close()
         except Exception:
             pass
+
+
+class RrtTree:
+    """A tree grown by batched RRT extensions (cs_rrt_extend), held in device
+    tensors: nodes [capacity,3], parent [capacity] (-1 for the root), count."""
+
+    def __init__(self, scene: Scene, root, *, capacity=1 << 16, step=0.5, radius=0.15, nsigma=1.0, M=16,
+                 params: QueryParams | None = None):
+        torch = _torch()
+        dev = scene.device
+        self.scene = scene
+        self.nodes = torch.zeros((capacity, 3), dtype=torch.float32, device=dev)
+        self.nodes[0] = _as_f32(root, dev).reshape(3)
+        self.parent = torch.full((capacity,), -1, dtype=torch.int32, device=dev)
+        self.count = torch.ones(1, dtype=torch.int32, device=dev)
+        self.capacity, self.step, self.radius, self.nsigma, self.M = capacity, step, radius, nsigma, M
+        self.params = params or QueryParams()
+
+    def extend(self, samples, stream=None) -> dict:
+        """One extension with B = len(samples); returns the nearest node and
+        the free flag of each sample's edge (device tensors)."""
+        torch = _torch()
+        s = _as_f32(samples, self.scene.device).reshape(-1, 3)
+        B = s.shape[0]
+        d = abi.cs_rrt_desc()
+        d.B, d.M, d.step, d.radius, d.nsigma, d.capacity = B, self.M, self.step, self.radius, self.nsigma, \
+            self.capacity
+        out = {"nearest": torch.empty(B, dtype=torch.int32, device=s.device),
+               "edge_free": torch.empty(B, dtype=torch.uint8, device=s.device)}
+        p = self.params.to_c()
+        p.stream = abi.stream_handle(stream)
+        check(abi.cs_rrt_extend(self.scene.handle, d, self.nodes, self.parent, self.count, s, out["nearest"],
+                                out["edge_free"], p))
+        out["_samples"] = s
+        return out
 
 
 def _set_events(p, events):

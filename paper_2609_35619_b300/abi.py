@@ -144,6 +144,17 @@ class cs_mppi_desc(ctypes.Structure):
     ]
 
 
+class cs_rrt_desc(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("step", ctypes.c_float),
+        ("radius", ctypes.c_float),
+        ("nsigma", ctypes.c_float),
+        ("capacity", ctypes.c_int32),
+    ]
+
+
 CS_TILE_TUNED = -1
 
 _P = ctypes.c_void_p
@@ -175,6 +186,8 @@ _SIGNATURES = {
                                    _P, ctypes.c_int32]),
     "cs_mppi_step": (ctypes.c_int, [_P, ctypes.POINTER(cs_mppi_desc), _P, _P, _P, _P, _P, _P, _P,
                                     ctypes.POINTER(cs_params)]),
+    "cs_rrt_extend": (ctypes.c_int, [_P, ctypes.POINTER(cs_rrt_desc), _P, _P, _P, _P, _P, _P,
+                                     ctypes.POINTER(cs_params)]),
     "cs_server_config_init": (ctypes.c_int, [ctypes.POINTER(cs_server_config)]),
     "cs_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cs_server_config), ctypes.POINTER(_P)]),
     "cs_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(cs_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -348,6 +361,11 @@ def cs_autotune(scene, prim_type, prims, Q, conservatism, params, reps, best: ct
 def cs_mppi_step(scene, desc: cs_mppi_desc, x0, U, eps, U_out, cost, weights, collide, params) -> int:
     return load().cs_mppi_step(scene, ctypes.byref(desc), ptr(x0), ptr(U), ptr(eps), ptr(U_out), ptr(cost),
                                ptr(weights), ptr(collide), None if params is None else ctypes.byref(params))
+
+
+def cs_rrt_extend(scene, desc: cs_rrt_desc, nodes, parent, count, samples, nearest, edge_free, params) -> int:
+    return load().cs_rrt_extend(scene, ctypes.byref(desc), ptr(nodes), ptr(parent), ptr(count), ptr(samples),
+                                ptr(nearest), ptr(edge_free), None if params is None else ctypes.byref(params))
 
 
 def cs_server_config_init(cfg: cs_server_config) -> int:

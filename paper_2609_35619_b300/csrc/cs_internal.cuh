@@ -109,6 +109,8 @@ struct Workspace {
     // MPPI iteration scratch (cs_mppi_step): sphere centres of the rollouts
     // [K*T,4], then per rollout the collision cost and the task + control cost
     float *mppi = nullptr;           size_t cap_mppi = 0;  // floats
+    // RRT extension scratch (cs_rrt_extend): edge points, nearest, new nodes, edge flags
+    float *rrt = nullptr;            size_t cap_rrt = 0;   // floats
     unsigned *err = nullptr;         // device error word
 };
 

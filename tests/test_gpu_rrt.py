@@ -1,0 +1,89 @@
+"""cs_rrt_extend (batched RRT extension, tree on the device) against the RRT
+oracle, extension by extension from the same tree.
+
+Nearest nodes, new nodes and edge points are computed in FP32 by both sides
+with the same correctly rounded operations, so they must agree bit for bit;
+edge flags must agree exactly except for edges with a point whose pair sits
+in the collision band (|st^2 - 1| <= 1e-5), which are counted; the grown tree
+(nodes, parents, count) must then agree exactly.
+"""
+import numpy as np
+import pytest
+
+import cs_synth as S
+from oracle import rrt as orrt
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cs(cuda_device):
+    import paper_2609_35619_b300 as cs
+    return cs
+
+
+@pytest.fixture(scope="module")
+def room(cs):
+    sc = S.drone_scene(n=200_000)
+    return sc, cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"])
+
+
+@pytest.mark.parametrize("ns,k_thr", [(1.0, 0), (0.0, 3)])
+def test_extensions_match_oracle(cs, room, ns, k_thr):
+    import oracle
+    sc, scene = room
+    d = orrt.RrtDesc(B=32, M=8, step=0.3, radius=0.05, nsigma=ns, capacity=512)
+    # the root: the first of a few seeded points that the oracle finds free
+    cand = np.random.default_rng(11).uniform([0.5, 0.5, 0.5], [5.5, 4.5, 2.5], (64, 3)).astype(np.float32)
+    res = oracle.query(sc, np.c_[cand, np.full(64, d.radius, np.float32)], 0, ns, oracle.Params(k_thr=k_thr))
+    root = cand[np.flatnonzero((res["collide"] == 0) & (res["band_in"] == 0))[0]]
+    tree = cs.RrtTree(scene, root, capacity=d.capacity, step=d.step, radius=d.radius, nsigma=ns,
+                      M=d.M, params=cs.QueryParams(k_thr=k_thr))
+    nodes = np.zeros((d.capacity, 3), np.float32)
+    nodes[0] = root
+    parent = np.full(d.capacity, -1, np.int64)
+    count = 1
+    rng = np.random.default_rng(7 + k_thr)
+    banded = inserted_free = collided = 0
+    for it in range(6):
+        samples = rng.uniform([0.1, 0.1, 0.1], [5.9, 4.9, 2.9], (d.B, 3)).astype(np.float32)
+        out = tree.extend(samples)
+        torch.cuda.synchronize()
+        ref = orrt.extend(sc, nodes, parent, count, samples, d, oracle.Params(k_thr=k_thr))
+        np.testing.assert_array_equal(out["nearest"].cpu().numpy(), ref["nearest"], err_msg=f"it {it}")
+        free = out["edge_free"].cpu().numpy().astype(bool)
+        band = ref["edge_band"]
+        banded += int(band.sum())
+        np.testing.assert_array_equal(free[~band], ref["edge_collide"][~band] == 0, err_msg=f"it {it}")
+        if (free != (ref["edge_collide"] == 0)).any():
+            break  # a band edge went the other way: the trees part here
+        g_nodes = tree.nodes.cpu().numpy()
+        g_parent = tree.parent.cpu().numpy()
+        g_count = int(tree.count.cpu().item())
+        assert g_count == ref["count"], it
+        np.testing.assert_array_equal(g_nodes[:g_count], ref["nodes"][:g_count], err_msg=f"it {it}")
+        np.testing.assert_array_equal(g_parent[:g_count], ref["parent"][:g_count], err_msg=f"it {it}")
+        inserted_free += int(free.sum())
+        collided += int((~free).sum())
+        nodes, parent, count = ref["nodes"], ref["parent"], ref["count"]
+    assert inserted_free > 0 and collided > 0, (inserted_free, collided)
+    assert banded <= 2
+
+
+def test_capacity_and_arguments(cs, room):
+    _, scene = room
+    tree = cs.RrtTree(scene, [3.0, 2.5, 1.5], capacity=5, step=0.2, radius=0.05, nsigma=0.0)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        tree.extend(rng.uniform([2.6, 2.1, 1.1], [3.4, 2.9, 1.9], (8, 3)).astype(np.float32))
+    torch.cuda.synchronize()
+    assert int(tree.count.item()) <= 5
+    par = tree.parent.cpu().numpy()[: int(tree.count.item())]
+    assert par[0] == -1 and (par[1:] >= 0).all() and (par[1:] < np.arange(1, len(par))).all()
+    with pytest.raises(cs.CsError):
+        bad = cs.RrtTree(scene, [3.0, 2.5, 1.5], capacity=5, step=-1.0)
+        bad.extend(np.zeros((2, 3), np.float32))
+    with pytest.raises(cs.CsError):
+        tree.M = 1
+        tree.extend(np.zeros((2, 3), np.float32))
