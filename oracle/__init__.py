@@ -54,6 +54,7 @@ class _Params(ctypes.Structure):
         ("use_filter", ctypes.c_int32),
         ("nthreads", ctypes.c_int32),
         ("band", ctypes.c_double),
+        ("exact_variance", ctypes.c_int32),
     ]
 
 
@@ -79,6 +80,7 @@ class Params:
     use_filter: bool = True
     nthreads: int = 0
     band: float = 1e-5  # width of the reporting bands (band_cut, band_in, band_kink)
+    exact_variance: bool = False  # the exact variance of Eq. 5 instead of Eq. 7's linearisation
 
     @property
     def s_cut(self) -> float:
@@ -87,7 +89,7 @@ class Params:
     def _c(self) -> _Params:
         return _Params(self.gamma, self.d_max, self.s_min, self.eps, self.tau, int(self.k_thr),
                        self.opacity_min, self.extent_max, int(bool(self.use_filter)),
-                       int(self.nthreads), float(self.band))
+                       int(self.nthreads), float(self.band), int(bool(self.exact_variance)))
 
 
 _lib = None

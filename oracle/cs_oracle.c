@@ -54,6 +54,8 @@ typedef struct {
     int32_t use_filter;
     int32_t nthreads;   /* <= 0: OpenMP default */
     double band;        /* width of the reporting bands below (<= 0: 1e-5) */
+    int32_t exact_variance; /* 1: the exact variance of Eq. 5 under the Gaussian instead of
+                               the linearisation of Eq. 7 (adds 2 tr((A Sigma)^2)) */
 } orc_params;
 
 /* Per-query outputs.  Any pointer may be NULL. */
@@ -155,8 +157,22 @@ typedef struct {
     double raw;   /* s2 - n_sigma sqrt(var), before the clamp */
 } pair_terms;
 
+/* tr((A Sigma)^2) = sum_ab (A Sigma)_ab (A Sigma)_ba: for X ~ N(mu, Sigma) the
+ * quadratic form s^2(X) = (X - c)^T A (X - c) has variance
+ * 4 d^T A Sigma A d + 2 tr((A Sigma)^2); Eq. 7 keeps the first term only. */
+static double trace_asas(const double A[3][3], const double Sig[3][3])
+{
+    double M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) M[a][b] = A[a][0] * Sig[0][b] + A[a][1] * Sig[1][b] + A[a][2] * Sig[2][b];
+    double t = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) t += M[a][b] * M[b][a];
+    return t;
+}
+
 static pair_terms evaluate_pair(const double mu[3], const double Sig[3][3], const double c[3],
-                                const double A[3][3], double nsigma)
+                                const double A[3][3], double nsigma, int exact)
 {
     pair_terms t;
     double d[3] = {mu[0] - c[0], mu[1] - c[1], mu[2] - c[2]};
@@ -170,6 +186,7 @@ static pair_terms evaluate_pair(const double mu[3], const double Sig[3][3], cons
     double Sg[3];
     for (int a = 0; a < 3; ++a) Sg[a] = Sig[a][0] * g[0] + Sig[a][1] * g[1] + Sig[a][2] * g[2];
     t.var = g[0] * Sg[0] + g[1] * Sg[1] + g[2] * Sg[2];
+    if (exact) t.var += 2.0 * trace_asas(A, Sig);
     if (t.var < 0.0) t.var = 0.0; /* Sigma is PSD; guards round-off only */
     /* Eq. 8 */
     t.raw = t.s2 - nsigma * sqrt(t.var);
@@ -200,7 +217,7 @@ int orc_pair(const float *mean, const float *scale, const float *quat, int prim_
     gaussian_covariance(scale, quat, Sig);
     if (robot_primitive(prim_type, prim, c, A) != 0) return -1;
     double mu[3] = {mean[0], mean[1], mean[2]};
-    pair_terms t = evaluate_pair(mu, Sig, c, A, nsigma);
+    pair_terms t = evaluate_pair(mu, Sig, c, A, nsigma, prm->exact_variance);
     out[0] = t.s2;
     out[1] = t.var;
     out[2] = t.st2;
@@ -256,7 +273,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
             const double *S = Sig + 9 * i;
             double Sg[3][3] = {{S[0], S[1], S[2]}, {S[3], S[4], S[5]}, {S[6], S[7], S[8]}};
             double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-            pair_terms t = evaluate_pair(mu, Sg, c, A, ns);
+            pair_terms t = evaluate_pair(mu, Sg, c, A, ns, prm->exact_variance);
             if (fabs(t.st2 - S_cut) <= band * S_cut) ++bcut;
             if (fabs(t.st2 - 1.0) <= band) ++bin;
             if (t.st2 <= S_cut * (1.0 + band) &&
@@ -300,7 +317,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
  *   sqrt(sigma^2)          = 2 sqrt(w^T Sigma w)
  *   d sqrt(sigma^2) / d c  = -2 A Sigma w / sqrt(w^T Sigma w)               */
 static void st2_grad(const double mu[3], const double Sig[3][3], const double c[3],
-                     const double A[3][3], double nsigma, double *st2_out, double gvec[3],
+                     const double A[3][3], double nsigma, int exact, double *st2_out, double gvec[3],
                      double *gmag)
 {
     double d[3] = {mu[0] - c[0], mu[1] - c[1], mu[2] - c[2]};
@@ -311,7 +328,9 @@ static void st2_grad(const double mu[3], const double Sig[3][3], const double c[
     for (int a = 0; a < 3; ++a) Sw[a] = Sig[a][0] * w[0] + Sig[a][1] * w[1] + Sig[a][2] * w[2];
     double wSw = w[0] * Sw[0] + w[1] * Sw[1] + w[2] * Sw[2];
     if (wSw < 0.0) wSw = 0.0;
-    double root = sqrt(wSw);
+    /* sqrt(sigma^2) / 2; the exact variance adds tr((A Sigma)^2) / 2 under the
+     * root, a term that does not depend on c */
+    double root = sqrt(wSw + (exact ? 0.5 * trace_asas(A, Sig) : 0.0));
     double raw = s2 - nsigma * 2.0 * root;
     *st2_out = raw > 0.0 ? raw : 0.0;
     for (int a = 0; a < 3; ++a) gvec[a] = 0.0;
@@ -369,7 +388,7 @@ int orc_grad(int64_t n, const float *means, const float *scales, const float *qu
             double Sg[3][3] = {{S[0], S[1], S[2]}, {S[3], S[4], S[5]}, {S[6], S[7], S[8]}};
             double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
             double st2, g[3], gm;
-            st2_grad(mu, Sg, c, A, ns, &st2, g, &gm);
+            st2_grad(mu, Sg, c, A, ns, prm->exact_variance, &st2, g, &gm);
             if (!(st2 <= S_cut)) continue;
             ++cnt;
             if (mode == 0 || mode == 1) {

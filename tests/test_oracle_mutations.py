@@ -23,6 +23,8 @@ MUTATIONS = {
     "grad_sign": ("double p1 = -2.0 * w[a], p2", "double p1 = 2.0 * w[a], p2"),
     "eq6_not_inverse": ("double P[3] = {1.0 / (ax * ax), 1.0 / (bx * bx), 1.0 / (cx * cx)};",
                         "double P[3] = {ax * ax, bx * bx, cx * cx};"),
+    "exact_var_half_trace": ("if (exact) t.var += 2.0 * trace_asas(A, Sig);",
+                             "if (exact) t.var += trace_asas(A, Sig);"),
 }
 
 
@@ -38,6 +40,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            str(mutated), "-lm"])
     env = dict(os.environ, CS_ORACLE_LIB=str(lib))
     proc = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                           os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                           os.path.join(ROOT, "tests", "test_oracle_exact_variance.py")],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert proc.returncode != 0, f"pins did not catch {name}:\n{proc.stdout[-2000:]}"
