@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
     ap.add_argument("--flags", action="store_true", help="--case eval: collision flags only (early exit)")
+    ap.add_argument("--exact", action="store_true",
+                    help="--case eval: exact variance of the quadratic form in Eq. 8 (cs_params.exact_variance)")
     return ap.parse_args()
 
 
@@ -746,7 +748,7 @@ def run_eval_case(args):
     arm = torch.as_tensor(S.arm_queries() if args.batch == "arm" else S.edge_queries(), device=dev)
     scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
     G = 64 if args.batch == "arm" else 1024
-    qp = cs.QueryParams(group_size=G, tile_config=args.tile,
+    qp = cs.QueryParams(group_size=G, tile_config=args.tile, exact_variance=args.exact,
                         mode=cs.CS_METRIC_FLAGS if args.flags else cs.CS_METRIC_MEAN_COST)
     ns = args.nsigma
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
@@ -759,7 +761,7 @@ def run_eval_case(args):
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1])
         print(json.dumps({"case": "eval", "grad": True, "batch": args.batch, "tile": args.tile, "nsigma": ns,
-                          "queries": arm.shape[0], "eval_ms": ms}))
+                          "exact": args.exact, "queries": arm.shape[0], "eval_ms": ms}))
         return
     scene.query(arm, ns, params=qp)
     scene.query(arm, ns, params=qp, pair_stats=stats, eval_events=ev)
@@ -774,7 +776,7 @@ def run_eval_case(args):
              "producer_cycles", "producer_wait_cycles", "consumer_first_cycles", "producer_first_cycles",
              "consumer_tail_cycles", "tiles"]
     print(json.dumps({"case": "eval", "batch": args.batch, "tile": args.tile, "nsigma": ns,
-                      "queries": arm.shape[0], "useful_pairs": useful,
+                      "exact": args.exact, "flags": args.flags, "queries": arm.shape[0], "useful_pairs": useful,
                       "candidate_pairs": cand, "eval_ms": ms,
                       "kernel_stats": dict(zip(names, kstats.cpu().tolist())), "info": scene.info()}))
 

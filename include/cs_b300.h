@@ -155,6 +155,13 @@ typedef struct cs_params {
                                   [13] producer cycles until the first stage was closed,
                                   [14] consumer cycles after the last stage (reductions),
                                   [15] tiles */
+    int32_t exact_variance;    /* 1: sigma^2 of Eq. 8 is the exact variance of the quadratic
+                                  form of Eq. 5 under the Gaussian, 4 d^T A Sigma A d +
+                                  2 tr((A Sigma)^2), instead of Eq. 7's first-order term
+                                  (more conservative: st^2 can only drop).  The forward call
+                                  then runs the default tile shape of its batch size and the
+                                  adjoint its default shape (tile_config is ignored).
+                                  Default 0. */
 } cs_params;
 
 /* Scene information returned by cs_scene_info. */

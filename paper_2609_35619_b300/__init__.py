@@ -44,12 +44,14 @@ class QueryParams:
     mode: int = CS_METRIC_MEAN_COST
     group_size: int = 0
     tile_config: int = 0
+    exact_variance: bool = False
 
     def to_c(self) -> abi.cs_params:
         p = abi.cs_params()
         check(abi.cs_params_init(p))
         p.gamma, p.d_max, p.s_min, p.eps, p.tau = self.gamma, self.d_max, self.s_min, self.eps, self.tau
         p.k_thr, p.mode, p.group_size, p.tile_config = self.k_thr, self.mode, self.group_size, self.tile_config
+        p.exact_variance = 1 if self.exact_variance else 0
         return p
 
 

@@ -60,6 +60,7 @@ class cs_params(ctypes.Structure):
         ("out_pair_stats", ctypes.c_void_p),
         ("eval_events", ctypes.c_void_p * 2),
         ("out_kernel_stats", ctypes.c_void_p),
+        ("exact_variance", ctypes.c_int32),
     ]
 
 

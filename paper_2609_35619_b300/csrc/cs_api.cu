@@ -170,6 +170,7 @@ cs_status check_params(const cs_params &p) {
     if (p.mode < 0 || p.mode > 4) return invalid("mode must be a cs_metric_mode");
     if (p.group_size < 0) return invalid("group_size must be >= 0");
     if (p.host_io != 0 && p.host_io != 1) return invalid("host_io must be 0 or 1");
+    if (p.exact_variance != 0 && p.exact_variance != 1) return invalid("exact_variance must be 0 or 1");
     if (p.tile_config != 0 && p.tile_config != CS_TILE_TUNED) {
         int32_t ids[32];
         int n = tile_configs(ids, 32);
@@ -487,6 +488,6 @@ int64_t cs_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 
 const char *cs_last_error(void) { return g_err.c_str(); }
 
-const char *cs_version(void) { return "cs_b300 0.4 (sm_103a)"; }
+const char *cs_version(void) { return "cs_b300 0.5 (sm_103a)"; }
 
 }  // extern "C"

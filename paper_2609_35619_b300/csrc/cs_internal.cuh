@@ -339,8 +339,20 @@ __device__ __forceinline__ float lg2_approx(float x) {
 // Reach of a cull: every pair whose centre distance exceeds
 // R(sigma) = alpha sigma + sqrt(alpha^2 sigma^2 + beta) has st^2 > S_reach,
 // where (alpha, beta) come from the primitive (see prepare kernels).
+// EX (exact variance of the quadratic form): the trace term adds at most
+// 1.5 sigma^4 (scaled like the rest) under the root of sigma^2, and the
+// condition x^2 - 2 alpha sqrt(sigma^2 x^2 + 1.5 sigma^4) <= beta on the
+// centre distance x solves to
+//   x^2 <= beta + 2 a^2 + 2 a sqrt(beta + a^2 + 1.5 sigma^2),  a = alpha sigma,
+// which reduces to R(sigma)^2 without the 1.5 sigma^2.  Both grow with alpha
+// and beta, so the largest of a group bound the whole group.
+template <bool EX = false>
 __device__ __forceinline__ float reach(float alpha, float beta, float sigma, float pad_abs) {
     float a = alpha * sigma;
+    if constexpr (EX) {
+        const float inner = sqrtf(fmaf(a, a, fmaf(1.5f * sigma, sigma, beta)));
+        return sqrtf(fmaf(2.f * a, a + inner, beta)) * (1.f + kReachPadRel) + pad_abs;
+    }
     return (a + sqrtf(fmaf(a, a, beta))) * (1.f + kReachPadRel) + pad_abs;
 }
 

@@ -40,6 +40,7 @@ struct QueryConsts {
     int k_thr;
     int mode;
     int group_size;
+    int exact;      // sigma^2 is the exact variance of the quadratic form (Eq. 5)
 };
 
 struct EvalArgs {
@@ -129,6 +130,9 @@ template <> struct PrimTraits<1> { static constexpr int RECS = 3; };  // ellipso
 // |d|^2 - 2 n s |d| a_max^2/a_min^2 - S a_max^2 <= 0:
 //   sphere:    alpha = n,                 beta = S r^2
 //   ellipsoid: alpha = n a_max^2/a_min^2, beta = S a_max^2.
+// With the exact variance, tr((A Sigma)^2)/2 <= 1.5 s^4 / a_min^4 joins
+// (s |d| / a_min^2)^2 under the root, which the exact-variance reach takes
+// into account with the same alpha and beta.
 template <int PRIM>
 __device__ __forceinline__ void prim_reach(const float4 *rec, float ns, float S, float &alpha,
                                            float &beta) {
@@ -173,7 +177,7 @@ __device__ __noinline__ long long wait_phase(uint64_t *bar, unsigned parity, lon
 
 
 // ------------------------------------------------------------- producer
-template <class C>
+template <class C, bool EX>
 struct Producer {
     EvalSmem<C> *sm;
     const SceneDev *sc;
@@ -245,12 +249,12 @@ struct Producer {
     // sparse tile (primitives scattered over the scene) stages only what
     // some group of its rows can reach.
     __device__ bool meets(const NodeBox &b) const {
-        const float R = reach(al, be, b.lo.w, sc->pad_abs);
+        const float R = reach<EX>(al, be, b.lo.w, sc->pad_abs);
         if (box_gap2(lx, ly, lz, hx, hy, hz, b.lo, b.hi) > R * R) return false;
 #pragma unroll 1
         for (int k = 0; k < kSub; ++k) {
             const float4 lo = sm->sub[k][0], hi = sm->sub[k][1];
-            const float Rk = reach(lo.w, hi.w, b.lo.w, sc->pad_abs);
+            const float Rk = reach<EX>(lo.w, hi.w, b.lo.w, sc->pad_abs);
             if (box_gap2(lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, b.lo, b.hi) <= Rk * Rk) return true;
         }
         return false;
@@ -322,7 +326,7 @@ struct Producer {
     }
 };
 
-template <int PRIM, class C>
+template <int PRIM, class C, bool EX>
 __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool early) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int TQ = C::NCW * C::QW;
@@ -380,7 +384,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool
         al = fmaxf(al, __shfl_xor_sync(0xffffffffu, al, o));
         be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
     }
-    Producer<C> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
+    Producer<C, EX> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
     pr.early = early;
     pr.lane = lane;
     pr.t0 = t_start;
@@ -421,9 +425,10 @@ struct Acc {
     int cin[GRAD ? 1 : QW];
 };
 
-// Lane-local Gaussian of the current chunk slot.
+// Lane-local Gaussian of the current chunk slot (f: tr(Sigma^2)/2, set for
+// spheres with the exact variance only).
 struct LaneG {
-    float x, y, z, sxx, syy, szz, sxy2, sxz2, syz2;
+    float x, y, z, sxx, syy, szz, sxy2, sxz2, syz2, f;
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -437,7 +442,37 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
-template <int PRIM, int QW, int MODE, bool GRAD>
+// tr((A Sigma)^2) / 2 for an ellipsoid record (A symmetric) and a Gaussian:
+// with P = A Sigma, tr(P P) = sum_i P_ii^2 + 2 sum_{i<j} P_ij P_ji.
+__device__ __forceinline__ float half_tr_asas(const float4 *qd, const LaneG &g) {
+    const float axx = qd[1].x, ayy = qd[1].y, azz = qd[1].z, axy = qd[1].w, axz = qd[2].x, ayz = qd[2].y;
+    const float hxy = 0.5f * g.sxy2, hxz = 0.5f * g.sxz2, hyz = 0.5f * g.syz2;
+    const float p00 = fmaf(axz, hxz, fmaf(axy, hxy, axx * g.sxx));
+    const float p01 = fmaf(axz, hyz, fmaf(axy, g.syy, axx * hxy));
+    const float p02 = fmaf(axz, g.szz, fmaf(axy, hyz, axx * hxz));
+    const float p10 = fmaf(ayz, hxz, fmaf(ayy, hxy, axy * g.sxx));
+    const float p11 = fmaf(ayz, hyz, fmaf(ayy, g.syy, axy * hxy));
+    const float p12 = fmaf(ayz, g.szz, fmaf(ayy, hyz, axy * hxz));
+    const float p20 = fmaf(azz, hxz, fmaf(ayz, hxy, axz * g.sxx));
+    const float p21 = fmaf(azz, hyz, fmaf(ayz, g.syy, axz * hxy));
+    const float p22 = fmaf(azz, g.szz, fmaf(ayz, hyz, axz * hxz));
+    const float diag = fmaf(p22, p22, fmaf(p11, p11, p00 * p00));
+    const float off = fmaf(p12, p21, fmaf(p02, p20, p01 * p10));
+    return fmaf(0.5f, diag, off);
+}
+
+// tr(Sigma^2)/2 of a Gaussian from its doubled off-diagonals (the exact
+// variance's trace term for a sphere, before the 1/r^2 scaling).
+__device__ __forceinline__ float half_tr_ss(const LaneG &g) {
+    return fmaf(0.25f, fmaf(g.syz2, g.syz2, fmaf(g.sxz2, g.sxz2, g.sxy2 * g.sxy2)),
+                0.5f * fmaf(g.szz, g.szz, fmaf(g.syy, g.syy, g.sxx * g.sxx)));
+}
+
+// One (primitive, Gaussian) pair.  EX: sigma^2 is the exact variance of the
+// quadratic form, 4 w^T Sigma w + 2 tr((A Sigma)^2), i.e. u + tr((A Sigma)^2)/2
+// under the root (for a sphere A = I / r^2 and the trace term is the lane's
+// g.f = tr(Sigma^2)/2, scaled by 1/r^2 with the rest).
+template <int PRIM, int QW, int MODE, bool GRAD, bool EX = false>
 __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j, const LaneG &g,
                                             const float4 *qd, const QueryConsts &k) {
     const float dx = g.x - qd[0].x, dy = g.y - qd[0].y, dz = g.z - qd[0].z;
@@ -457,17 +492,19 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
         wz = fmaf(azz, dz, fmaf(ayz, dy, axz * dx));
         s2 = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
     }
+    float F = 0.f;  // EX: the trace term, added first (the packed path does the same)
+    if constexpr (EX) F = (PRIM == 0) ? g.f : half_tr_asas(qd, g);
     if (!GRAD) {
         // w^T Sigma w with the doubled off-diagonals: 9 FP32 ops
         const float t1 = fmaf(g.sxz2, wz, fmaf(g.sxy2, wy, g.sxx * wx));
         const float t2 = fmaf(g.syz2, wz, g.syy * wy);
-        u = fmaf(wx, t1, fmaf(wy, t2, wz * (g.szz * wz)));
+        u = fmaf(wx, t1, fmaf(wy, t2, EX ? fmaf(wz, g.szz * wz, F) : wz * (g.szz * wz)));
     } else {
         const float hxy = 0.5f * g.sxy2, hxz = 0.5f * g.sxz2, hyz = 0.5f * g.syz2;
         vx = fmaf(hxz, wz, fmaf(hxy, wy, g.sxx * wx));  // Sigma w
         vy = fmaf(hyz, wz, fmaf(g.syy, wy, hxy * wx));
         vz = fmaf(g.szz, wz, fmaf(hyz, wy, hxz * wx));
-        u = fmaf(wx, vx, fmaf(wy, vy, wz * vz));
+        u = fmaf(wx, vx, fmaf(wy, vy, EX ? fmaf(wz, vz, F) : wz * vz));
     }
     u = fmaxf(u, 0.f);
     float sq, rsq = 0.f;
@@ -549,7 +586,7 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
 
 // Does the primitive (shared-memory record) reach the chunk (bounding box,
 // largest scale)?  Dead slots never do.  The same answer on every lane.
-template <int PRIM>
+template <int PRIM, bool EX>
 __device__ __forceinline__ bool reaches(const float4 *qd, const float4 &blo, const float4 &bhi,
                                         float pad_abs) {
     const float4 q0 = qd[0];
@@ -561,13 +598,13 @@ __device__ __forceinline__ bool reaches(const float4 *qd, const float4 &blo, con
         const float4 q2 = qd[2];
         alpha = q2.z; beta = q2.w; live = qd[3].x;
     }
-    const float R = reach(alpha, beta, blo.w, pad_abs);
+    const float R = reach<EX>(alpha, beta, blo.w, pad_abs);
     return live != 0.f && box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) <= R * R;
 }
 
 // Lane-local Gaussian duplicated into both halves of packed registers.
 struct LaneG2 {
-    f32x2 x, y, z, sxx, syy, szz, sxy2, sxz2, syz2;
+    f32x2 x, y, z, sxx, syy, szz, sxy2, sxz2, syz2, f;
 };
 
 // One sphere (cost reductions, forward) against the lane's two Gaussians
@@ -575,7 +612,7 @@ struct LaneG2 {
 // the Eq. 11 exponent in packed FP32x2: the same operations in the same
 // order as pair_update, hence the same bits; half 0 is accumulated before
 // half 1, so each lane still adds its Gaussians in increasing order.
-template <int QW>
+template <int QW, bool EX>
 __device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, const LaneG2 &g,
                                                const float4 *qd, const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
     const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&qd[0]);  // -cx, -cy
@@ -585,7 +622,8 @@ __device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, c
     const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     const f32x2 t1 = fma2(g.sxz2, dz, fma2(g.sxy2, dy, mul2(g.sxx, dx)));
     const f32x2 t2 = fma2(g.syz2, dz, mul2(g.syy, dy));
-    const f32x2 u = fma2(dx, t1, fma2(dy, t2, mul2(dz, mul2(g.szz, dz))));
+    const f32x2 zz = mul2(g.szz, dz);
+    const f32x2 u = fma2(dx, t1, fma2(dy, t2, EX ? fma2(dz, zz, g.f) : mul2(dz, zz)));
     float u0, u1;
     upk2(u, u0, u1);
     const f32x2 sq = pk2(sqrt_approx(fmaxf(u0, 0.f)), sqrt_approx(fmaxf(u1, 0.f)));
@@ -622,7 +660,7 @@ __device__ __forceinline__ void lane_gaussian(const ChunkBlock &B, const SlotMet
 // `qmask` (the primitives reaching either chunk): lane l holds Gaussian l of
 // each chunk in the two halves of packed registers; spheres are evaluated in
 // groups of GROUP (a member reaching neither chunk adds exactly nothing).
-template <int QW, int GROUP>
+template <int QW, int GROUP, bool EX>
 __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, const SlotMeta mt0,
                                                 const ChunkBlock &B1, const SlotMeta mt1, unsigned qmask,
                                                 float4 (*wqd)[3], const QueryConsts &k, int lane,
@@ -635,6 +673,7 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
     g2.x = pk2(g0.x, g1.x); g2.y = pk2(g0.y, g1.y); g2.z = pk2(g0.z, g1.z);
     g2.sxx = pk2(g0.sxx, g1.sxx); g2.syy = pk2(g0.syy, g1.syy); g2.szz = pk2(g0.szz, g1.szz);
     g2.sxy2 = pk2(g0.sxy2, g1.sxy2); g2.sxz2 = pk2(g0.sxz2, g1.sxz2); g2.syz2 = pk2(g0.syz2, g1.syz2);
+    if constexpr (EX) g2.f = pk2(half_tr_ss(g0), half_tr_ss(g1));
     const f32x2 nG2 = pk2(-k.G, -k.G), Gs2 = pk2(k.Gsmin, k.Gsmin);
     // bit j0 of gm: group j0 .. j0 + GROUP - 1 has a member reaching a chunk
     unsigned gm = qmask;
@@ -650,7 +689,7 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
         if ((gm >> j0) & 1u) {
 #pragma unroll
-            for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW>(A, j, g2, wqd[j], k, nG2, Gs2);
+            for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW, EX>(A, j, g2, wqd[j], k, nG2, Gs2);
         }
     }
 }
@@ -658,7 +697,7 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 // One staged chunk against the primitives of `qmask`: lane l takes Gaussian
 // l of the chunk (lanes outside the staged range hold a point that meets no
 // primitive), then the primitives are evaluated two per basic block.
-template <int PRIM, int QW, int MODE, bool GRAD>
+template <int PRIM, int QW, int MODE, bool GRAD, bool EX>
 __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const ChunkBlock &B, const SlotMeta &mt,
                                            unsigned qmask, float4 (*wq)[kQRec], const QueryConsts &k, int lane,
                                            int &group, unsigned &cand, unsigned &c_hits) {
@@ -676,24 +715,26 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
     }
     LaneG g;
     lane_gaussian(B, mt, lane, g);
+    g.f = 0.f;
+    if constexpr (EX && PRIM == 0) g.f = half_tr_ss(g);
     cand += (unsigned)__popc(qmask) * (unsigned)(mt.hi - mt.lo);
     {
 #pragma unroll
         for (int j = 0; j < QW; j += 2) {
             const bool p0 = (qmask >> j) & 1u, p1 = (qmask >> (j + 1)) & 1u;
             if (p0 && p1) {
-                pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
-                pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j, g, wq[j], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j + 1, g, wq[j + 1], k);
             } else if (p0) {
-                pair_update<PRIM, QW, MODE, GRAD>(A, j, g, wq[j], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j, g, wq[j], k);
             } else if (p1) {
-                pair_update<PRIM, QW, MODE, GRAD>(A, j + 1, g, wq[j + 1], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j + 1, g, wq[j + 1], k);
             }
         }
     }
 }
 
-template <int PRIM, class C, int MODE, bool GRAD>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX>
 __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int warp, bool abort) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int QW = C::QW;
@@ -850,7 +891,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             bool wpass = false;
             if (lane < nslots) {
                 const float4 blo = sm->blk[s][lane].lo, bhi = sm->blk[s][lane].hi;
-                const float R = reach(wal, wbe, blo.w, sc.pad_abs);
+                const float R = reach<EX>(wal, wbe, blo.w, sc.pad_abs);
                 wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
             }
             unsigned pmask = __ballot_sync(0xffffffffu, wpass);
@@ -873,7 +914,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
 #pragma unroll
                 for (int r = 1; r < CPR; ++r) my = part == r ? sl[r] : my;
                 bool qp = false;
-                if (my >= 0) qp = reaches<PRIM>(wq[lane % QW], sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs);
+                if (my >= 0) qp = reaches<PRIM, EX>(wq[lane % QW], sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs);
                 const unsigned hits = __ballot_sync(0xffffffffu, qp);
 #pragma unroll
                 for (int r = 0; r < CPR; ++r)
@@ -893,7 +934,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     }
                     const unsigned qa = __shfl_sync(0xffffffffu, myq, sa);
                     const unsigned qb = sb >= 0 ? __shfl_sync(0xffffffffu, myq, sb) : 0u;
-                    eval_chunk_pair<QW, C::GROUP>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
+                    eval_chunk_pair<QW, C::GROUP, EX>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
                                                   sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd, k,
                                                   lane, cand, c_hits);
                 }
@@ -903,8 +944,8 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     const int sl = __ffs(cmask) - 1;
                     cmask &= cmask - 1;
                     const unsigned q = __shfl_sync(0xffffffffu, myq, sl);
-                    eval_chunk<PRIM, QW, MODE, GRAD>(A, sm->blk[s][sl], sm->meta[s][sl], q, wq, k, lane, group, cand,
-                                                     c_hits);
+                    eval_chunk<PRIM, QW, MODE, GRAD, EX>(A, sm->blk[s][sl], sm->meta[s][sl], q, wq, k, lane, group,
+                                                         cand, c_hits);
                 }
             }
         }
@@ -1006,7 +1047,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     }
 }
 
-template <int PRIM, class C, int MODE, bool GRAD>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX = false>
 __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     EvalSmem<C> *sm = reinterpret_cast<EvalSmem<C> *>(smem_raw);
@@ -1024,9 +1065,9 @@ __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalA
     const int tile = blockIdx.x;
     const bool abort = sm->abort != 0;
     if (warp == C::NCW) {
-        if (!abort) producer_warp<PRIM, C>(a, sm, tile, MODE == 3);
+        if (!abort) producer_warp<PRIM, C, EX>(a, sm, tile, MODE == 3);
     } else {
-        consumer_warp<PRIM, C, MODE, GRAD>(a, sm, tile, warp, abort);
+        consumer_warp<PRIM, C, MODE, GRAD, EX>(a, sm, tile, warp, abort);
     }
 }
 
@@ -1186,6 +1227,7 @@ QueryConsts make_consts(const cs_params &p) {
     k.k_thr = p.k_thr;
     k.mode = p.mode;
     k.group_size = p.group_size;
+    k.exact = p.exact_variance;
     return k;
 }
 
@@ -1253,12 +1295,12 @@ int tile_configs(int32_t *ids, int32_t cap) {
     return n;
 }
 
-template <int PRIM, class C, int MODE, bool GRAD>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX = false>
 static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
     constexpr int TQ = C::NCW * C::QW;
     const int ntiles = (a.Q + TQ - 1) / TQ;
     const size_t smem = sizeof(EvalSmem<C>);
-    auto kern = k_eval<PRIM, C, MODE, GRAD>;
+    auto kern = k_eval<PRIM, C, MODE, GRAD, EX>;
     static bool attr = false;  // once per instantiation (idempotent)
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1289,8 +1331,29 @@ static cudaError_t launch_grad(const EvalArgs &a, int mode, cudaStream_t s) {
     return launch_eval_t<PRIM, C, 2, true>(a, s);
 }
 
+// The exact variance (cs_params.exact_variance) runs the default shapes only:
+// shape 23 up to 2^17 rows, 18 above (flags mode likewise), adjoint shape 2.
+template <int PRIM>
+static cudaError_t launch_exact(const EvalArgs &a, bool grad, cudaStream_t s) {
+    const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
+    if (grad) {
+        if (mode == 0) return launch_eval_t<PRIM, CfgGrad2, 0, true, true>(a, s);
+        if (mode == 1) return launch_eval_t<PRIM, CfgGrad2, 1, true, true>(a, s);
+        return launch_eval_t<PRIM, CfgGrad2, 2, true, true>(a, s);
+    }
+    const bool small = a.Q <= kSmallBatchQ;
+    if (a.k.mode == CS_METRIC_FLAGS)
+        return small ? launch_eval_t<PRIM, Cfg23, 3, false, true>(a, s) : launch_eval_t<PRIM, Cfg18, 3, false, true>(a, s);
+    if (mode == 0)
+        return small ? launch_eval_t<PRIM, Cfg23, 0, false, true>(a, s) : launch_eval_t<PRIM, Cfg18, 0, false, true>(a, s);
+    if (mode == 1)
+        return small ? launch_eval_t<PRIM, Cfg23, 1, false, true>(a, s) : launch_eval_t<PRIM, Cfg18, 1, false, true>(a, s);
+    return small ? launch_eval_t<PRIM, Cfg23, 2, false, true>(a, s) : launch_eval_t<PRIM, Cfg18, 2, false, true>(a, s);
+}
+
 template <int PRIM>
 static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStream_t s) {
+    if (a.k.exact) return launch_exact<PRIM>(a, grad, s);
     if (grad) {
         const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
         const int gt = (tile >= 1 && tile <= 4) ? tile : kDefaultGradTile;

@@ -12,8 +12,8 @@ may change neighbour-set membership in FP32 and are excluded from the
 metric/count checks; queries with a pair inside the collision band
 (|st^2 - 1| <= 1e-5) are excluded from the flag/in-count checks; queries
 whose Eq. 8 terms cancel strongly (cond = max over N_j of s^2 + n sqrt(sigma^2)
-above 50) are held to the derived bound 1e-5 + 16 u gamma cond instead.  Every
-exclusion is counted and returned.
+above 50, or cond_strict) are held to the derived bound 1e-5 + 16 u gamma cond
+instead.  Every exclusion is counted and returned.
 
 Thin ellipsoids: evaluating s^2 = d^T (A d) in FP32 with A = R P R^T rounds with
 an error up to 8 u d^T|A|d <= 24 u kappa s^2, kappa = (a_max / a_min)^2 the
@@ -28,14 +28,15 @@ REL = 1e-5
 COND_STRICT = 50.0
 
 
-def compare(gpu: dict, orc: dict, mode: int, params, label: str = "", check_count=True, kappa=None):
+def compare(gpu: dict, orc: dict, mode: int, params, label: str = "", check_count=True, kappa=None,
+            cond_strict=COND_STRICT):
     import oracle
     metric_o = oracle.metric(orc, mode)
     g_metric = gpu["metric"].astype(np.float64)
     Q = metric_o.shape[0]
     band_cut = orc["band_cut"] > 0
     band_in = orc["band_in"] > 0
-    strong = orc["cond"] > COND_STRICT
+    strong = orc["cond"] > cond_strict
     report = {"Q": Q, "band_cut": int(band_cut.sum()), "band_in": int(band_in.sum()),
               "cancel": int((strong & ~band_cut).sum())}
     ok = ~band_cut

@@ -1,0 +1,160 @@
+"""The exact-variance option (cs_params.exact_variance) against the FP64
+oracle's exact variance (oracle.Params(exact_variance=True)).
+
+sigma^2 of Eq. 8 becomes the exact variance of the quadratic form of Eq. 5
+under the Gaussian, 4 d^T A Sigma A d + 2 tr((A Sigma)^2), instead of Eq. 7's
+first-order term.  The tolerances are those of the other parity tests, with
+one change: the trace term enlarges n sqrt(sigma^2), so Eq. 8 cancels more
+often, and rows with cond = s^2 + n sqrt(sigma^2) above 10 (rather than 50)
+are held to the bound derived from that cancellation, 1e-5 + 16 u gamma cond
+relative (the FP32 error of st^2, 8 u cond, times the gamma of Eq. 11's
+exponent); below it the 1e-5 relative bound stands.  The trace term itself
+adds non-negative contributions for spheres (tr(Sigma^2)), and for ellipsoids
+products whose rounding the thin-ellipsoid bound (24 u kappa cond) covers.
+Both forward shapes the option runs (up to 2^17 rows and above), the flags
+mode, the adjoint and the cull's wider reach are covered.
+"""
+import numpy as np
+import pytest
+
+import cs_synth as S
+import oracle
+from _parity import compare, to_np
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+EXACT = oracle.Params(exact_variance=True)
+U32 = 2.0 ** -24
+COND = 10.0
+
+
+@pytest.fixture(scope="module")
+def cs(cuda_device):
+    import paper_2609_35619_b300 as cs
+    return cs
+
+
+@pytest.fixture(scope="module")
+def tiny(cs):
+    sc = S.tiny_scene(n=3000)
+    return sc, cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"])
+
+
+def _run(cs, scene, prims, ns, prim_type=0, mode=0, **kw):
+    out = scene.query(torch.as_tensor(prims), ns, prim_type=prim_type,
+                      params=cs.QueryParams(mode=mode, exact_variance=True, **kw), want_count=True)
+    torch.cuda.synchronize()
+    return to_np(out)
+
+
+@pytest.mark.parametrize("nsigma", [0.5, 1.0, 2.0])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_spheres_all_modes(cs, tiny, nsigma, mode):
+    sc, scene = tiny
+    rng = np.random.default_rng(int(nsigma * 10) + mode)
+    Q = 3000
+    q = np.c_[rng.uniform(0, 2, (Q, 3)), rng.uniform(0.03, 0.3, Q)].astype(np.float32)
+    out = _run(cs, scene, q, nsigma, mode=mode)
+    orc = oracle.query(sc, q, 0, nsigma, EXACT)
+    rep = compare(out, orc, mode, EXACT, f"exact spheres ns={nsigma} mode={mode}", cond_strict=COND)
+    assert rep["checked"] > 0.9 * rep["Q"], rep
+    # the trace term matters here: the linearised oracle disagrees somewhere
+    lin = oracle.query(sc, q, 0, nsigma)
+    assert (lin["count_nbr"] != orc["count_nbr"]).any() or (lin["count_in"] != orc["count_in"]).any()
+
+
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_ellipsoids(cs, tiny, mode):
+    sc, scene = tiny
+    rng = np.random.default_rng(50 + mode)
+    e = S.ellipsoid_queries(51, rng.uniform(0, 2, (1500, 3)), semi_lo=0.03, semi_hi=0.2)
+    kappa = (e[:, 7:10].max(1) / e[:, 7:10].min(1)).astype(np.float64) ** 2
+    cond = oracle.query(sc, e, 1, 1.0, EXACT)["cond"]
+    band = max(1e-5, 24 * U32 * kappa.max() * max(cond.max(), 4.0))
+    orc = oracle.query(sc, e, 1, 1.0, oracle.Params(exact_variance=True, band=band))
+    out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode)
+    rep = compare(out, orc, mode, EXACT, f"exact ellipsoids mode={mode}", kappa=kappa, cond_strict=COND)
+    assert rep["checked"] > 0.5 * rep["Q"], rep
+
+
+def test_large_batch_shape_sampled(cs, tiny):
+    """More than 2^17 rows: the large-batch shape, sampled rows checked."""
+    sc, scene = tiny
+    rng = np.random.default_rng(61)
+    Q = (1 << 17) + 3001
+    q = np.c_[rng.uniform(0, 2, (Q, 3)), rng.uniform(0.03, 0.3, Q)].astype(np.float32)
+    out = _run(cs, scene, q, 1.0)
+    idx = np.sort(rng.choice(Q, 3000, replace=False))
+    orc = oracle.query(sc, q[idx], 0, 1.0, EXACT)
+    rep = compare({k: v[idx] for k, v in out.items()}, orc, 0, EXACT, "exact large batch", cond_strict=COND)
+    assert rep["checked"] > 0.9 * rep["Q"], rep
+
+
+def test_tile_config_is_ignored_and_more_conservative(cs, tiny):
+    """The option runs the default shape whatever tile_config says (same bits),
+    and can only add neighbours and collisions relative to Eq. 7."""
+    sc, scene = tiny
+    rng = np.random.default_rng(62)
+    q = np.c_[rng.uniform(0, 2, (4000, 3)), rng.uniform(0.03, 0.3, 4000)].astype(np.float32)
+    a = _run(cs, scene, q, 1.0)
+    for cfg in (1, 5, 18):
+        b = _run(cs, scene, q, 1.0, tile_config=cfg)
+        np.testing.assert_array_equal(a["metric"].view(np.uint32), b["metric"].view(np.uint32))
+        np.testing.assert_array_equal(a["count"], b["count"])
+    lin = to_np(scene.query(torch.as_tensor(q), 1.0, want_count=True))
+    torch.cuda.synchronize()
+    assert (a["count"] >= lin["count"]).all() and (a["collide"] >= lin["collide"]).all()
+    assert (a["count"] > lin["count"]).any()
+
+
+@pytest.mark.parametrize("prim_type", [0, 1])
+def test_flags_mode(cs, tiny, prim_type):
+    sc, scene = tiny
+    rng = np.random.default_rng(70 + prim_type)
+    Q, G = 4000, 4
+    c = rng.uniform(0, 2, (Q, 3))
+    prims = (np.c_[c, rng.uniform(0.02, 0.06, Q)] if prim_type == 0
+             else S.ellipsoid_queries(71, c, semi_lo=0.02, semi_hi=0.06)).astype(np.float32)
+    full = scene.query(torch.as_tensor(prims), 1.0, prim_type=prim_type,
+                       params=cs.QueryParams(group_size=G, exact_variance=True))
+    fl = scene.query(torch.as_tensor(prims), 1.0, prim_type=prim_type,
+                     params=cs.QueryParams(group_size=G, mode=cs.CS_METRIC_FLAGS, exact_variance=True))
+    torch.cuda.synchronize()
+    f_row, g_row = fl["collide"].cpu().numpy(), full["collide"].cpu().numpy()
+    done = f_row != 2
+    np.testing.assert_array_equal(f_row[done], g_row[done])
+    gf = fl["group_collide"].cpu().numpy()
+    np.testing.assert_array_equal(gf, full["group_collide"].cpu().numpy())
+    assert gf.sum() > 0 and (gf == 0).sum() > 0
+    orc = oracle.query(sc, prims, prim_type, 1.0, EXACT)
+    og = oracle.group_reduce(orc["mean_cost"], orc["collide"], G)[1]
+    band = oracle.group_reduce(orc["mean_cost"], orc["band_in"] > 0, G)[1].astype(bool)
+    np.testing.assert_array_equal(gf[~band], og[~band])
+
+
+@pytest.mark.parametrize("mode", [0, 2, 3])
+@pytest.mark.parametrize("prim_type", [0, 1])
+def test_adjoint(cs, tiny, mode, prim_type):
+    """The adjoint with the exact variance against the oracle's analytic
+    gradient (which central differences pin), tolerance of the adjoint tests."""
+    sc, scene = tiny
+    rng = np.random.default_rng(80 + mode)
+    Q = 700
+    c = rng.uniform(0, 2, (Q, 3))
+    prims = (np.c_[c, rng.uniform(0.05, 0.25, Q)] if prim_type == 0
+             else S.ellipsoid_queries(81, c)).astype(np.float32)
+    up = rng.normal(size=Q).astype(np.float32)
+    g = scene.query_grad(torch.as_tensor(prims), 1.0, grad_out=torch.as_tensor(up), prim_type=prim_type,
+                         params=cs.QueryParams(mode=mode, exact_variance=True)).cpu().numpy()
+    go, scale = oracle.grad(sc, prims, prim_type, 1.0, mode, grad_out=up.astype(np.float64),
+                            return_scale=True, params=EXACT)
+    orc = oracle.query(sc, prims, prim_type, 1.0, EXACT)
+    excl = (orc["band_cut"] > 0) | (orc["band_kink"] > 0)
+    wrel = (16 * U32 * EXACT.gamma * orc["cond"] if mode in (0, 1)
+            else 16 * U32 * orc["cond"] / EXACT.tau if mode == 3 else 0.0 * orc["cond"])
+    ok = ~excl
+    err = np.linalg.norm(g[ok] - go[ok], axis=1)
+    tol = (1e-4 + wrel[ok]) * np.linalg.norm(go[ok], axis=1) + 1e-5 * scale[ok] + 1e-12
+    assert (err <= tol).all(), (mode, prim_type, (err > tol).sum(), ok.sum())
+    assert ok.sum() > 0.8 * Q
