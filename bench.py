@@ -39,7 +39,7 @@ OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes
 # DRAM bytes (read + write) of one forward launch of the fused kernel, from the
 # ncu capture of that case summarised under profiles/, valid for the library
 # version it was taken with (reported as null otherwise)
-TRAFFIC = {"version": "cs_b300 0.4 (sm_103a)", "bytes": 40.669e6 + 0.010e6,
+TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": 40.671e6 + 0.006e6,
            "case": "262,144 arm spheres, tile 23, n_sigma 1"}
 WORKLOAD = "tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres fwd+adjoint"
 
