@@ -61,14 +61,15 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=3, help="server batch slots in --case serve")
     ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
     ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
-    ap.add_argument("--case", default="step", choices=["step", "eval", "serve", "mppi", "rrt"],
+    ap.add_argument("--case", default="step", choices=["step", "eval", "serve", "mppi", "rrt", "variants"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
                          "(two fused-kernel launches); prints a short JSON summary. "
                          "serve: the serving sweep (two 3M apartment scenes, Poisson arrivals at "
                          "25/50/75/90 %% of the served capacity, 10,000 requests per load)")
     ap.add_argument("--tile", type=int, default=0, help="tile configuration for --case eval (0 = auto)")
-    ap.add_argument("--batch", default="arm", choices=["arm", "edge"], help="query batch for --case eval")
+    ap.add_argument("--batch", default="arm", choices=["arm", "edge", "arm_ellipsoids"],
+                    help="query batch for --case eval (arm_ellipsoids: 229,376 link ellipsoids, groups of 7)")
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
     ap.add_argument("--flags", action="store_true", help="--case eval: collision flags only (early exit)")
@@ -331,6 +332,7 @@ def run_ours(args, rank, world):
         result["served"] = run_served(torch, cs, dev, args.serve_requests)
         result["mppi"] = run_mppi(torch, cs, dev)
         result["rrt"] = run_rrt(torch, cs, dev)
+        result["variants"] = run_variants(torch, cs, dev)
     return result
 
 
@@ -658,6 +660,45 @@ def run_rrt(torch, cs, dev, iters=200, B=32, M=8):
     return res
 
 
+def run_variants(torch, cs, dev, iters=5):
+    """Variants of the metric on the 1M tabletop, each one launch per call at
+    n_sigma 1 with the default tile shape, the fused kernel timed with CUDA
+    events (mean of `iters` calls after two warm-up calls): Gaussians as
+    printed (Eq. 7), the exact-variance option, the scene as 2DGS disks and as
+    a point cloud (262,144 arm spheres each), and the arm as 229,376 link
+    ellipsoids (with Eq. 7 and the exact variance)."""
+    import cs_synth as S
+    arm = torch.as_tensor(S.arm_queries(), device=dev)
+    ell = torch.as_tensor(S.arm_ellipsoids(), device=dev)
+    cases = [("gaussians", "tabletop", arm, 0, 64, False), ("exact_variance", "tabletop", arm, 0, 64, True),
+             ("disks_2dgs", "disks", arm, 0, 64, False), ("point_cloud", "points", arm, 0, 64, False),
+             ("ellipsoid_arm", "tabletop", ell, 1, 7, False),
+             ("ellipsoid_arm_exact_variance", "tabletop", ell, 1, 7, True)]
+    gens = {"tabletop": S.tabletop_scene, "disks": S.tabletop_disks, "points": S.tabletop_points}
+    scenes, out = {}, {}
+    for name, kind, q, prim, G, exact in cases:
+        if kind not in scenes:
+            sc = gens[kind]()
+            scenes[kind] = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+        scene = scenes[kind]
+        qp = cs.QueryParams(group_size=G, exact_variance=exact)
+        for _ in range(2):
+            scene.query(q, 1.0, prim_type=prim, params=qp)
+        stats = torch.zeros(2, dtype=torch.int64, device=dev)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(iters)]
+        for i in range(iters):
+            scene.query(q, 1.0, prim_type=prim, params=qp, pair_stats=stats, eval_events=evs[i])
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs) / iters
+        cand, useful = (v // iters for v in stats.cpu().tolist())
+        out[name] = {"rows": int(q.shape[0]), "prim": "ellipsoid" if prim else "sphere", "eval_ms": ms,
+                     "useful_pairs": useful, "candidate_pairs": cand, "useful_pairs_per_s": useful / (ms * 1e-3)}
+    for scene in scenes.values():
+        scene.close()
+    return {"workload": "tabletop 1M (as printed / 2DGS disks / point cloud); 262,144 arm spheres or "
+                        "229,376 link ellipsoids; n_sigma 1; default tile shapes", **out}
+
+
 def run_rrt_case(args):
     import torch
 
@@ -745,9 +786,11 @@ def run_eval_case(args):
     import paper_2609_35619_b300 as cs
     dev = torch.device("cuda", 0)
     sc = S.tabletop_scene()
-    arm = torch.as_tensor(S.arm_queries() if args.batch == "arm" else S.edge_queries(), device=dev)
+    batches = {"arm": S.arm_queries, "edge": S.edge_queries, "arm_ellipsoids": S.arm_ellipsoids}
+    arm = torch.as_tensor(batches[args.batch](), device=dev)
     scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
-    G = 64 if args.batch == "arm" else 1024
+    G = {"arm": 64, "edge": 1024, "arm_ellipsoids": 7}[args.batch]
+    prim = cs.CS_PRIM_ELLIPSOID if args.batch == "arm_ellipsoids" else cs.CS_PRIM_SPHERE
     qp = cs.QueryParams(group_size=G, tile_config=args.tile, exact_variance=args.exact,
                         mode=cs.CS_METRIC_FLAGS if args.flags else cs.CS_METRIC_MEAN_COST)
     ns = args.nsigma
@@ -756,18 +799,18 @@ def run_eval_case(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     if args.grad:
         up = torch.ones(arm.shape[0] // G + (arm.shape[0] % G > 0), device=dev)
-        scene.query_grad(arm, ns, grad_out=up, params=qp)
-        scene.query_grad(arm, ns, grad_out=up, params=qp, eval_events=ev)
+        scene.query_grad(arm, ns, grad_out=up, params=qp, prim_type=prim)
+        scene.query_grad(arm, ns, grad_out=up, params=qp, eval_events=ev, prim_type=prim)
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1])
         print(json.dumps({"case": "eval", "grad": True, "batch": args.batch, "tile": args.tile, "nsigma": ns,
                           "exact": args.exact, "queries": arm.shape[0], "eval_ms": ms}))
         return
-    scene.query(arm, ns, params=qp)
-    scene.query(arm, ns, params=qp, pair_stats=stats, eval_events=ev)
+    scene.query(arm, ns, params=qp, prim_type=prim)
+    scene.query(arm, ns, params=qp, pair_stats=stats, eval_events=ev, prim_type=prim)
     torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1])
-    scene.query(arm, ns, params=qp, kernel_stats=kstats)
+    scene.query(arm, ns, params=qp, kernel_stats=kstats, prim_type=prim)
     torch.cuda.synchronize()
     scene.sync()
     cand, useful = stats.cpu().tolist()
@@ -791,6 +834,14 @@ def main():
         return
     if args.case == "mppi":
         run_mppi_case(args)
+        return
+    if args.case == "variants":
+        import torch
+
+        import paper_2609_35619_b300 as cs
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"case": "variants", **run_variants(torch, cs, dev)}))
         return
     if args.case == "rrt":
         run_rrt_case(args)

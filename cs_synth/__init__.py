@@ -12,9 +12,13 @@ available, so seeded stand-ins with the same structure are generated here:
   tabletop_scene    1M: a 1.2x0.8 m table plane plus 25 object clusters
   apartment_scene   3M: a 12x8x2.7 m four-room flat (walls with door gaps)
                     plus furniture clusters
+  tabletop_disks    the tabletop as a 2DGS scene: every Gaussian a disk (its
+                    third scale zero, Section I)
+  tabletop_points   the tabletop as a point cloud (every scale zero)
 
 Queries are sphere batches laid out the way MPPI and RRT consume them
-(Section II-D: (K, T, N_link); Section II-E: (N_batch, N_strides, N_links)).
+(Section II-D: (K, T, N_link); Section II-E: (N_batch, N_strides, N_links)),
+and one ellipsoid per link of the same arm (arm_ellipsoids).
 
 Conventions: float32 arrays; quaternions (w, x, y, z); scales are per-axis
 standard deviations in metres; opacity in [0, 1]; sphere rows (cx, cy, cz, r).
@@ -27,6 +31,7 @@ __all__ = [
     "tiny_scene", "tiny_queries", "drone_scene", "drone_queries", "tabletop_scene",
     "arm_queries", "edge_queries", "trajectory_poses", "apartment_scene",
     "serving_requests", "random_quats", "matrix_to_quat", "ellipsoid_queries",
+    "tabletop_disks", "tabletop_points", "arm_ellipsoids",
 ]
 
 
@@ -285,6 +290,49 @@ def _random_joints(rng, n):
     j[:, 1] = rng.uniform(0.2, 1.9, n)          # shoulder pitched over the table
     j[:, 3] = rng.uniform(-2.0, 2.0, n)
     return j
+
+
+def tabletop_disks(seed=1003, n=1_000_000):
+    """The tabletop with every Gaussian flattened into a 2DGS disk: the third
+    scale (the plane splats' normal axis; a random axis of the cluster
+    Gaussians) set to zero."""
+    sc = tabletop_scene(seed, n)
+    sc["scales"][:, 2] = 0.0
+    return sc
+
+
+def tabletop_points(seed=1003, n=1_000_000):
+    """The tabletop's means as a point cloud: every scale zero."""
+    sc = tabletop_scene(seed, n)
+    sc["scales"][:] = 0.0
+    return sc
+
+
+def _arm_ellipsoids(joints):
+    """One ellipsoid per link of the 7-joint chain: centred on the link's
+    midpoint, its third axis along the link (semi-axis half the link plus the
+    radius), the first two the link radius (8 cm at the base to 2 cm at the
+    tip); rows [n, 7, 10]."""
+    n = joints.shape[0]
+    R = np.broadcast_to(np.eye(3), (n, 3, 3)).copy()
+    p = np.broadcast_to(_ARM_BASE, (n, 3)).copy()
+    radii = np.linspace(0.08, 0.02, 7)
+    rows = []
+    for k in range(7):
+        R = R @ _axis_rot(_AXES[k], joints[:, k])
+        q = p + R[:, :, 2] * _LINK[k]
+        semi = np.broadcast_to([radii[k], radii[k], _LINK[k] / 2 + radii[k]], (n, 3))
+        rows.append(np.concatenate([(p + q) / 2, matrix_to_quat(R), semi], 1))
+        p = q
+    return np.stack(rows, 1)
+
+
+def arm_ellipsoids(seed=1003, configs=32768):
+    """Multi-link ellipsoid robot batch: configs x 7 link ellipsoids (one group
+    of 7 rows per configuration); 229,376 rows by default."""
+    rng = np.random.default_rng(seed + 900)
+    e = _arm_ellipsoids(_random_joints(rng, configs))
+    return np.ascontiguousarray(e.reshape(-1, 10), np.float32)
 
 
 def arm_queries(seed=1003, configs=4096):

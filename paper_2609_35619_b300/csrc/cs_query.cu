@@ -96,7 +96,7 @@ struct SlotMeta {
 
 // Per-primitive data in shared memory, 4 float4 (QREC) per primitive:
 //   sphere:    (c, 1/r^2) (2n, alpha, beta, live) - -
-//   ellipsoid: (c, 2n) (Axx, Ayy, Azz, Axy) (Axz, Ayz, alpha, beta) (live, - - -)
+//   ellipsoid: (c, 2n) (Axx, Ayy, Azz, Axy) (Axz, Ayz, alpha, beta) (live, 1/a_min, - -)
 constexpr int kQRec = 4;
 constexpr int kSub = 8;  // sub-boxes of a tile in the producer's cull
 
@@ -125,24 +125,28 @@ template <> struct PrimTraits<1> { static constexpr int RECS = 3; };  // ellipso
 
 // Cull parameters of one prepared primitive: every pair whose centre distance
 // exceeds alpha*s + sqrt(alpha^2 s^2 + beta) (s = the Gaussian's largest
-// scale) has st2 > S_reach.  With d the centre offset, s^2 >= |d|^2/a_max^2
-// and sqrt(sigma^2) <= 2 s |d| / a_min^2, so st2 <= S requires
-// |d|^2 - 2 n s |d| a_max^2/a_min^2 - S a_max^2 <= 0:
-//   sphere:    alpha = n,                 beta = S r^2
-//   ellipsoid: alpha = n a_max^2/a_min^2, beta = S a_max^2.
-// With the exact variance, tr((A Sigma)^2)/2 <= 1.5 s^4 / a_min^4 joins
-// (s |d| / a_min^2)^2 under the root, which the exact-variance reach takes
-// into account with the same alpha and beta.
-template <int PRIM>
-__device__ __forceinline__ void prim_reach(const float4 *rec, float ns, float S, float &alpha,
-                                           float &beta) {
+// scale) has st2 > S_reach.
+//   sphere:    alpha = n, beta = S r^2 (|d|^2 - 2 n s |d| <= S r^2; with the
+//              exact variance the reach adds the trace term itself);
+//   ellipsoid: in the ellipsoid's own scaling t = sqrt(s^2) = |A^1/2 d|,
+//              |A d| <= t / a_min, so sqrt(sigma^2) <= 2 s t / a_min and
+//              st2 <= S requires t <= t_max(s) = nu s/a_min + sqrt(nu^2 s^2/a_min^2 + S)
+//              with nu = n; then |d| <= a_max t_max(s), i.e.
+//              alpha = nu a_max/a_min, beta = S a_max^2.  With the exact
+//              variance, tr((A Sigma)^2)/2 <= 1.5 s^4/a_min^4 adds at most
+//              sqrt(6) n s^2/a_min^2 to the condition on t, which
+//              nu = sqrt(n^2 + sqrt(6) n) covers.
+// The consumers' per-chunk ellipsoid test (reaches) works with t_max itself.
+template <int PRIM, bool EX>
+__device__ __forceinline__ void prim_reach(const float4 *rec, float ns, float S, float &alpha, float &beta) {
     if (PRIM == 0) {
         float r = rec[0].w;
         alpha = ns;
         beta = S * r * r;
     } else {
         float amax = rec[0].w, amin = rec[2].z;
-        alpha = ns * (amax * amax) / (amin * amin);
+        const float nu = EX ? sqrtf(fmaf(ns, ns, 2.4494898f * ns)) : ns;
+        alpha = nu * amax / amin;
         beta = S * amax * amax;
     }
 }
@@ -177,7 +181,7 @@ __device__ __noinline__ long long wait_phase(uint64_t *bar, unsigned parity, lon
 
 
 // ------------------------------------------------------------- producer
-template <class C, bool EX>
+template <int PRIM, class C, bool EX>
 struct Producer {
     EvalSmem<C> *sm;
     const SceneDev *sc;
@@ -249,12 +253,12 @@ struct Producer {
     // sparse tile (primitives scattered over the scene) stages only what
     // some group of its rows can reach.
     __device__ bool meets(const NodeBox &b) const {
-        const float R = reach<EX>(al, be, b.lo.w, sc->pad_abs);
+        const float R = reach<EX && PRIM == 0>(al, be, b.lo.w, sc->pad_abs);
         if (box_gap2(lx, ly, lz, hx, hy, hz, b.lo, b.hi) > R * R) return false;
 #pragma unroll 1
         for (int k = 0; k < kSub; ++k) {
             const float4 lo = sm->sub[k][0], hi = sm->sub[k][1];
-            const float Rk = reach<EX>(lo.w, hi.w, b.lo.w, sc->pad_abs);
+            const float Rk = reach<EX && PRIM == 0>(lo.w, hi.w, b.lo.w, sc->pad_abs);
             if (box_gap2(lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, b.lo, b.hi) <= Rk * Rk) return true;
         }
         return false;
@@ -347,7 +351,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool
             const float4 *rec = a.qrec + (size_t)q * RECS;
             const float4 r0 = rec[0];
             if (rec_valid(r0)) {
-                prim_reach<PRIM>(rec, a.qns[q], a.k.S_reach, alpha, beta);
+                prim_reach<PRIM, EX>(rec, a.qns[q], a.k.S_reach, alpha, beta);
                 cx = dx = r0.x; cy = dy = r0.y; cz = dz = r0.z;
             }
         }
@@ -384,7 +388,7 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool
         al = fmaxf(al, __shfl_xor_sync(0xffffffffu, al, o));
         be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
     }
-    Producer<C, EX> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
+    Producer<PRIM, C, EX> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
     pr.early = early;
     pr.lane = lane;
     pr.t0 = t_start;
@@ -588,18 +592,37 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
 // largest scale)?  Dead slots never do.  The same answer on every lane.
 template <int PRIM, bool EX>
 __device__ __forceinline__ bool reaches(const float4 *qd, const float4 &blo, const float4 &bhi,
-                                        float pad_abs) {
+                                        float pad_abs, float S) {
     const float4 q0 = qd[0];
-    float alpha, beta, live;
     if (PRIM == 0) {
         const float4 q1 = qd[1];
-        alpha = q1.y; beta = q1.z; live = q1.w;
+        const float R = reach<EX>(q1.y, q1.z, blo.w, pad_abs);
+        return q1.w != 0.f && box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) <= R * R;
     } else {
-        const float4 q2 = qd[2];
-        alpha = q2.z; beta = q2.w; live = qd[3].x;
+        // In the ellipsoid's scaling t = |A^1/2 (x - c)|, which changes by at
+        // most |x - y| / a_min between two points: every point of the chunk's
+        // box lies within its half-diagonal rho of the box centre b, so a pair
+        // of the chunk can be within reach only if
+        //   t(b) <= t_max(sigma) + (rho + pad) / a_min,
+        // t_max the largest t with t^2 - 2 n sqrt(tau^2 t^2 [+ 1.5 tau^4]) <= S,
+        // tau = sigma / a_min (the bracket with the exact variance): the
+        // sphere reach in the ellipsoid's own scaling (reach with alpha = n,
+        // beta = S), checked with a relative margin for the FP32 rounding of
+        // t(b)^2.
+        const float4 q1 = qd[1], q2 = qd[2], q3 = qd[3];
+        const float inv_amin = q3.y;
+        const float dx = fmaf(0.5f, blo.x + bhi.x, -q0.x), dy = fmaf(0.5f, blo.y + bhi.y, -q0.y),
+                    dz = fmaf(0.5f, blo.z + bhi.z, -q0.z);
+        const float ex = bhi.x - blo.x, ey = bhi.y - blo.y, ez = bhi.z - blo.z;
+        const float rho = 0.5f * sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+        const float wx = fmaf(q2.x, dz, fmaf(q1.w, dy, q1.x * dx));
+        const float wy = fmaf(q2.y, dz, fmaf(q1.y, dy, q1.w * dx));
+        const float wz = fmaf(q1.z, dz, fmaf(q2.y, dy, q2.x * dx));
+        const float t2 = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+        const float tmax = reach<EX>(0.5f * q0.w, S, blo.w * inv_amin, 0.f);
+        const float T = fmaf(rho + pad_abs, inv_amin, tmax) * (1.f + 1e-3f);
+        return q3.x != 0.f && t2 <= T * T;
     }
-    const float R = reach<EX>(alpha, beta, blo.w, pad_abs);
-    return live != 0.f && box_gap2(q0.x, q0.y, q0.z, q0.x, q0.y, q0.z, blo, bhi) <= R * R;
 }
 
 // Lane-local Gaussian duplicated into both halves of packed registers.
@@ -754,7 +777,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             if (rec_valid(r0)) {
                 const float ns = a.qns[q];
                 float alpha, beta;
-                prim_reach<PRIM>(rec, ns, k.S_reach, alpha, beta);
+                prim_reach<PRIM, EX>(rec, ns, k.S_reach, alpha, beta);
                 if (PRIM == 0) {
                     d0 = make_float4(r0.x, r0.y, r0.z, 1.f / (r0.w * r0.w));
                     d1 = make_float4(2.f * ns, alpha, beta, 1.f);
@@ -763,7 +786,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     d0 = make_float4(r0.x, r0.y, r0.z, 2.f * ns);
                     d1 = r1;
                     d2 = make_float4(r2.x, r2.y, alpha, beta);
-                    d3 = make_float4(1.f, 0.f, 0.f, 0.f);
+                    d3 = make_float4(1.f, 1.f / r2.z, 0.f, 0.f);
                 }
                 nvalid = 1;
             }
@@ -891,7 +914,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             bool wpass = false;
             if (lane < nslots) {
                 const float4 blo = sm->blk[s][lane].lo, bhi = sm->blk[s][lane].hi;
-                const float R = reach<EX>(wal, wbe, blo.w, sc.pad_abs);
+                const float R = reach<EX && PRIM == 0>(wal, wbe, blo.w, sc.pad_abs);
                 wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
             }
             unsigned pmask = __ballot_sync(0xffffffffu, wpass);
@@ -914,7 +937,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
 #pragma unroll
                 for (int r = 1; r < CPR; ++r) my = part == r ? sl[r] : my;
                 bool qp = false;
-                if (my >= 0) qp = reaches<PRIM, EX>(wq[lane % QW], sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs);
+                if (my >= 0) qp = reaches<PRIM, EX>(wq[lane % QW], sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs, k.S_reach);
                 const unsigned hits = __ballot_sync(0xffffffffu, qp);
 #pragma unroll
                 for (int r = 0; r < CPR; ++r)

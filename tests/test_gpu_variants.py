@@ -1,0 +1,200 @@
+"""Variants of the metric on the same kernel, against the FP64 oracle:
+
+- 2DGS disk scenes (Section I: a Gaussian with one zero scale is a disk; the
+  metric uses Sigma, which stays valid although it is singular);
+- point-cloud mode (every scale zero, or n_sigma = 0: Eq. 8 reduces to the
+  scaling function of the means, Eq. 5), where the outputs must not depend
+  on n_sigma at all;
+- multi-link ellipsoid robots at scale (one ellipsoid per link of the 7-link
+  arm, 229,376 rows against the 1M tabletop, in the launch the benchmark
+  times), sampled rows checked with the thin-ellipsoid tolerance.
+
+Tolerances and exclusions are those of the other parity tests
+(tests/_parity.py), with the derived cancellation bound of Eq. 8 (1e-5 +
+16 u gamma cond relative) applied from cond = s^2 + n sqrt(sigma^2) above 10
+rather than 50: a disk's zero normal variance and n_sigma up to 2 make Eq. 8
+cancel more often than in the Gaussian scenes.  The ellipsoid checks widen the
+oracle's bands per row by that row's FP32 rounding bound of d^T A d
+(24 u kappa cond), so one badly conditioned row does not widen them all.
+"""
+import numpy as np
+import pytest
+
+import cs_synth as S
+import oracle
+from _parity import compare, to_np
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+U32 = 2.0 ** -24
+COND = 10.0
+
+
+@pytest.fixture(scope="module")
+def cs(cuda_device):
+    import paper_2609_35619_b300 as cs
+    return cs
+
+
+def _scene(cs, sc, **kw):
+    return cs.Scene(sc["means"], sc["scales"], sc["quats"], sc.get("opacity"), **kw)
+
+
+def _run(cs, scene, prims, ns, prim_type=0, mode=0, **kw):
+    out = scene.query(torch.as_tensor(prims), ns, prim_type=prim_type, params=cs.QueryParams(mode=mode, **kw),
+                      want_count=True)
+    torch.cuda.synchronize()
+    return to_np(out)
+
+
+def _tiny_variant(kind):
+    sc = S.tiny_scene(n=3000)
+    if kind == "disks":
+        sc["scales"][:, 2] = 0.0
+    elif kind == "points":
+        sc["scales"][:] = 0.0
+    return sc
+
+
+def _ellipsoid_case(sc, e, ns, **kw):
+    """Oracle results with each row's bands widened by its own FP32 rounding
+    bound of d^T A d (rows grouped by that width, rounded up to a power of
+    two: one oracle call per group), and kappa per row."""
+    kappa = (e[:, 7:10].max(1) / e[:, 7:10].min(1)).astype(np.float64) ** 2
+    cond = oracle.query(sc, e, 1, ns, oracle.Params(**kw))["cond"]
+    band = np.maximum(1e-5, 24 * U32 * kappa * np.maximum(cond, 4.0))
+    band = 2.0 ** np.ceil(np.log2(band))
+    res = None
+    for b in np.unique(band):
+        rows = np.flatnonzero(band == b)
+        r = oracle.query(sc, e[rows], 1, ns, oracle.Params(band=float(b), **kw))
+        if res is None:
+            res = {k: np.empty((e.shape[0],) + v.shape[1:], v.dtype) for k, v in r.items()}
+        for k, v in r.items():
+            res[k][rows] = v
+    return res, kappa
+
+
+# ------------------------------------------------------------ 2DGS disks
+@pytest.mark.parametrize("nsigma", [0.0, 1.0, 2.0])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_disk_scene_spheres(cs, mode, nsigma):
+    sc = _tiny_variant("disks")
+    rng = np.random.default_rng(200 + mode)
+    q = np.c_[rng.uniform(0, 2, (2500, 3)), rng.uniform(0.03, 0.3, 2500)].astype(np.float32)
+    out = _run(cs, _scene(cs, sc), q, nsigma, mode=mode)
+    rep = compare(out, oracle.query(sc, q, 0, nsigma), mode, oracle.Params(), f"disks mode={mode} ns={nsigma}",
+                  cond_strict=COND)
+    assert rep["checked"] > 0.9 * rep["Q"], rep
+
+
+@pytest.mark.parametrize("mode", [0, 3])
+def test_disk_scene_ellipsoids_and_exact_variance(cs, mode):
+    sc = _tiny_variant("disks")
+    scene = _scene(cs, sc)
+    rng = np.random.default_rng(210 + mode)
+    e = S.ellipsoid_queries(211, rng.uniform(0, 2, (1500, 3)), semi_lo=0.03, semi_hi=0.2)
+    orc, kappa = _ellipsoid_case(sc, e, 1.0)
+    rep = compare(_run(cs, scene, e, 1.0, prim_type=1, mode=mode), orc, mode, oracle.Params(),
+                  f"disks ellipsoids mode={mode}", kappa=kappa, cond_strict=COND)
+    assert rep["checked"] > 0.5 * rep["Q"], rep
+    # the exact variance with disks: tr((A Sigma)^2) of a singular Sigma
+    orc, kappa = _ellipsoid_case(sc, e, 1.0, exact_variance=True)
+    rep = compare(_run(cs, scene, e, 1.0, prim_type=1, mode=mode, exact_variance=True), orc, mode,
+                  oracle.Params(exact_variance=True), f"disks ellipsoids exact mode={mode}", kappa=kappa,
+                  cond_strict=COND)
+    assert rep["checked"] > 0.5 * rep["Q"], rep
+
+
+# ------------------------------------------------------ point-cloud mode
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_point_cloud_scene(cs, mode):
+    """Every scale zero: the outputs are the oracle's and do not depend on
+    n_sigma, bit for bit (sqrt(sigma^2) is exactly 0)."""
+    sc = _tiny_variant("points")
+    scene = _scene(cs, sc)
+    rng = np.random.default_rng(220 + mode)
+    q = np.c_[rng.uniform(0, 2, (2500, 3)), rng.uniform(0.03, 0.3, 2500)].astype(np.float32)
+    out0 = _run(cs, scene, q, 0.0, mode=mode)
+    rep = compare(out0, oracle.query(sc, q, 0, 0.0), mode, oracle.Params(), f"points mode={mode}", cond_strict=COND)
+    assert rep["checked"] > 0.9 * rep["Q"], rep
+    for ns in (1.0, 2.5):
+        o = _run(cs, scene, q, ns, mode=mode)
+        np.testing.assert_array_equal(o["metric"].view(np.uint32), out0["metric"].view(np.uint32))
+        np.testing.assert_array_equal(o["count"], out0["count"])
+        np.testing.assert_array_equal(o["collide"], out0["collide"])
+
+
+def test_nsigma_zero_equals_the_point_cloud_of_the_means(cs):
+    """n_sigma = 0 on a Gaussian scene gives the point cloud of its means:
+    the same neighbour sets and flags, the same metric up to the order of the
+    sums (the two scenes chunk differently)."""
+    sc = S.tiny_scene(n=3000)
+    pts = dict(sc, scales=np.zeros_like(sc["scales"]))
+    rng = np.random.default_rng(230)
+    q = np.c_[rng.uniform(0, 2, (3000, 3)), rng.uniform(0.03, 0.3, 3000)].astype(np.float32)
+    a = _run(cs, _scene(cs, sc, use_filter=False), q, 0.0)
+    b = _run(cs, _scene(cs, pts, use_filter=False), q, 0.0)
+    np.testing.assert_array_equal(a["count"], b["count"])
+    np.testing.assert_array_equal(a["collide"], b["collide"])
+    np.testing.assert_allclose(a["metric"], b["metric"], rtol=1e-5, atol=0)
+    assert (a["count"] > 0).mean() > 0.5
+
+
+# ---------------------------------------------------- full-size variants
+def _sample(Q, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(Q, size=min(k, Q), replace=False))
+
+
+def _touching(out, k, seed):
+    t = np.flatnonzero(out["count"] > 0)
+    return np.random.default_rng(seed).choice(t, size=min(k, t.size), replace=False)
+
+
+@pytest.mark.parametrize("kind", ["disks", "points"])
+def test_tabletop_variant_full_size(cs, kind):
+    """The 1M tabletop as 2DGS disks / as a point cloud, 262,144 arm spheres
+    at n_sigma 1 in one launch, sampled rows checked."""
+    sc = S.tabletop_disks() if kind == "disks" else S.tabletop_points()
+    q = S.arm_queries()
+    out = _run(cs, _scene(cs, sc), q, 1.0, group_size=64)
+    idx = np.unique(np.r_[_sample(q.shape[0], 96, 240), _touching(out, 64, 241)])
+    orc = oracle.query(sc, q[idx], 0, 1.0)
+    rep = compare({k: v[idx] for k, v in out.items() if v.shape[0] == q.shape[0]}, orc, 0, oracle.Params(),
+                  f"tabletop {kind}", cond_strict=COND)
+    assert rep["checked"] > 100, rep
+
+
+@pytest.mark.parametrize("mode", [0, 4])
+def test_ellipsoid_arm_full_size(cs, mode):
+    """229,376 link ellipsoids (32,768 configurations x 7 links) against the
+    1M tabletop at n_sigma 1, groups of 7 rows per configuration: sampled rows
+    against the oracle; group outputs against the rows (cost mode) or the
+    oracle's group flags (flags mode)."""
+    sc = S.tabletop_scene()
+    e = S.arm_ellipsoids()
+    scene = _scene(cs, sc)
+    out = scene.query(torch.as_tensor(e), 1.0, prim_type=1, params=cs.QueryParams(mode=mode, group_size=7),
+                      want_count=mode != 4)
+    torch.cuda.synchronize()
+    out = to_np(out)
+    if mode == 4:
+        cfg = _sample(e.shape[0] // 7, 48, 250)
+        rows = (cfg[:, None] * 7 + np.arange(7)[None]).reshape(-1)
+        orc, _ = _ellipsoid_case(sc, e[rows], 1.0)
+        og = oracle.group_reduce(orc["mean_cost"], orc["collide"], 7)[1]
+        band = oracle.group_reduce(orc["mean_cost"], orc["band_in"] > 0, 7)[1].astype(bool)
+        gc = out["group_collide"][cfg]
+        np.testing.assert_array_equal(gc[~band], og[~band])
+        assert 0 < gc.sum() < gc.size
+        return
+    # rows with thousands of neighbours often have a pair in the cutoff band
+    # (excluded), so the sample is larger than for the sphere batches
+    idx = np.unique(np.r_[_sample(e.shape[0], 256, 251), _touching(out, 160, 252)])
+    orc, kappa = _ellipsoid_case(sc, e[idx], 1.0)
+    rep = compare({k: v[idx] for k, v in out.items() if v.shape[0] == e.shape[0]}, orc, 0, oracle.Params(),
+                  "ellipsoid arm", kappa=kappa, cond_strict=COND)
+    assert rep["checked"] > 150, rep
+    np.testing.assert_allclose(out["group_metric"], out["metric"].reshape(-1, 7).astype(np.float64).sum(1),
+                               rtol=1e-5)
+    assert (out["group_collide"] == out["collide"].reshape(-1, 7).max(1)).all()
