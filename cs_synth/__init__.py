@@ -31,7 +31,8 @@ __all__ = [
     "tiny_scene", "tiny_queries", "drone_scene", "drone_queries", "tabletop_scene",
     "arm_queries", "edge_queries", "trajectory_poses", "apartment_scene",
     "serving_requests", "random_quats", "matrix_to_quat", "ellipsoid_queries",
-    "tabletop_disks", "tabletop_points", "arm_ellipsoids",
+    "tabletop_disks", "tabletop_points", "arm_ellipsoids", "look_at", "scene_colors",
+    "drone_terminal_cameras", "tabletop_cameras",
 ]
 
 
@@ -439,3 +440,59 @@ def serving_requests(seed=1007, count=1000, q_lo=16, q_hi=262_144, mean_interarr
             "spheres": np.ascontiguousarray(np.concatenate([c, r], 1), np.float32),
         })
     return out
+
+
+# ------------------------------------------------------- rendering inputs
+def look_at(eye, target, up=(0.0, 0.0, 1.0), f=100.0, width=128, height=128) -> np.ndarray:
+    """Camera row (16 float32: world-to-camera R row-major, t, fx, fy, cx, cy)
+    at `eye` looking at `target`: camera z along the view direction, x to the
+    right, y down the image rows, principal point at the image centre."""
+    eye = np.asarray(eye, np.float64)
+    zc = np.asarray(target, np.float64) - eye
+    zc /= np.linalg.norm(zc)
+    xc = np.cross(zc, np.asarray(up, np.float64))
+    xc /= np.linalg.norm(xc)
+    yc = np.cross(zc, xc)
+    R = np.stack([xc, yc, zc])
+    t = -R @ eye
+    return np.concatenate([R.ravel(), t, [f, f, width / 2.0, height / 2.0]]).astype(np.float32)
+
+
+def scene_colors(scene, seed=1100) -> np.ndarray:
+    """Per-Gaussian RGB in [0, 1] (view-independent colour, the degree-0 part
+    of 3DGS appearance): a smooth function of position plus noise, so images
+    have structure."""
+    rng = np.random.default_rng(seed)
+    m = np.asarray(scene["means"], np.float64)
+    phase = rng.uniform(0, 2 * np.pi, 3)
+    freq = rng.uniform(3.0, 9.0, 3)
+    base = 0.5 + 0.35 * np.sin(m * freq[None] + phase[None])
+    return np.ascontiguousarray(np.clip(base + rng.normal(0, 0.05, m.shape), 0, 1), np.float32)
+
+
+def drone_terminal_cameras(seed=1002, rollouts=256, horizon=32, width=128, height=128, fov_deg=90.0):
+    """Cameras at the terminal states of drone MPPI rollouts in the room
+    (Section II-D: the terminal state of each rollout is rendered), looking
+    along the last step's horizontal heading: [rollouts, 16] float32."""
+    q = drone_queries(seed, rollouts=rollouts, horizon=horizon).reshape(rollouts, horizon, 4)
+    eye = q[:, -1, :3].astype(np.float64)
+    head = eye - q[:, -2, :3]
+    head[:, 2] = 0.0
+    nrm = np.linalg.norm(head, axis=1)
+    head[nrm < 1e-6] = (1.0, 0.0, 0.0)
+    head /= np.linalg.norm(head, axis=1, keepdims=True)
+    f = 0.5 * width / np.tan(np.radians(fov_deg) / 2)
+    return np.stack([look_at(e, e + h, f=f, width=width, height=height) for e, h in zip(eye, head)])
+
+
+def tabletop_cameras(seed=1101, views=256, width=128, height=128, fov_deg=60.0):
+    """Cameras on a hemisphere of radius 0.8-1.4 m around the table centre,
+    looking at points on the table: [views, 16] float32."""
+    rng = np.random.default_rng(seed)
+    az = rng.uniform(0, 2 * np.pi, views)
+    el = rng.uniform(np.radians(20), np.radians(70), views)
+    r = rng.uniform(0.8, 1.4, views)
+    eye = np.stack([r * np.cos(el) * np.cos(az), r * np.cos(el) * np.sin(az), r * np.sin(el)], 1)
+    tgt = np.c_[rng.uniform(-0.3, 0.3, (views, 2)), np.zeros(views)]
+    f = 0.5 * width / np.tan(np.radians(fov_deg) / 2)
+    return np.stack([look_at(e, t, f=f, width=width, height=height) for e, t in zip(eye, tgt)])

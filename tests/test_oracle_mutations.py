@@ -44,3 +44,38 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            os.path.join(ROOT, "tests", "test_oracle_exact_variance.py")],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert proc.returncode != 0, f"pins did not catch {name}:\n{proc.stdout[-2000:]}"
+
+
+RASTER_SRC = os.path.join(ROOT, "oracle", "raster.c")
+RASTER_MUTATIONS = {
+    "R_transposed": ("xc[a] = R[3 * a] * xw[0] + R[3 * a + 1] * xw[1] + R[3 * a + 2] * xw[2] + t[a];",
+                     "xc[a] = R[a] * xw[0] + R[3 + a] * xw[1] + R[6 + a] * xw[2] + t[a];"),
+    "J_without_z2": ("{0.0, fy / z, -fy * xc[1] / (z * z)}", "{0.0, fy / z, -fy * xc[1] / z}"),
+    "exp_without_half": ("const double A = opacity[p->idx] * exp(-0.5 * q);",
+                         "const double A = opacity[p->idx] * exp(-q);"),
+    "back_to_front": ("if (a->z32 < b->z32) return -1;\n    if (a->z32 > b->z32) return 1;",
+                      "if (a->z32 < b->z32) return 1;\n    if (a->z32 > b->z32) return -1;"),
+    "no_pixel_centre": ("const double u = x + 0.5, v = y + 0.5;", "const double u = x, v = y;"),
+    "no_clamp": ("const double a = A < 0.99 ? A : 0.99;", "const double a = A;"),
+    "conic_sign": ("p.ib = -b / det;", "p.ib = b / det;"),
+    "dilation_one_axis": ("double c = MS[1][0] * M[1][0] + MS[1][1] * M[1][1] + MS[1][2] * M[1][2] + d->dilation;",
+                          "double c = MS[1][0] * M[1][0] + MS[1][1] * M[1][1] + MS[1][2] * M[1][2];"),
+    "depth_is_z": ("p.dist = sqrt(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);", "p.dist = xc[2];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RASTER_MUTATIONS))
+def test_raster_pins_catch_planted_mistake(name, tmp_path):
+    old, new = RASTER_MUTATIONS[name]
+    src = open(RASTER_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutated = tmp_path / "raster_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libcs_oracle_raster_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, CS_ORACLE_RASTER_LIB=str(lib))
+    proc = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_raster_oracle.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert proc.returncode != 0, f"pins did not catch {name}:\n{proc.stdout[-2000:]}"
