@@ -504,6 +504,74 @@ CS_API double cs_server_clock(void);
  * progress.  NULL is a no-op. */
 CS_API cs_status cs_server_destroy(cs_server *server);
 
+/* ---------------------------------------------------------------------------
+ * Image synthesis (Section II-A, Eq. 3-4), the terminal-state images of
+ * Section II-D: the scene's kept Gaussians are projected into pinhole cameras
+ * (the mean by the point projection, the covariance by Eq. 3,
+ * Sigma' = J R Sigma R^T J^T with J the Jacobian of the projection at the
+ * mean) and alpha-blended front to back in depth order at every pixel
+ * (Eq. 4), in 16x16-pixel tiles, into device buffers (no graphics API).
+ *
+ * Rules the paper leaves open, fixed here:
+ *   - camera: x_c = R x_w + t, looking along +z, x to the right, y down the
+ *     image rows; u = fx x/z + cx, v = fy y/z + cy; pixel (i, j) samples the
+ *     image point (i + 0.5, j + 0.5);
+ *   - Sigma' gets `dilation` px^2 added to its diagonal (it stays invertible
+ *     for 2DGS disks seen edge on); a Gaussian is drawn when its camera-frame
+ *     depth is at least near_plane and det(Sigma') > 0;
+ *   - G2D(x) = exp(-(x - u)^T Sigma'^-1 (x - u) / 2); a Gaussian counts at a
+ *     pixel when opacity * G2D >= 1/255, that product is clamped to 0.99, and
+ *     a pixel stops before the Gaussian that would bring its transmittance
+ *     below 1e-4;
+ *   - order: increasing float32 depth of the mean, computed as
+ *     ((R[6] x + R[7] y) + R[8] z) + t[2] with each operation rounded, equal
+ *     depths in the scene's internal order;
+ *   - colour: one RGB per Gaussian (view independent); depth output: the
+ *     blended Euclidean distance of the means from the camera centre (the
+ *     colour replaced by the splat's distance); alpha output: 1 - final
+ *     transmittance; the background shows through the final transmittance.
+ * ------------------------------------------------------------------------- */
+typedef struct cs_camera {
+    float R[9];            /* world-to-camera rotation, row-major */
+    float t[3];            /* x_c = R x_w + t */
+    float fx, fy, cx, cy;  /* pinhole intrinsics in pixels */
+} cs_camera;
+
+typedef struct cs_render_desc {
+    int32_t n_views;       /* cameras (images), >= 0 */
+    int32_t width, height; /* pixels, each in [1, 4096] */
+    float near_plane;      /* default 0.01 (scene units) */
+    float dilation;        /* px^2 added to the diagonal of Sigma', >= 0 (default 0.3) */
+    float background[3];   /* colour behind the Gaussians (default 0, 0, 0) */
+    void *stream;          /* cudaStream_t */
+} cs_render_desc;
+
+CS_API cs_status cs_render_desc_init(cs_render_desc *desc);
+
+/* Appearance used by cs_render: per input row of cs_scene_create, its
+ * opacity (NULL: 1) and RGB colour ([n,3], NULL: 1, 1, 1), gathered into the
+ * scene's internal order (rows the floater filter dropped are ignored).
+ * on_device: 1 device pointers, 0 host pointers.  Replaces an earlier
+ * appearance; allocates the scene's appearance array on the first call and
+ * returns after the stream has finished.  Values are not range-checked:
+ * opacities outside [0, 1] blend as given. */
+CS_API cs_status cs_scene_set_appearance(cs_scene *scene, const float *opacity, const float *colors,
+                                         int32_t on_device, void *stream);
+
+/* Render desc->n_views images (Eq. 3-4).  cams: device [n_views] cs_camera.
+ * out_rgb: device [n_views, height, width, 3] (required); out_depth,
+ * out_alpha: device [n_views, height, width] or NULL.  Steps: projection of
+ * every (view, Gaussian) with its tile range, the (Gaussian, tile) instances
+ * listed and sorted by (view, tile, depth) with a stable radix sort, then one
+ * CTA per tile blending its pixels.  Scratch is pooled per (device, stream)
+ * and grown on demand; the call waits for the stream once, after counting
+ * the instances, to size it.  Errors: CS_ERR_INVALID_ARG for sizes out of
+ * range, NULL required pointers or a scene without appearance
+ * (cs_scene_set_appearance); CS_ERR_UNSUPPORTED when a call has more than
+ * 2^31 instances (render fewer views per call). */
+CS_API cs_status cs_render(const cs_scene *scene, const cs_render_desc *desc, const cs_camera *cams,
+                           float *out_rgb, float *out_depth, float *out_alpha);
+
 /* Self-test of the bounded-wait machinery: launches one block that waits on
  * a barrier nothing completes, with a budget of `spins` polls, and returns
  * CS_ERR_TIMEOUT when the wait gave up (the expected result) or CS_OK if it

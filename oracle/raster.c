@@ -33,7 +33,10 @@
  *    weight, q_k the quadratic form, kappa_k the condition number of Sigma'_k:
  *    the relative FP32 error of alpha_k G_k is at most a constant times
  *    u (1 + q_k kappa_k), and an output moves by at most 2 T_k per unit of
- *    alpha_k G_k, so the output error is bounded by a constant times u cond.
+ *    alpha_k G_k, so the output error is bounded by a constant times u cond;
+ *  - slack = sum over the Gaussians of bit 0 of 2 (1/255) (1 + band) T_k: the
+ *    most an output can move when such a Gaussian is drawn on one side and
+ *    not on the other (its weight plus its share of the later transmittance).
  */
 #include <math.h>
 #include <stdint.h>
@@ -129,10 +132,10 @@ static int64_t project_all(int64_t n, const float *means, const double *sig, con
 
 static void blend_pixel(const proj_t *P, int64_t m, const double *opacity, const double *color,
                         const orc_rdesc *d, int32_t x, int32_t y, double *rgb, double *depth, double *alpha,
-                        int32_t *ncontrib, int32_t *flags, double *cond) {
+                        int32_t *ncontrib, int32_t *flags, double *cond, double *slack) {
     const double u = x + 0.5, v = y + 0.5;
     const double thr = 1.0 / 255.0, t_stop = 1e-4, u32 = ldexp(1.0, -24);
-    double T = 1.0, c[3] = {0, 0, 0}, dd = 0.0, cd = 0.0, tband = 0.0;
+    double T = 1.0, c[3] = {0, 0, 0}, dd = 0.0, cd = 0.0, tband = 0.0, sl = 0.0;
     int32_t K = 0, fl = 0;
     float last_z = 0.f;
     int have_last = 0;
@@ -143,7 +146,10 @@ static void blend_pixel(const proj_t *P, int64_t m, const double *opacity, const
         const double A = opacity[p->idx] * exp(-0.5 * q);
         const double eps = d->band_cond * u32 * (1.0 + q * p->kappa);
         const double band = d->band_rel + eps;
-        if (fabs(A - thr) <= band * thr) fl |= 1;
+        if (fabs(A - thr) <= band * thr) {
+            fl |= 1;
+            sl += 2.0 * thr * (1.0 + band) * T;
+        }
         if (A < thr) continue;
         const double a = A < 0.99 ? A : 0.99;
         const double Tn = T * (1.0 - a);
@@ -168,13 +174,14 @@ static void blend_pixel(const proj_t *P, int64_t m, const double *opacity, const
     *ncontrib = K;
     *flags = fl;
     *cond = cd;
+    *slack = sl;
 }
 
 /* Render the listed pixels (npix triples: view, x, y). */
 int orc_render_pixels(int64_t n, const float *means, const double *sig, const double *opacity,
                       const double *color, int32_t nviews, const float *cams, const orc_rdesc *d,
                       int64_t npix, const int32_t *pix, double *rgb, double *depth, double *alpha,
-                      int32_t *ncontrib, int32_t *flags, double *cond) {
+                      int32_t *ncontrib, int32_t *flags, double *cond, double *slack) {
     proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
     int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(npix > 0 ? npix : 1));
     if (!P || !list) {
@@ -194,7 +201,7 @@ int orc_render_pixels(int64_t n, const float *means, const double *sig, const do
         for (int64_t j = 0; j < cnt; ++j) {
             const int64_t i = list[j];
             blend_pixel(P, m, opacity, color, d, pix[3 * i + 1], pix[3 * i + 2], rgb + 3 * i, depth + i, alpha + i,
-                        ncontrib + i, flags + i, cond + i);
+                        ncontrib + i, flags + i, cond + i, slack + i);
         }
     }
     free(P);

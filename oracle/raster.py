@@ -61,7 +61,7 @@ def _load():
                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.POINTER(_RDesc), ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                          ctypes.c_void_p, ctypes.c_void_p]
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -72,13 +72,13 @@ def _p(a):
 
 def render(scene, colors, cams, width: int, height: int, *, near_plane: float = 0.01, dilation: float = 0.3,
            background=(0.0, 0.0, 0.0), pixels=None, use_filter: bool = True, band_rel: float = 1e-6,
-           band_cond: float = 64.0) -> dict:
+           band_cond: float = 16.0) -> dict:
     """Render the pixels (view, x, y) listed in `pixels` ([P,3] int), or every
     pixel of every view when None (outputs then shaped [V,H,W,...]).
 
     The scene's Gaussians pass the floater filter of Section II-C first (as
     the device scene does when built with use_filter); opacity defaults to 1.
-    Returns rgb, depth, alpha, ncontrib, flags and cond (see raster.c)."""
+    Returns rgb, depth, alpha, ncontrib, flags, cond and slack (see raster.c)."""
     lib = _load()
     means = np.ascontiguousarray(scene["means"], np.float32).reshape(-1, 3)
     op = scene.get("opacity")
@@ -106,12 +106,14 @@ def render(scene, colors, cams, width: int, height: int, *, near_plane: float = 
     ncontrib = np.zeros(P, np.int32)
     flags = np.zeros(P, np.int32)
     cond = np.zeros(P)
+    slack = np.zeros(P)
     rc = lib.orc_render_pixels(means_k.shape[0], _p(means_k), _p(sig_k), _p(op_k), _p(col_k), V, _p(cams),
                                ctypes.byref(d), P, _p(pixels), _p(rgb), _p(depth), _p(alpha), _p(ncontrib),
-                               _p(flags), _p(cond))
+                               _p(flags), _p(cond), _p(slack))
     if rc != 0:
         raise MemoryError("oracle render: allocation failed")
-    out = {"rgb": rgb, "depth": depth, "alpha": alpha, "ncontrib": ncontrib, "flags": flags, "cond": cond}
+    out = {"rgb": rgb, "depth": depth, "alpha": alpha, "ncontrib": ncontrib, "flags": flags, "cond": cond,
+           "slack": slack}
     if full:
         out = {k: a.reshape((V, height, width) + a.shape[1:]) for k, a in out.items()}
     return out

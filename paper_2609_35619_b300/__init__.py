@@ -185,6 +185,39 @@ class Scene:
     def sync(self, stream=None):
         check(abi.cs_sync(self._h, stream))
 
+    def set_appearance(self, opacity=None, colors=None, *, stream=None):
+        """cs_scene_set_appearance: per input row its opacity ([n], default 1)
+        and RGB colour ([n,3], default white), used by render()."""
+        o = None if opacity is None else _as_f32(opacity, self.device).reshape(-1)
+        c = None if colors is None else _as_f32(colors, self.device).reshape(-1, 3)
+        check(abi.cs_scene_set_appearance(self._h, o, c, 1 if self.device.type == "cuda" else 0, stream))
+
+    def render(self, cams, width: int, height: int, *, near_plane: float = 0.01, dilation: float = 0.3,
+               background=(0.0, 0.0, 0.0), want_depth: bool = True, want_alpha: bool = True, stream=None,
+               out=None) -> dict:
+        """cs_render (Section II-A, Eq. 3-4): images of the scene from the
+        cameras ([V,16] float32 rows: world-to-camera R row-major, t, fx, fy,
+        cx, cy).  Returns device tensors rgb [V,H,W,3] and, if wanted, depth
+        and alpha [V,H,W]."""
+        torch = _torch()
+        cams = _as_f32(cams, self.device).reshape(-1, 16)
+        V = cams.shape[0]
+        if out is None:
+            out = {"rgb": torch.empty((V, height, width, 3), dtype=torch.float32, device=self.device)}
+            if want_depth:
+                out["depth"] = torch.empty((V, height, width), dtype=torch.float32, device=self.device)
+            if want_alpha:
+                out["alpha"] = torch.empty((V, height, width), dtype=torch.float32, device=self.device)
+        d = abi.cs_render_desc()
+        check(abi.cs_render_desc_init(d))
+        d.n_views, d.width, d.height = V, int(width), int(height)
+        d.near_plane, d.dilation = float(near_plane), float(dilation)
+        for k in range(3):
+            d.background[k] = float(background[k])
+        d.stream = abi.stream_handle(stream)
+        check(abi.cs_render(self._h, d, cams, out["rgb"], out.get("depth"), out.get("alpha")))
+        return out
+
     def autotune(self, prims, nsigma=1.0, *, prim_type=CS_PRIM_SPHERE, params: QueryParams | None = None,
                  reps: int = 3, stream=None):
         """cs_autotune on a device batch: returns (best tile id, {id: ms})."""

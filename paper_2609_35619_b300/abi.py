@@ -156,6 +156,18 @@ class cs_rrt_desc(ctypes.Structure):
     ]
 
 
+class cs_render_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_views", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("near_plane", ctypes.c_float),
+        ("dilation", ctypes.c_float),
+        ("background", ctypes.c_float * 3),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 CS_TILE_TUNED = -1
 
 _P = ctypes.c_void_p
@@ -189,6 +201,9 @@ _SIGNATURES = {
                                     ctypes.POINTER(cs_params)]),
     "cs_rrt_extend": (ctypes.c_int, [_P, ctypes.POINTER(cs_rrt_desc), _P, _P, _P, _P, _P, _P,
                                      ctypes.POINTER(cs_params)]),
+    "cs_render_desc_init": (ctypes.c_int, [ctypes.POINTER(cs_render_desc)]),
+    "cs_scene_set_appearance": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
+    "cs_render": (ctypes.c_int, [_P, ctypes.POINTER(cs_render_desc), _P, _P, _P, _P]),
     "cs_server_config_init": (ctypes.c_int, [ctypes.POINTER(cs_server_config)]),
     "cs_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cs_server_config), ctypes.POINTER(_P)]),
     "cs_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(cs_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -367,6 +382,18 @@ def cs_mppi_step(scene, desc: cs_mppi_desc, x0, U, eps, U_out, cost, weights, co
 def cs_rrt_extend(scene, desc: cs_rrt_desc, nodes, parent, count, samples, nearest, edge_free, params) -> int:
     return load().cs_rrt_extend(scene, ctypes.byref(desc), ptr(nodes), ptr(parent), ptr(count), ptr(samples),
                                 ptr(nearest), ptr(edge_free), None if params is None else ctypes.byref(params))
+
+
+def cs_render_desc_init(desc: cs_render_desc) -> int:
+    return load().cs_render_desc_init(ctypes.byref(desc))
+
+
+def cs_scene_set_appearance(scene, opacity, colors, on_device, stream) -> int:
+    return load().cs_scene_set_appearance(scene, ptr(opacity), ptr(colors), int(on_device), stream_handle(stream))
+
+
+def cs_render(scene, desc: cs_render_desc, cams, rgb, depth, alpha) -> int:
+    return load().cs_render(scene, ctypes.byref(desc), ptr(cams), ptr(rgb), ptr(depth), ptr(alpha))
 
 
 def cs_server_config_init(cfg: cs_server_config) -> int:

@@ -54,7 +54,7 @@ constexpr int64_t kMaxRows = (int64_t)1 << 30;
 static void free_ws(Workspace *w) {
     void *ptrs[] = {w->keys[0], w->keys[1], w->vals[0], w->vals[1], w->sort_hist, w->scan_tmp,
                     w->qrec, w->qns, w->io_prims, w->io_ns, w->io_metric, w->io_collide,
-                    w->io_count, w->io_grad, w->io_gout, w->io_gm, w->io_gc, w->mppi, w->rrt, w->err};
+                    w->io_count, w->io_grad, w->io_gout, w->io_gm, w->io_gc, w->mppi, w->rrt, w->rnd, w->rnd2, w->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete w;
@@ -235,6 +235,7 @@ cs_status cs_scene_destroy(cs_scene *s) {
     Scene *sc = reinterpret_cast<Scene *>(s);
     sc->magic = 0;
     for (int i = 0; i < sc->nblocks; ++i) cudaFree(sc->blocks[i]);
+    if (sc->app) cudaFree(sc->app);
     delete sc;
     return CS_OK;
 }

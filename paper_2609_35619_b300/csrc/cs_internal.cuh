@@ -111,6 +111,9 @@ struct Workspace {
     float *mppi = nullptr;           size_t cap_mppi = 0;  // floats
     // RRT extension scratch (cs_rrt_extend): edge points, nearest, new nodes, edge flags
     float *rrt = nullptr;            size_t cap_rrt = 0;   // floats
+    // rendering scratch (cs_render): projections, instance lists, sort buffers
+    void *rnd = nullptr;             size_t cap_rnd = 0;   // bytes: per (view, slot)
+    void *rnd2 = nullptr;            size_t cap_rnd2 = 0;  // bytes: per instance
     unsigned *err = nullptr;         // device error word
 };
 
@@ -121,6 +124,7 @@ struct Scene {
     std::unordered_map<uint32_t, int32_t> tuned;
     int64_t n_input = 0, n_kept = 0, n_grid = 0, n_large = 0, n_invalid = 0;
     int64_t device_bytes = 0;
+    float4 *app = nullptr;           // per slot (opacity, r, g, b) for rendering (cs_scene_set_appearance)
     void *blocks[8] = {};            // owned device allocations
     int nblocks = 0;
     int device = 0;
