@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=3, help="server batch slots in --case serve")
     ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
     ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
-    ap.add_argument("--case", default="step", choices=["step", "eval", "serve", "mppi", "rrt", "variants"],
+    ap.add_argument("--case", default="step",
+                    choices=["step", "eval", "serve", "mppi", "rrt", "variants", "render"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
                          "(two fused-kernel launches); prints a short JSON summary. "
@@ -333,6 +334,7 @@ def run_ours(args, rank, world):
         result["mppi"] = run_mppi(torch, cs, dev)
         result["rrt"] = run_rrt(torch, cs, dev)
         result["variants"] = run_variants(torch, cs, dev)
+        result["render"] = run_render(torch, cs, dev)
     return result
 
 
@@ -699,6 +701,43 @@ def run_variants(torch, cs, dev, iters=5):
                         "229,376 link ellipsoids; n_sigma 1; default tile shapes", **out}
 
 
+RENDER_WORKLOAD = ("drone room 500k Gaussians; the terminal states of 256 MPPI rollouts rendered at "
+                   "128 x 128 (near plane 0.2 m), RGB + depth + alpha, one call per batch")
+
+
+def run_render(torch, cs, dev, iters=10, views=256, width=128, height=128):
+    """Batched image synthesis (Eq. 3-4): `views` terminal-state images of
+    the drone room per call, timed with CUDA events on the stream around each
+    call (the call waits for the stream once, mid-way, to size its instance
+    list), after two warm-up calls."""
+    import cs_synth as S
+    sc = S.drone_scene()
+    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    scene.set_appearance(sc["opacity"], S.scene_colors(sc))
+    cams = torch.as_tensor(S.drone_terminal_cameras(rollouts=views, width=width, height=height), device=dev)
+    out = None
+    for _ in range(2):
+        out = scene.render(cams, width, height, near_plane=0.2, out=out)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    l0 = cs.abi.cs_launch_count()
+    for a, b in evs:
+        a.record()
+        scene.render(cams, width, height, near_plane=0.2, out=out)
+        b.record()
+    torch.cuda.synchronize(dev)
+    ms = sorted(a.elapsed_time(b) for a, b in evs)
+    med = ms[len(ms) // 2]
+    res = {"workload": RENDER_WORKLOAD, "views": views, "width": width, "height": height,
+           "ms_per_call": med, "ms_min": ms[0], "images_per_s": views * 1e3 / med,
+           "pixels_per_s": views * width * height * 1e3 / med,
+           "kernels_per_call": (cs.abi.cs_launch_count() - l0) / iters,
+           "instances": scene.last_render_instances,
+           "mean_alpha": float(out["alpha"].mean().item())}
+    scene.close()
+    return res
+
+
 def run_rrt_case(args):
     import torch
 
@@ -834,6 +873,14 @@ def main():
         return
     if args.case == "mppi":
         run_mppi_case(args)
+        return
+    if args.case == "render":
+        import torch
+
+        import paper_2609_35619_b300 as cs
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"case": "render", **run_render(torch, cs, dev, iters=max(args.steps, 1))}))
         return
     if args.case == "variants":
         import torch

@@ -544,6 +544,8 @@ typedef struct cs_render_desc {
     float dilation;        /* px^2 added to the diagonal of Sigma', >= 0 (default 0.3) */
     float background[3];   /* colour behind the Gaussians (default 0, 0, 0) */
     void *stream;          /* cudaStream_t */
+    int64_t *out_instances;/* optional host pointer: receives the number of (view, Gaussian,
+                              tile) instances the call blended from */
 } cs_render_desc;
 
 CS_API cs_status cs_render_desc_init(cs_render_desc *desc);

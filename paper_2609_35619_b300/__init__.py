@@ -215,7 +215,10 @@ class Scene:
         for k in range(3):
             d.background[k] = float(background[k])
         d.stream = abi.stream_handle(stream)
+        n_inst = ctypes.c_int64(0)
+        d.out_instances = ctypes.pointer(n_inst)
         check(abi.cs_render(self._h, d, cams, out["rgb"], out.get("depth"), out.get("alpha")))
+        self.last_render_instances = int(n_inst.value)
         return out
 
     def autotune(self, prims, nsigma=1.0, *, prim_type=CS_PRIM_SPHERE, params: QueryParams | None = None,

@@ -165,6 +165,7 @@ class cs_render_desc(ctypes.Structure):
         ("dilation", ctypes.c_float),
         ("background", ctypes.c_float * 3),
         ("stream", ctypes.c_void_p),
+        ("out_instances", ctypes.POINTER(ctypes.c_int64)),
     ]
 
 

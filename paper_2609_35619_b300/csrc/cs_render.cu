@@ -44,12 +44,14 @@ struct RenderConsts {
 };
 
 // Projected Gaussian, three float4 per (view, slot):
-//   (u, v, pa, pb) (pc, opacity, distance, depth) (r, g, b, tile rect)
+//   (u, v, pa, pb) (pc, opacity, distance, x range) (r, g, b, y range)
 // with 2^-(pa dx^2 + pb dx dy + pc dy^2) = G2D at offset (dx, dy), and the
-// tile rect packed as tx0 | ty0 << 8 | tx1 << 16 | ty1 << 24.
+// pixel columns / rows its footprint can touch packed as lo | hi << 16; the
+// float32 depth (the sort key) goes to its own array.
 __global__ void __launch_bounds__(256) k_rs_project(SceneDev sc, const float4 *__restrict__ app,
                                                     const cs_camera *__restrict__ cams, RenderConsts rc,
-                                                    float4 *__restrict__ proj, uint32_t *__restrict__ ntile,
+                                                    float4 *__restrict__ proj, float *__restrict__ zkey,
+                                                    uint32_t *__restrict__ ntile,
                                                     unsigned long long *__restrict__ total) {
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -99,23 +101,27 @@ __global__ void __launch_bounds__(256) k_rs_project(SceneDev sc, const float4 *_
             const float det = fmaf(A, C, -(Bc * Bc));
             if (det > 0.f) {
                 // footprint: alpha G >= 1/255 <=> q <= 2 ln(255 alpha); its box has
-                // half-extents sqrt(q Sigma'_xx), sqrt(q Sigma'_yy) (padded)
+                // half-extents sqrt(q Sigma'_xx), sqrt(q Sigma'_yy).  The box is
+                // widened by the FP32 error of q and of Sigma' (relative, at most
+                // ~40 u kappa with kappa the condition number of Sigma'), so every
+                // pixel the blending can draw lies inside it.
+                const float tr = 0.5f * (A + C), disc = sqrtf(fmaf(0.25f * (A - C), A - C, Bc * Bc));
+                const float lmax = tr + disc, kap = lmax * lmax / det;  // lmax / lmin, lmin = det / lmax
+                const float grow = fmaf(40.f * 5.9604645e-8f, kap, 1.0001f);
                 const float qmax = fmaxf(2.f * logf(255.f * ap.x), 0.f);
-                const float rx = fmaf(sqrtf(qmax * A), 1.01f, 1.f), ry = fmaf(sqrtf(qmax * C), 1.01f, 1.f);
-                const float inv = 1.f / (float)kTile;
-                const float fx0 = fmaxf(floorf((u - rx - 0.5f) * inv), 0.f);
-                const float fx1 = fminf(floorf((u + rx - 0.5f) * inv), (float)(rc.tiles_x - 1));
-                const float fy0 = fmaxf(floorf((vv - ry - 0.5f) * inv), 0.f);
-                const float fy1 = fminf(floorf((vv + ry - 0.5f) * inv), (float)(rc.tiles_y - 1));
+                const float rx = fmaf(sqrtf(qmax * A), grow, 1e-3f), ry = fmaf(sqrtf(qmax * C), grow, 1e-3f);
+                // pixel i is touched when |i + 0.5 - u| <= rx
+                const float fx0 = fmaxf(ceilf(u - rx - 0.5f), 0.f), fx1 = fminf(floorf(u + rx - 0.5f), (float)(rc.W - 1));
+                const float fy0 = fmaxf(ceilf(vv - ry - 0.5f), 0.f), fy1 = fminf(floorf(vv + ry - 0.5f), (float)(rc.H - 1));
                 if (fx0 <= fx1 && fy0 <= fy1) {
-                    const uint32_t tx0 = (uint32_t)fx0, tx1 = (uint32_t)fx1, ty0 = (uint32_t)fy0, ty1 = (uint32_t)fy1;
-                    n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+                    const uint32_t x0 = (uint32_t)fx0, x1 = (uint32_t)fx1, y0 = (uint32_t)fy0, y1 = (uint32_t)fy1;
+                    n = ((x1 >> 4) - (x0 >> 4) + 1) * ((y1 >> 4) - (y0 >> 4) + 1);
                     const float id = 1.f / det;
                     const float dist = sqrtf(fmaf(zz, zz, fmaf(yc, yc, xc * xc)));
-                    const uint32_t rect = tx0 | (ty0 << 8) | (tx1 << 16) | (ty1 << 24);
                     proj[3 * g + 0] = make_float4(u, vv, C * id * kHalfLog2e, -2.f * Bc * id * kHalfLog2e);
-                    proj[3 * g + 1] = make_float4(A * id * kHalfLog2e, ap.x, dist, zz);
-                    proj[3 * g + 2] = make_float4(ap.y, ap.z, ap.w, __uint_as_float(rect));
+                    proj[3 * g + 1] = make_float4(A * id * kHalfLog2e, ap.x, dist, __uint_as_float(x0 | (x1 << 16)));
+                    proj[3 * g + 2] = make_float4(ap.y, ap.z, ap.w, __uint_as_float(y0 | (y1 << 16)));
+                    zkey[g] = zz;
                 }
             }
         }
@@ -128,8 +134,9 @@ __global__ void __launch_bounds__(256) k_rs_project(SceneDev sc, const float4 *_
 }
 
 // One instance per (view, Gaussian, tile), in (view, slot, tile) order.
-__global__ void k_rs_emit(const float4 *__restrict__ proj, const uint32_t *__restrict__ ntile,
-                          const uint32_t *__restrict__ offs, RenderConsts rc, size_t VS,
+__global__ void k_rs_emit(const float4 *__restrict__ proj, const float *__restrict__ zkey,
+                          const uint32_t *__restrict__ ntile, const uint32_t *__restrict__ offs, RenderConsts rc,
+                          size_t VS,
                           uint32_t *__restrict__ dkey, uint32_t *__restrict__ ival, uint32_t *__restrict__ tkey,
                           uint32_t *__restrict__ iproj) {
     const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,9 +144,9 @@ __global__ void k_rs_emit(const float4 *__restrict__ proj, const uint32_t *__res
     const uint32_t n = ntile[g];
     if (n == 0) return;
     const uint32_t base = offs[g];
-    const uint32_t zbits = __float_as_uint(proj[3 * g + 1].w);
-    const uint32_t rect = __float_as_uint(proj[3 * g + 2].w);
-    const uint32_t tx0 = rect & 0xFFu, ty0 = (rect >> 8) & 0xFFu, tx1 = (rect >> 16) & 0xFFu, ty1 = rect >> 24;
+    const uint32_t zbits = __float_as_uint(zkey[g]);
+    const uint32_t xr = __float_as_uint(proj[3 * g + 1].w), yr = __float_as_uint(proj[3 * g + 2].w);
+    const uint32_t tx0 = (xr & 0xFFFFu) >> 4, tx1 = (xr >> 16) >> 4, ty0 = (yr & 0xFFFFu) >> 4, ty1 = (yr >> 16) >> 4;
     const uint32_t tbase = (uint32_t)(g / rc.S) * (uint32_t)rc.T;
     uint32_t i = base;
     for (uint32_t ty = ty0; ty <= ty1; ++ty)
@@ -182,6 +189,7 @@ __global__ void __launch_bounds__(256) k_rs_render(const uint2 *__restrict__ ran
     const bool inside = px < rc.W && py < rc.H;
     const uint2 r = ranges[(size_t)v * rc.T + tile];
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const uint32_t row0 = (uint32_t)(ty * kTile + 2 * (threadIdx.x >> 5));  // this warp's two rows
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
     bool done = !inside;
     for (uint32_t start = r.x; start < r.y; start += 256) {
@@ -197,6 +205,10 @@ __global__ void __launch_bounds__(256) k_rs_render(const uint2 *__restrict__ ran
         const int n = (int)min(256u, r.y - start);
         if (!done) {
             for (int k = 0; k < n; ++k) {
+                const float4 c2 = s2[k];
+                // the whole warp skips a Gaussian whose footprint misses its two rows
+                const uint32_t yr = __float_as_uint(c2.w);
+                if ((yr & 0xFFFFu) > row0 + 1 || (yr >> 16) < row0) continue;
                 const float4 a = s0[k], b = s1[k];
                 const float dx = fx - a.x, dy = fy - a.y;
                 const float power = fmaf(a.z, dx * dx, fmaf(a.w, dx * dy, b.x * (dy * dy)));
@@ -209,10 +221,9 @@ __global__ void __launch_bounds__(256) k_rs_render(const uint2 *__restrict__ ran
                     break;
                 }
                 const float w = al * T;
-                const float4 col = s2[k];
-                cr = fmaf(w, col.x, cr);
-                cg = fmaf(w, col.y, cg);
-                cb = fmaf(w, col.z, cb);
+                cr = fmaf(w, c2.x, cr);
+                cg = fmaf(w, c2.y, cg);
+                cb = fmaf(w, c2.z, cb);
                 dd = fmaf(w, b.z, dd);
                 T = Tn;
             }
@@ -365,19 +376,21 @@ cs_status cs_render(const cs_scene *scene, const cs_render_desc *d, const cs_cam
     Workspace *w = nullptr;
     if ((st = get_workspace(sc->device, s, 1, false, &w)) != CS_OK) return st;
     // per (view, slot): projections, tile counts, their scan, the instance total
-    const size_t o_ntile = align256(48 * VS), o_offs = align256(o_ntile + 4 * VS), o_total = align256(o_offs + 4 * VS);
+    const size_t o_zkey = align256(48 * VS), o_ntile = align256(o_zkey + 4 * VS), o_offs = align256(o_ntile + 4 * VS);
+    const size_t o_total = align256(o_offs + 4 * VS);
     const size_t o_scan = align256(o_total + 8);
     const size_t need1 = o_scan + 4 * scan_tmp_elems(std::max<size_t>(VS, 1));
     if ((st = ensure(&w->rnd, &w->cap_rnd, need1)) != CS_OK) return st;
     char *b1 = (char *)w->rnd;
     float4 *proj = (float4 *)b1;
+    float *zkey = (float *)(b1 + o_zkey);
     uint32_t *ntile = (uint32_t *)(b1 + o_ntile), *offs = (uint32_t *)(b1 + o_offs);
     unsigned long long *total = (unsigned long long *)(b1 + o_total);
     uint32_t *scan1 = (uint32_t *)(b1 + o_scan);
     CS_CUDA(cudaMemsetAsync(total, 0, 8, s));
     if (VS > 0) {
         k_rs_project<<<dim3((unsigned)((rc.nchunks + 7) / 8), (unsigned)rc.V), 256, 0, s>>>(dv, sc->app, cams, rc, proj,
-                                                                                          ntile, total);
+                                                                                          zkey, ntile, total);
         count_launches(1);
         CS_CUDA(cudaGetLastError());
         scan_exclusive(ntile, offs, VS, scan1, s);
@@ -390,6 +403,7 @@ cs_status cs_render(const cs_scene *scene, const cs_render_desc *d, const cs_cam
         return CS_ERR_UNSUPPORTED;
     }
     const size_t I = (size_t)I64;
+    if (d->out_instances) *d->out_instances = (int64_t)I64;
 
     // per instance: two key and two value buffers, tile keys, projection
     // indices (unsorted and sorted), tile ranges, sort scratch
@@ -406,8 +420,8 @@ cs_status cs_render(const cs_scene *scene, const cs_render_desc *d, const cs_cam
     uint32_t *hist = (uint32_t *)(b2 + o_hist), *scan2 = (uint32_t *)(b2 + o_scan2);
     CS_CUDA(cudaMemsetAsync(ranges, 0, 8 * VT, s));
     if (I > 0) {
-        k_rs_emit<<<(unsigned)((VS + 255) / 256), 256, 0, s>>>(proj, ntile, offs, rc, VS, dkey[0], ival[0], tkey,
-                                                               iproj);
+        k_rs_emit<<<(unsigned)((VS + 255) / 256), 256, 0, s>>>(proj, zkey, ntile, offs, rc, VS, dkey[0], ival[0],
+                                                               tkey, iproj);
         count_launches(1);
         const int r1 = radix_sort(dkey, ival, I, 32, hist, scan2, s);
         k_rs_gather<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(ival[r1], tkey, (uint32_t)I, dkey[r1 ^ 1]);
