@@ -504,6 +504,46 @@ CS_API double cs_server_clock(void);
  * progress.  NULL is a no-op. */
 CS_API cs_status cs_server_destroy(cs_server *server);
 
+/* Zeroth-order path refinement (Section III): the RRT path smoothed by one
+ * MPPI step (Section II-D) whose horizon is the whole plan, over the control
+ * points ("knots") of a clamped uniform cubic B-spline through it.
+ *   - the curve: the control points P_0 .. P_{N-1} padded with two more
+ *     copies of each endpoint (so it starts at P_0 and ends at P_{N-1}),
+ *     N + 1 segments of the uniform cubic basis, each sampled at u = m / M,
+ *     m < M, plus the last point: (N + 1) M + 1 spheres of `radius`;
+ *   - rollout k moves the interior control points by eps[k] (the endpoints
+ *     stay fixed; their perturbations are ignored);
+ *   - cost C^k = w_length * (length of the polyline through the samples) +
+ *     w_collision * (sum over the samples of the Eq. 11 cost averaged over
+ *     the neighbour set);
+ *   - Eq. 10 weights w^k and the update P' = P + sum_k w^k eps[k] (interior).
+ * The sample points are computed in float32 with every operation rounded in
+ * a fixed order:
+ *     u = m / M, u2 = u u, u3 = u2 u, v = 1 - u;
+ *     b0 = ((v v) v) / 6, b1 = ((3 u3 - 6 u2) + 4) / 6,
+ *     b2 = (((3 u2 - 3 u3) + 3 u) + 1) / 6, b3 = u3 / 6;
+ *     x = ((b0 Q0 + b1 Q1) + b2 Q2) + b3 Q3,
+ * so they are reproducible exactly. */
+typedef struct cs_refine_desc {
+    int32_t K;          /* perturbed paths, [1, 2^20] */
+    int32_t N;          /* control points, [2, 4096] */
+    int32_t M;          /* samples per spline segment, [1, 256] */
+    float radius;       /* robot sphere radius, > 0 */
+    float nsigma;       /* conservatism n_sigma, >= 0 */
+    float lambda;       /* Eq. 10 temperature, > 0 */
+    float w_length;     /* >= 0 */
+    float w_collision;  /* >= 0 */
+} cs_refine_desc;
+
+/* One refinement step on device buffers: ctrl [N,3], eps [K,N,3] (the
+ * caller draws the perturbations), ctrl_out [N,3] (may not alias ctrl or
+ * eps); cost and weights [K] optional (NULL: not returned).  params as for
+ * cs_query (mode, group_size and the output pointers are set by the call;
+ * host_io must be 0).  Scratch comes from the stream's pool. */
+CS_API cs_status cs_path_refine(const cs_scene *scene, const cs_refine_desc *desc, const float *ctrl,
+                                const float *eps, float *ctrl_out, float *cost, float *weights,
+                                const cs_params *params);
+
 /* ---------------------------------------------------------------------------
  * Image synthesis (Section II-A, Eq. 3-4), the terminal-state images of
  * Section II-D: the scene's kept Gaussians are projected into pinhole cameras

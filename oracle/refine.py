@@ -74,18 +74,21 @@ def basis32(m, M):
 
 
 def points(ctrl, M):
-    """The (N + 1) M + 1 sample points of the clamped spline of ctrl [N,3]
-    (float32 in, float32 out, the stated operation order)."""
+    """The (N + 1) M + 1 sample points of the clamped spline of ctrl [N,3], or
+    of a batch [K,N,3] (float32 in, float32 out, the stated operation order)."""
     P = np.asarray(ctrl, np.float32)
-    Q = np.concatenate([P[:1], P[:1], P, P[-1:], P[-1:]])
-    N = P.shape[0]
-    out = np.empty(((N + 1) * M + 1, 3), np.float32)
+    single = P.ndim == 2
+    if single:
+        P = P[None]
+    Q = np.concatenate([P[:, :1], P[:, :1], P, P[:, -1:], P[:, -1:]], axis=1)
+    K, N = P.shape[0], P.shape[1]
+    out = np.empty((K, (N + 1) * M + 1, 3), np.float32)
     for m in range(M):
         b0, b1, b2, b3 = basis32(m, M)
-        for j in range(N + 1):
-            out[j * M + m] = ((b0 * Q[j] + b1 * Q[j + 1]) + b2 * Q[j + 2]) + b3 * Q[j + 3]
-    out[-1] = P[-1]
-    return out
+        seg = ((b0 * Q[:, 0:N + 1] + b1 * Q[:, 1:N + 2]) + b2 * Q[:, 2:N + 3]) + b3 * Q[:, 3:N + 4]
+        out[:, m:(N + 1) * M:M] = seg
+    out[:, -1] = P[:, -1]
+    return out[0] if single else out
 
 
 def refine(scene, ctrl, eps, d: RefineDesc, params: Params | None = None) -> dict:
@@ -95,7 +98,7 @@ def refine(scene, ctrl, eps, d: RefineDesc, params: Params | None = None) -> dic
     eps32 = np.array(eps, np.float32)
     eps32[:, 0, :] = 0.0
     eps32[:, -1, :] = 0.0
-    pts = np.stack([points(ctrl32 + eps32[k], d.M) for k in range(d.K)])   # [K,P,3] float32
+    pts = points(ctrl32[None] + eps32, d.M)   # [K,P,3] float32
     P = pts.shape[1]
     length = np.linalg.norm(np.diff(pts.astype(np.float64), axis=1), axis=2).sum(1)
     sph = np.c_[pts.reshape(-1, 3), np.full(d.K * P, d.radius, np.float32)].astype(np.float32)
@@ -106,7 +109,7 @@ def refine(scene, ctrl, eps, d: RefineDesc, params: Params | None = None) -> dic
     w = e / e.sum()
     new = ctrl32.astype(np.float64) + np.einsum("k,knd->nd", w, eps32.astype(np.float64))
     return {"ctrl": new, "cost": cost, "weights": w, "length": length, "collision": col, "points": pts,
-            "band_in": res["band_in"].reshape(d.K, P), "band_cut": res["band_cut"].reshape(d.K, P)}
+            "query": res}
 
 
 __all__ = ["RefineDesc", "basis", "basis32", "points", "refine"]

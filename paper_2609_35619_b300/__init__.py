@@ -409,6 +409,28 @@ def mppi_step(scene: Scene, x0, U, eps, *, dt=0.1, radius=0.15, nsigma=1.0, lam=
     return out
 
 
+def path_refine(scene: Scene, ctrl, eps, *, M=8, radius=0.05, nsigma=1.0, lam=1.0, w_length=1.0,
+                w_collision=10.0, params: QueryParams | None = None, stream=None, out=None) -> dict:
+    """cs_path_refine on device tensors: the control points ctrl [N,3] of a
+    plan, eps [K,N,3] perturbations (endpoints ignored).  Returns the
+    refined control points, per-rollout cost and Eq. 10 weights."""
+    torch = _torch()
+    dev = scene.device
+    ctrl = _as_f32(ctrl, dev).reshape(-1, 3)
+    N = ctrl.shape[0]
+    eps = _as_f32(eps, dev).reshape(-1, N, 3)
+    K = eps.shape[0]
+    if out is None:
+        out = {"ctrl": torch.empty((N, 3), dtype=torch.float32, device=dev),
+               "cost": torch.empty(K, dtype=torch.float32, device=dev),
+               "weights": torch.empty(K, dtype=torch.float32, device=dev)}
+    d = abi.cs_refine_desc(K, N, M, radius, nsigma, lam, w_length, w_collision)
+    p = (params or QueryParams()).to_c()
+    p.stream = abi.stream_handle(stream)
+    check(abi.cs_path_refine(scene.handle, d, ctrl, eps, out["ctrl"], out.get("cost"), out.get("weights"), p))
+    return out
+
+
 class MppiGraph:
     """One MPPI iteration captured into a CUDA graph (cs_mppi_graph_create)
     over fixed device tensors x0 [3], U [T,3], eps [K,T,3]; each launch()

@@ -156,6 +156,19 @@ class cs_rrt_desc(ctypes.Structure):
     ]
 
 
+class cs_refine_desc(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("radius", ctypes.c_float),
+        ("nsigma", ctypes.c_float),
+        ("lam", ctypes.c_float),
+        ("w_length", ctypes.c_float),
+        ("w_collision", ctypes.c_float),
+    ]
+
+
 class cs_render_desc(ctypes.Structure):
     _fields_ = [
         ("n_views", ctypes.c_int32),
@@ -202,6 +215,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(cs_params)]),
     "cs_rrt_extend": (ctypes.c_int, [_P, ctypes.POINTER(cs_rrt_desc), _P, _P, _P, _P, _P, _P,
                                      ctypes.POINTER(cs_params)]),
+    "cs_path_refine": (ctypes.c_int, [_P, ctypes.POINTER(cs_refine_desc), _P, _P, _P, _P, _P,
+                                      ctypes.POINTER(cs_params)]),
     "cs_render_desc_init": (ctypes.c_int, [ctypes.POINTER(cs_render_desc)]),
     "cs_scene_set_appearance": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P]),
     "cs_render": (ctypes.c_int, [_P, ctypes.POINTER(cs_render_desc), _P, _P, _P, _P]),
@@ -383,6 +398,11 @@ def cs_mppi_step(scene, desc: cs_mppi_desc, x0, U, eps, U_out, cost, weights, co
 def cs_rrt_extend(scene, desc: cs_rrt_desc, nodes, parent, count, samples, nearest, edge_free, params) -> int:
     return load().cs_rrt_extend(scene, ctypes.byref(desc), ptr(nodes), ptr(parent), ptr(count), ptr(samples),
                                 ptr(nearest), ptr(edge_free), None if params is None else ctypes.byref(params))
+
+
+def cs_path_refine(scene, desc: cs_refine_desc, ctrl, eps, ctrl_out, cost, weights, params) -> int:
+    return load().cs_path_refine(scene, ctypes.byref(desc), ptr(ctrl), ptr(eps), ptr(ctrl_out), ptr(cost),
+                                 ptr(weights), None if params is None else ctypes.byref(params))
 
 
 def cs_render_desc_init(desc: cs_render_desc) -> int:

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <math.h>
+#include <string.h>
 
 #include "cs_internal.cuh"
 
@@ -25,6 +26,7 @@ struct MppiConsts {
     float dt, radius;
     float w_collision, w_goal, w_terminal, w_control, lambda;
     float gx, gy, gz;
+    int fixed_ends;  // path refinement: the first and last rows of U stay
 };
 
 constexpr int kWeightThreads = 1024;
@@ -102,7 +104,66 @@ __global__ void k_mppi_update(const float *__restrict__ U, const float *__restri
     for (int k = lane; k < c.K; k += 32) s = fmaf(w[k], eps[(size_t)k * c.T * 3 + o], s);
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    if (lane == 0) U_out[o] = U[o] + s;
+    const bool fixed = c.fixed_ends && (o < 3 || o >= 3 * (c.T - 1));
+    if (lane == 0) U_out[o] = fixed ? U[o] : U[o] + s;
+}
+
+// Path refinement: one thread per (rollout, spline segment) writes the
+// segment's M sample spheres (the stated float32 operation order); the
+// rollout's last thread also writes the end point.
+__global__ void k_refine_points(const float *__restrict__ ctrl, const float *__restrict__ eps, int K, int N,
+                                int M, float radius, float4 *__restrict__ spheres) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)K * (N + 1)) return;
+    const int k = (int)(t / (N + 1)), j = (int)(t % (N + 1));
+    const int P = (N + 1) * M + 1;
+    // padded control points j .. j + 3 -> control index clamp(j + i - 2, 0, N - 1)
+    float q[4][3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int n = min(max(j + i - 2, 0), N - 1);
+        const bool end = n == 0 || n == N - 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float e = end ? 0.f : eps[((size_t)k * N + n) * 3 + a];
+            q[i][a] = __fadd_rn(ctrl[3 * n + a], e);
+        }
+    }
+    float4 *out = spheres + (size_t)k * P + (size_t)j * M;
+    for (int m = 0; m < M; ++m) {
+        const float u = __fdiv_rn((float)m, (float)M);
+        const float u2 = __fmul_rn(u, u), u3 = __fmul_rn(u2, u), v = __fsub_rn(1.f, u);
+        const float b0 = __fdiv_rn(__fmul_rn(__fmul_rn(v, v), v), 6.f);
+        const float b1 = __fdiv_rn(__fadd_rn(__fsub_rn(__fmul_rn(3.f, u3), __fmul_rn(6.f, u2)), 4.f), 6.f);
+        const float b2 = __fdiv_rn(
+            __fadd_rn(__fadd_rn(__fsub_rn(__fmul_rn(3.f, u2), __fmul_rn(3.f, u3)), __fmul_rn(3.f, u)), 1.f), 6.f);
+        const float b3 = __fdiv_rn(u3, 6.f);
+        float x[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            x[a] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(b0, q[0][a]), __fmul_rn(b1, q[1][a])), __fmul_rn(b2, q[2][a])),
+                             __fmul_rn(b3, q[3][a]));
+        out[m] = make_float4(x[0], x[1], x[2], radius);
+    }
+    if (j == N) spheres[(size_t)k * P + P - 1] = make_float4(ctrl[3 * (N - 1)], ctrl[3 * (N - 1) + 1],
+                                                             ctrl[3 * (N - 1) + 2], radius);
+}
+
+// One thread per rollout: w_length times the polyline length, in point order.
+__global__ void k_refine_length(const float4 *__restrict__ spheres, int K, int P, float w_length,
+                                float *__restrict__ tc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const float4 *p = spheres + (size_t)k * P;
+    float L = 0.f;
+    float4 a = p[0];
+    for (int i = 1; i < P; ++i) {
+        const float4 b = p[i];
+        const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+        L += sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+        a = b;
+    }
+    tc[k] = w_length * L;
 }
 
 }  // namespace
@@ -169,6 +230,7 @@ cs_status mppi_common(const cs_scene *scene, const cs_mppi_desc *d, const float 
     MppiConsts c;
     c.K = d->K;
     c.T = d->T;
+    c.fixed_ends = 0;
     c.dt = d->dt;
     c.radius = d->radius;
     c.w_collision = d->w_collision;
@@ -213,6 +275,77 @@ cs_status cs_mppi_step(const cs_scene *scene, const cs_mppi_desc *desc, const fl
                        const float *eps, float *U_out, float *cost, float *weights, uint8_t *collide,
                        const cs_params *params) {
     return mppi_common(scene, desc, x0, U, eps, U_out, cost, weights, collide, params, nullptr);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+cs_status cs_path_refine(const cs_scene *scene, const cs_refine_desc *d, const float *ctrl, const float *eps,
+                         float *ctrl_out, float *cost, float *weights, const cs_params *params) {
+    cs_status st = check_scene(scene);
+    if (st != CS_OK) return st;
+    if (!d) return invalid("desc is NULL");
+    if (d->K < 1 || d->K > (1 << 20)) return invalid("K must lie in [1, 2^20]");
+    if (d->N < 2 || d->N > 4096) return invalid("N must lie in [2, 4096]");
+    if (d->M < 1 || d->M > 256) return invalid("M must lie in [1, 256]");
+    const int64_t P = (int64_t)(d->N + 1) * d->M + 1;
+    if ((int64_t)d->K * P > ((int64_t)1 << 26)) return invalid("K * ((N + 1) M + 1) must not exceed 2^26");
+    if (!(d->radius > 0.f) || !isfinite(d->radius)) return invalid("radius must be finite and > 0");
+    if (!(d->nsigma >= 0.f) || !isfinite(d->nsigma)) return invalid("nsigma must be finite and >= 0");
+    if (!(d->lambda > 0.f) || !isfinite(d->lambda)) return invalid("lambda must be finite and > 0");
+    if (!(d->w_length >= 0.f) || !isfinite(d->w_length) || !(d->w_collision >= 0.f) || !isfinite(d->w_collision))
+        return invalid("cost weights must be finite and >= 0");
+    if (!ctrl || !eps || !ctrl_out) return invalid("ctrl, eps and ctrl_out are required");
+    if (ctrl_out == ctrl || ctrl_out == eps) return invalid("ctrl_out may not alias ctrl or eps");
+    cs_params p;
+    if (params) p = *params;
+    else cs_params_init(&p);
+    if (p.host_io) return invalid("cs_path_refine takes device buffers only (host_io must be 0)");
+    if ((st = check_params(p)) != CS_OK) return st;
+    const Scene *sc = reinterpret_cast<const Scene *>(scene);
+    cudaStream_t s = (cudaStream_t)p.stream;
+    const int64_t Q = (int64_t)d->K * P;
+
+    // scratch as for an MPPI iteration of K rollouts x P points
+    Workspace *w = nullptr;
+    if ((st = get_workspace(sc->device, s, (size_t)Q, false, &w)) != CS_OK) return st;
+    if ((st = mppi_reserve(w, d->K, P)) != CS_OK) return st;
+    float4 *spheres = reinterpret_cast<float4 *>(w->mppi);
+    float *col = w->mppi + 4 * Q, *tc = col + d->K;
+    float *c_out = cost ? cost : tc + d->K, *w_out = weights ? weights : c_out + d->K;
+
+    MppiConsts c;
+    memset(&c, 0, sizeof(c));
+    c.K = d->K;
+    c.T = d->N;
+    c.radius = d->radius;
+    c.w_collision = d->w_collision;
+    c.lambda = d->lambda;
+    c.fixed_ends = 1;
+    const int64_t nthr = (int64_t)d->K * (d->N + 1);
+    k_refine_points<<<(unsigned)((nthr + 127) / 128), 128, 0, s>>>(ctrl, eps, d->K, d->N, d->M, d->radius,
+                                                                   spheres);
+    k_refine_length<<<(d->K + 127) / 128, 128, 0, s>>>(spheres, d->K, (int)P, d->w_length, tc);
+    count_launches(2);
+    CS_CUDA(cudaGetLastError());
+    // the metric of every sample, mean cost per sample summed over the path
+    cs_params q = p;
+    q.mode = CS_METRIC_MEAN_COST;
+    q.group_size = (int32_t)P;
+    q.nsigma_per_query = nullptr;
+    q.out_count = nullptr;
+    q.out_group_metric = col;
+    q.out_group_collide = nullptr;
+    q.host_io = 0;
+    if ((st = query_common(scene, CS_PRIM_SPHERE, reinterpret_cast<const float *>(spheres), Q, d->nsigma, &q, false,
+                           nullptr, nullptr, nullptr, nullptr, w)) != CS_OK)
+        return st;
+    k_mppi_weights<<<1, kWeightThreads, 0, s>>>(col, tc, c, c_out, w_out);
+    k_mppi_update<<<(c.T * 3 * 32 + 255) / 256, 256, 0, s>>>(ctrl, eps, w_out, c, ctrl_out);
+    count_launches(2);
+    CS_CUDA(cudaGetLastError());
+    return CS_OK;
 }
 
 }  // extern "C"

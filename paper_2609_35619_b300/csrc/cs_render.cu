@@ -254,12 +254,14 @@ __global__ void k_rs_appearance(const int32_t *__restrict__ index, const int32_t
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Grow a scratch buffer to at least `need` bytes (by half again its old size
+// at least, so a slowly growing workload reallocates rarely).
 cs_status ensure(void **buf, size_t *cap, size_t need) {
     if (*cap >= need) return CS_OK;
+    const size_t grow = std::max(need, *cap + *cap / 2);
     if (*buf) CS_CUDA(cudaFree(*buf));
     *buf = nullptr;
     *cap = 0;
-    const size_t grow = std::max(need, *cap + *cap / 2);
     cudaError_t e = cudaMalloc(buf, grow);
     if (e != cudaSuccess) {
         *buf = nullptr;
