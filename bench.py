@@ -333,6 +333,7 @@ def run_ours(args, rank, world):
         result["served"] = run_served(torch, cs, dev, args.serve_requests)
         result["mppi"] = run_mppi(torch, cs, dev)
         result["rrt"] = run_rrt(torch, cs, dev)
+        result["refine"] = run_refine(torch, cs, dev)
         result["variants"] = run_variants(torch, cs, dev)
         result["render"] = run_render(torch, cs, dev)
     return result
@@ -757,6 +758,44 @@ def run_render(torch, cs, dev, iters=10, views=256, width=128, height=128):
            "kernels_per_call": (cs.abi.cs_launch_count() - l0) / iters,
            "instances": scene.last_render_instances,
            "mean_alpha": float(out["alpha"].mean().item())}
+    scene.close()
+    return res
+
+
+REFINE_WORKLOAD = ("drone room 500k Gaussians; one zeroth-order refinement step of a 32-control-point plan "
+                   "across the room: 1,024 perturbed B-splines x 8 samples per segment (270,336 spheres, "
+                   "r = 0.1 m, n_sigma 1)")
+
+
+def run_refine(torch, cs, dev, iters=20, K=1024, N=32, M=8):
+    """Zeroth-order path refinement (one MPPI step over the plan's B-spline
+    control points), timed with CUDA events over `iters` back-to-back steps,
+    inputs resident on the device."""
+    import cs_synth as S
+    sc = S.drone_scene()
+    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    rng = np.random.default_rng(1012)
+    a, b = np.array([0.8, 0.7, 1.2]), np.array([5.2, 4.3, 1.6])
+    t = np.linspace(0, 1, N)[:, None]
+    P = (a + t * (b - a) + np.r_[np.zeros((1, 3)), rng.normal(0, 0.2, (N - 2, 3)), np.zeros((1, 3))])
+    ctrl = torch.as_tensor(P.astype(np.float32), device=dev)
+    eps = torch.as_tensor(rng.normal(0, 0.1, (K, N, 3)).astype(np.float32), device=dev)
+    out = None
+    for _ in range(3):
+        out = cs.path_refine(scene, ctrl, eps, M=M, radius=0.1, out=out)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = cs.abi.cs_launch_count()
+    e0.record()
+    for _ in range(iters):
+        cs.path_refine(scene, ctrl, eps, M=M, radius=0.1, out=out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / iters
+    P_pts = (N + 1) * M + 1
+    res = {"workload": REFINE_WORKLOAD, "K": K, "N": N, "M": M, "ms_per_step": ms,
+           "samples_per_s": K * P_pts * 1e3 / ms,
+           "kernels_per_step": (cs.abi.cs_launch_count() - l0) / iters}
     scene.close()
     return res
 
