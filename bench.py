@@ -39,8 +39,8 @@ OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes
 # DRAM bytes (read + write) of one forward launch of the fused kernel, from the
 # ncu capture of that case summarised under profiles/, valid for the library
 # version it was taken with (reported as null otherwise)
-TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": 40.671e6 + 0.006e6,
-           "case": "262,144 arm spheres, tile 23, n_sigma 1"}
+TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": 42.114e6 + 0.038e6,
+           "case": "262,144 arm spheres, tile 22, n_sigma 1"}
 WORKLOAD = "tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres fwd+adjoint"
 
 
@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
     ap.add_argument("--flags", action="store_true", help="--case eval: collision flags only (early exit)")
+    ap.add_argument("--cell", type=float, default=0.0,
+                    help="--case eval: chunk extent limit of the scene build (0 = automatic)")
     ap.add_argument("--exact", action="store_true",
                     help="--case eval: exact variance of the quadratic form in Eq. 8 (cs_params.exact_variance)")
     return ap.parse_args()
@@ -889,7 +891,7 @@ def run_eval_case(args):
     sc = S.tabletop_scene()
     batches = {"arm": S.arm_queries, "edge": S.edge_queries, "arm_ellipsoids": S.arm_ellipsoids}
     arm = torch.as_tensor(batches[args.batch](), device=dev)
-    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev)
+    scene = cs.Scene(sc["means"], sc["scales"], sc["quats"], sc["opacity"], device=dev, cell_size=args.cell)
     G = {"arm": 64, "edge": 1024, "arm_ellipsoids": 7}[args.batch]
     prim = cs.CS_PRIM_ELLIPSOID if args.batch == "arm_ellipsoids" else cs.CS_PRIM_SPHERE
     qp = cs.QueryParams(group_size=G, tile_config=args.tile, exact_variance=args.exact,
