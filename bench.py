@@ -41,7 +41,8 @@ OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes
 # version it was taken with (reported as null otherwise)
 TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": 42.114e6 + 0.038e6,
            "case": "262,144 arm spheres, tile 22, n_sigma 1"}
-WORKLOAD = "tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres fwd+adjoint"
+WORKLOAD = ("tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres "
+            "fwd+adjoint (the arm sweep as one launch with n_sigma per row)")
 
 
 def parse():
@@ -74,6 +75,9 @@ def parse():
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
     ap.add_argument("--flags", action="store_true", help="--case eval: collision flags only (early exit)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="--case eval: the four n_sigma values of the step in one launch (rows repeated, n_sigma "
+                         "per row) against four separate launches")
     ap.add_argument("--cell", type=float, default=0.0,
                     help="--case eval: chunk extent limit of the scene build (0 = automatic)")
     ap.add_argument("--exact", action="store_true",
@@ -159,6 +163,11 @@ def run_ours(args, rank, world):
     with torch.cuda.stream(stream):
         d_scene = {k: torch.as_tensor(v, device=dev) for k, v in scene_h.items()}
         d_arm = torch.as_tensor(arm_h, device=dev)
+        # the arm sweep in one launch: the batch once per n_sigma, n_sigma per row
+        # (the same bits per row as separate launches; copies of a sparse batch
+        # share tiles and staged chunks)
+        d_arm_sw = d_arm.repeat(len(NSIGMAS), 1).contiguous()
+        d_ns_arm = torch.as_tensor(np.repeat(np.asarray(NSIGMAS, np.float32), arm_h.shape[0]), device=dev)
         d_edge = torch.as_tensor(edge_h, device=dev)
         d_poses = torch.as_tensor(poses_h, device=dev)
         d_offs = torch.as_tensor(offs_h, device=dev)
@@ -166,7 +175,7 @@ def run_ours(args, rank, world):
         n_pose = poses_h.shape[0]
         ones = torch.ones(n_pose, dtype=torch.float32, device=dev)
         outs = {}
-        for name, q, G in (("arm", d_arm, 64), ("edge", d_edge, 1024)):
+        for name, q, G in (("arm", d_arm_sw, 64), ("edge", d_edge, 1024)):
             Q = q.shape[0]
             outs[name] = {"metric": torch.empty(Q, device=dev), "collide": torch.empty(Q, dtype=torch.uint8, device=dev),
                           "group_metric": torch.empty((Q + G - 1) // G, device=dev),
@@ -181,13 +190,14 @@ def run_ours(args, rank, world):
 
     # tile shapes for the two batch classes from the autotuner (untimed)
     if args.tiles:
-        ta, te = (int(x) for x in args.tiles.split(","))
-        tiles = {"arm": ta, "edge": te, "source": "--tiles"}
+        tt = [int(x) for x in args.tiles.split(",")]
+        tiles = {"arm": tt[0], "edge": tt[1], "pose": tt[2] if len(tt) > 2 else tt[0], "source": "--tiles"}
     else:
         tune_scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
                               device=dev, stream=stream)
-        tiles = {"arm": tune_scene.autotune(d_arm, 1.0, reps=2, stream=stream)[0],
-                 "edge": tune_scene.autotune(d_edge, 1.0, reps=1, stream=stream)[0], "source": "cs_autotune"}
+        tiles = {"arm": tune_scene.autotune(d_arm_sw, 1.0, reps=2, stream=stream)[0],
+                 "edge": tune_scene.autotune(d_edge, 1.0, reps=1, stream=stream)[0],
+                 "pose": tune_scene.autotune(d_arm, 1.0, reps=2, stream=stream)[0], "source": "cs_autotune"}
         tune_scene.close()
 
     def step(events=None, stats=None, build_ev=None):
@@ -199,14 +209,14 @@ def run_ours(args, rank, world):
                          device=dev, stream=stream)
         if build_ev is not None:
             build_ev[1].record(stream)
+        scene.query(d_arm_sw, 0.0, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
+                    nsigma_per_query=d_ns_arm, eval_events=nxt(), out=outs["arm"], pair_stats=stats)
         for ns in NSIGMAS:
-            scene.query(d_arm, ns, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
-                        eval_events=nxt(), out=outs["arm"], pair_stats=stats)
             scene.query(d_edge, ns, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"]), stream=stream,
                         eval_events=nxt(), out=outs["edge"], pair_stats=stats)
         with torch.cuda.stream(stream):
             sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
-            scene.query(sph, 1.0, params=cs.QueryParams(group_size=K, tile_config=tiles["arm"]), stream=stream,
+            scene.query(sph, 1.0, params=cs.QueryParams(group_size=K, tile_config=tiles["pose"]), stream=stream,
                         eval_events=nxt(), out=pose_out, pair_stats=stats)
             scene.query_grad(sph, 1.0, grad_out=ones, params=cs.QueryParams(group_size=K), stream=stream,
                              eval_events=nxt(), out=gbuf)
@@ -220,9 +230,9 @@ def run_ours(args, rank, world):
     cand_pairs, useful_pairs = (int(x) for x in stats.cpu().tolist())
     # forward sphere launches only (the roofline's kernel): rerun without the grad pass
     stats_fwd = torch.zeros(2, dtype=torch.int64, device=dev)
+    sc.query(d_arm_sw, 0.0, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
+             nsigma_per_query=d_ns_arm, out=outs["arm"], pair_stats=stats_fwd)
     for ns in NSIGMAS:
-        sc.query(d_arm, ns, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
-                 out=outs["arm"], pair_stats=stats_fwd)
         sc.query(d_edge, ns, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"]), stream=stream,
                  out=outs["edge"], pair_stats=stats_fwd)
     torch.cuda.synchronize(dev)
@@ -230,7 +240,7 @@ def run_ours(args, rank, world):
     info = sc.info()
     sc.close()
     n_queries = len(NSIGMAS) * (arm_h.shape[0] + edge_h.shape[0]) + 2 * n_pose * K
-    n_fwd_launches = 2 * len(NSIGMAS)
+    n_fwd_launches = 1 + len(NSIGMAS)
 
     for _ in range(args.warmup):
         s, _ = step()
@@ -357,22 +367,19 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
     K = offs_h.shape[0]
     n_pose = poses_h.shape[0]
     copy = torch.cuda.Stream(dev)
-    batches = (("arm", h_arm, 64), ("edge", h_edge, 1024))
-    dev_out, host_out = {}, {}
-    for ns in NSIGMAS:
-        for name, q, G in batches:
-            Q = q.shape[0]
-            ng = (Q + G - 1) // G
-            dev_out[(ns, name)] = {"metric": torch.empty(Q, device=dev),
-                                   "collide": torch.empty(Q, dtype=torch.uint8, device=dev),
-                                   "group_metric": torch.empty(ng, device=dev),
-                                   "group_collide": torch.empty(ng, dtype=torch.uint8, device=dev)}
-            host_out[(ns, name)] = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
-                                    for k, v in dev_out[(ns, name)].items()}
+    d_ns_arm = torch.as_tensor(np.repeat(np.asarray(NSIGMAS, np.float32), h_arm.shape[0]), device=dev)
+    sizes = [(len(NSIGMAS) * h_arm.shape[0], 64)] + [(h_edge.shape[0], 1024)] * len(NSIGMAS)
+    dev_out, host_out = [], []
+    for Q, G in sizes:
+        ng = (Q + G - 1) // G
+        dev_out.append({"metric": torch.empty(Q, device=dev), "collide": torch.empty(Q, dtype=torch.uint8, device=dev),
+                        "group_metric": torch.empty(ng, device=dev),
+                        "group_collide": torch.empty(ng, dtype=torch.uint8, device=dev)})
+        host_out.append({k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in dev_out[-1].items()})
     h_gpose = torch.empty((n_pose, 6)).pin_memory()
     h_posecost = torch.empty(n_pose).pin_memory()
     h2d = sum(v.numel() * 4 for v in h_scene.values()) + (h_arm.numel() + h_edge.numel() + h_poses.numel()) * 4
-    d2h = sum(v.numel() * v.element_size() for o in host_out.values() for v in o.values()) \
+    d2h = sum(v.numel() * v.element_size() for o in host_out for v in o.values()) \
         + h_gpose.numel() * 4 + h_posecost.numel() * 4
     sh = stream.cuda_stream
 
@@ -388,23 +395,26 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
             d_arm = h_arm.to(dev, non_blocking=True)
             d_edge = h_edge.to(dev, non_blocking=True)
             d_poses = h_poses.to(dev, non_blocking=True)
-        for ns in NSIGMAS:
-            for name, dq, G in (("arm", d_arm, 64), ("edge", d_edge, 1024)):
-                o = dev_out[(ns, name)]
-                p = cs.QueryParams(group_size=G, tile_config=tiles[name]).to_c()
-                p.stream = sh
-                p.out_group_metric, p.out_group_collide = o["group_metric"].data_ptr(), o["group_collide"].data_ptr()
-                cs.check(cs.abi.cs_query(h, 0, dq, dq.shape[0], ns, o["metric"], o["collide"], p))
-                done = torch.cuda.Event()
-                done.record(stream)
-                copy.wait_event(done)
-                with torch.cuda.stream(copy):
-                    for k, v in o.items():
-                        host_out[(ns, name)][k].copy_(v, non_blocking=True)
+            d_arm_sw = d_arm.repeat(len(NSIGMAS), 1)
+        passes = [("arm", d_arm_sw, 64, 0.0, d_ns_arm)] + [("edge", d_edge, 1024, ns, None) for ns in NSIGMAS]
+        for i, (name, dq, G, ns, nsq) in enumerate(passes):
+            o = dev_out[i]
+            p = cs.QueryParams(group_size=G, tile_config=tiles[name]).to_c()
+            p.stream = sh
+            p.out_group_metric, p.out_group_collide = o["group_metric"].data_ptr(), o["group_collide"].data_ptr()
+            if nsq is not None:
+                p.nsigma_per_query = nsq.data_ptr()
+            cs.check(cs.abi.cs_query(h, 0, dq, dq.shape[0], ns, o["metric"], o["collide"], p))
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy.wait_event(done)
+            with torch.cuda.stream(copy):
+                for k, v in o.items():
+                    host_out[i][k].copy_(v, non_blocking=True)
         with torch.cuda.stream(stream):
             sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
             Q = sph.shape[0]
-            p = cs.QueryParams(group_size=K, tile_config=tiles["arm"]).to_c()
+            p = cs.QueryParams(group_size=K, tile_config=tiles["pose"]).to_c()
             p.stream = sh
             gm = torch.empty(n_pose, device=dev)
             p.out_group_metric = gm.data_ptr()
@@ -900,6 +910,30 @@ def run_eval_case(args):
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
     kstats = torch.zeros(16, dtype=torch.int64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if args.sweep:
+        # one launch over the four copies (n_sigma per row) against four launches
+        Q = arm.shape[0]
+        rows = arm.repeat(len(NSIGMAS), 1).contiguous()
+        nsq = torch.as_tensor(np.repeat(np.asarray(NSIGMAS, np.float32), Q), device=dev)
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(2):
+            o1 = scene.query(rows, 0.0, params=qp, prim_type=prim, nsigma_per_query=nsq)
+        scene.query(rows, 0.0, params=qp, prim_type=prim, nsigma_per_query=nsq, eval_events=ev1, out=o1)
+        sep_ms = 0.0
+        outs = []
+        for ns in NSIGMAS:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            scene.query(arm, ns, params=qp, prim_type=prim)
+            o = scene.query(arm, ns, params=qp, prim_type=prim, eval_events=ev)
+            torch.cuda.synchronize()
+            sep_ms += ev[0].elapsed_time(ev[1])
+            outs.append(o["metric"].clone())
+        torch.cuda.synchronize()
+        same = all(torch.equal(o1["metric"][i * Q:(i + 1) * Q], outs[i]) for i in range(len(NSIGMAS)))
+        print(json.dumps({"case": "eval", "sweep": True, "batch": args.batch, "tile": args.tile,
+                          "queries": 4 * Q, "one_launch_ms": ev1[0].elapsed_time(ev1[1]),
+                          "four_launches_ms": sep_ms, "bitwise_equal": bool(same)}))
+        return
     if args.grad:
         up = torch.ones(arm.shape[0] // G + (arm.shape[0] % G > 0), device=dev)
         scene.query_grad(arm, ns, grad_out=up, params=qp, prim_type=prim)

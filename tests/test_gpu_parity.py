@@ -383,3 +383,29 @@ def test_flags_mode_without_groups_equals_full_flags(cs):
     fl = scene.query(torch.as_tensor(q), 1.0, params=cs.QueryParams(mode=cs.CS_METRIC_FLAGS))
     torch.cuda.synchronize()
     np.testing.assert_array_equal(fl["collide"].cpu().numpy(), full["collide"].cpu().numpy())
+
+
+def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
+    """The arm batch at four n_sigma values in one launch (rows repeated,
+    n_sigma per row, as the benchmark runs the sweep) gives every row the same
+    bits as four separate launches, in every metric mode."""
+    sc = _TABLE["scene"]
+    q = S.arm_queries(configs=1024)
+    scene = _TABLE.get("gpu") or _scene(cs, sc)
+    _TABLE["gpu"] = scene
+    ns = np.array([0.0, 0.5, 1.0, 2.0], np.float32)
+    Q = q.shape[0]
+    rows = torch.as_tensor(np.tile(q, (4, 1)), device="cuda")
+    nsq = torch.as_tensor(np.repeat(ns, Q), device="cuda")
+    for mode in (0, 2, 3):
+        p = cs.QueryParams(mode=mode, group_size=64)
+        one = scene.query(rows, 0.0, params=p, nsigma_per_query=nsq, want_count=True)
+        for i, v in enumerate(ns):
+            sep = scene.query(torch.as_tensor(q, device="cuda"), float(v), params=p, want_count=True)
+            torch.cuda.synchronize()
+            for k in ("metric", "collide", "count"):
+                a = one[k][i * Q:(i + 1) * Q].cpu().numpy()
+                b = sep[k].cpu().numpy()
+                np.testing.assert_array_equal(a.view(np.uint8), b.view(np.uint8), err_msg=f"{mode} {v} {k}")
+            np.testing.assert_array_equal(one["group_metric"][i * (Q // 64):(i + 1) * (Q // 64)].cpu().numpy(),
+                                          sep["group_metric"].cpu().numpy())
