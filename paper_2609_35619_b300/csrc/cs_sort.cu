@@ -124,45 +124,81 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t *__re
     hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter: items are ranked in index order (round, warp, lane).
+// Stable scatter.  Warp w of a block owns keys [w 512, (w + 1) 512) of the
+// block's 4,096 (16 rounds of 32 in index order).  Pass 1 counts each warp's
+// digits; the counts then give every digit its start in the block and every
+// warp its first slot per digit; pass 2 places each warp's keys in index
+// order (lanes of equal digit ranked by lane) into shared memory, sorted by
+// digit; a last pass writes each digit's run to its place in the output
+// (the block's offset from the global scan), so stores are contiguous runs
+// instead of one scattered 4-byte write per key.  Equal digits keep their
+// index order: the sort is stable.
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, size_t n, int shift, const uint32_t *__restrict__ offsets,
     unsigned nblocks) {
-    __shared__ uint32_t run[kRadix];
-    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    constexpr int kPerWarp = kSortTile / kSortWarps;  // 512
+    __shared__ uint32_t cnt[kSortWarps][kRadix];
+    __shared__ uint32_t lstart[kRadix], goff[kRadix];
+    __shared__ uint32_t skey[kSortTile], sval[kSortTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    run[threadIdx.x] = offsets[(size_t)threadIdx.x * nblocks + blockIdx.x];
     const unsigned lt_mask = (1u << lane) - 1u;
-    size_t base = (size_t)blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortRounds; ++r) {
-        size_t r0 = base + (size_t)r * kSortThreads;
-        if (r0 >= n) break;  // uniform across the block
-#pragma unroll
-        for (int k = 0; k < kSortWarps; ++k) wcnt[k][threadIdx.x] = 0;
-        __syncthreads();
-        size_t i = r0 + threadIdx.x;
-        bool valid = i < n;
-        uint32_t key = valid ? kin[i] : 0u;
-        uint32_t val = valid ? vin[i] : 0u;
-        int d = valid ? (int)((key >> shift) & 0xFFu) : kRadix;  // invalid lanes form their own group
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pre = 0;
-            for (int k = 0; k < w; ++k) pre += wcnt[k][d];
-            uint32_t pos = run[d] + pre + rank;
-            kout[pos] = key;
-            vout[pos] = val;
-        }
-        __syncthreads();
+    const size_t tile0 = (size_t)blockIdx.x * kSortTile;
+    const size_t base = tile0 + (size_t)w * kPerWarp;
+    for (int d = lane; d < kRadix; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    for (int r = 0; r < kPerWarp / 32; ++r) {
+        const size_t i = base + (size_t)r * 32 + lane;
+        const bool valid = i < n;
+        const int d = valid ? (int)((kin[i] >> shift) & 0xFFu) : kRadix;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lt_mask) == 0u) cnt[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // one thread per digit
         uint32_t tot = 0;
 #pragma unroll
-        for (int k = 0; k < kSortWarps; ++k) tot += wcnt[k][threadIdx.x];
-        run[threadIdx.x] += tot;
-        __syncthreads();
+        for (int k = 0; k < kSortWarps; ++k) tot += cnt[k][d];
+        uint32_t start;
+        block_excl_scan(tot, start);  // the digit's first slot in the block
+        lstart[d] = start;
+        goff[d] = offsets[(size_t)d * nblocks + blockIdx.x];
+        uint32_t run = start;
+#pragma unroll
+        for (int k = 0; k < kSortWarps; ++k) {
+            const uint32_t c = cnt[k][d];
+            cnt[k][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < kPerWarp / 32; ++r) {
+        const size_t i = base + (size_t)r * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t val = valid ? vin[i] : 0u;
+        const int d = valid ? (int)((key >> shift) & 0xFFu) : kRadix;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned rank = __popc(peers & lt_mask);
+        const uint32_t lp = valid ? cnt[w][d] + rank : 0u;
+        __syncwarp();
+        if (valid && rank == 0u) cnt[w][d] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            skey[lp] = key;
+            sval[lp] = val;
+        }
+    }
+    __syncthreads();
+    const int tn = (int)min((size_t)kSortTile, n - tile0);
+    for (int lp = threadIdx.x; lp < tn; lp += kSortThreads) {
+        const uint32_t key = skey[lp];
+        const int d = (int)((key >> shift) & 0xFFu);
+        const uint32_t pos = goff[d] + (uint32_t)lp - lstart[d];
+        kout[pos] = key;
+        vout[pos] = sval[lp];
     }
 }
 
