@@ -689,10 +689,29 @@ def run_rrt(torch, cs, dev, iters=200, B=32, M=8):
     e1.record()
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / iters
+    k_ext = (cs.abi.cs_launch_count() - l0) / iters
     n1 = int(tree.count.item())
+    # the same loop through a captured extension: samples written into the
+    # graph's buffer on the stream, then one graph launch per extension
+    gtree = cs.RrtTree(scene, [3.0, 2.5, 1.5], capacity=1 << 16, step=0.3, radius=0.05, nsigma=1.0, M=M)
+    g = gtree.graph(B)
+    for i in range(5):
+        g.samples.copy_(samples[i])
+        g.launch()
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for i in range(iters):
+        g.samples.copy_(samples[5 + i])
+        g.launch()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    g_ms = e0.elapsed_time(e1) / iters
+    same = int(gtree.count.item()) == n1
+    g.close()
     res = {"workload": RRT_WORKLOAD, "B": B, "M": M, "extensions": iters, "ms_per_extension": ms,
+           "graph_ms_per_extension": g_ms, "graph_edges_per_s": B * 1e3 / g_ms, "graph_same_tree_size": same,
            "edges_per_s": B * 1e3 / ms, "points_per_s": B * M * 1e3 / ms,
-           "kernels_per_extension": (cs.abi.cs_launch_count() - l0) / iters,
+           "kernels_per_extension": k_ext,
            "nodes_before": n0, "nodes_after": n1, "free_frac": (n1 - n0) / (B * iters)}
     scene.close()
     return res

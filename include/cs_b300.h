@@ -415,6 +415,17 @@ CS_API cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *desc, f
                                int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
                                const cs_params *params);
 
+/* The same extension captured into a query graph (see cs_graph_create):
+ * every cs_graph_launch extends the tree held in the buffers given here with
+ * the B samples `samples` holds at that time (an RRT loop writes the next
+ * samples there before each launch).  The tree's node count lives in
+ * `count` on the device, so consecutive launches grow it without the host.
+ * Launch, sync and free it with cs_graph_launch / cs_graph_sync /
+ * cs_graph_destroy.  Errors: those of cs_rrt_extend and cs_graph_create. */
+CS_API cs_status cs_rrt_graph_create(const cs_scene *scene, const cs_rrt_desc *desc, float *nodes, int32_t *parent,
+                                     int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
+                                     const cs_params *params, cs_graph **out);
+
 /* ------------------------------------------------------------------------
  * Serving loop.  The paper has no counterpart: this is the runtime that keeps
  * scenes resident and answers collision-query requests of uneven size (one

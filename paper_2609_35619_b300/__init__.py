@@ -27,7 +27,7 @@ from . import abi
 from .abi import (CS_METRIC_FLAGS, CS_METRIC_MEAN_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_SUM_COST,
                   CS_PRIM_ELLIPSOID, CS_PRIM_SPHERE, CsError, check)
 
-__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "mppi_step", "MppiGraph", "RrtTree", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
+__all__ = ["Scene", "QueryParams", "QueryGraph", "Server", "mppi_step", "MppiGraph", "RrtTree", "RrtGraph", "path_refine", "pose_spheres", "pose_spheres_grad", "CollisionCost", "abi",
            "CS_PRIM_SPHERE", "CS_PRIM_ELLIPSOID", "CS_METRIC_MEAN_COST", "CS_METRIC_SUM_COST",
            "CS_METRIC_MIN_S2", "CS_METRIC_SOFTMIN_S2", "CS_METRIC_FLAGS", "CsError"]
 
@@ -509,6 +509,48 @@ class RrtTree:
                                 out["edge_free"], p))
         out["_samples"] = s
         return out
+
+    def graph(self, B: int) -> "RrtGraph":
+        """Capture this tree's extension with B samples (cs_rrt_graph_create)."""
+        return RrtGraph(self, B)
+
+
+class RrtGraph:
+    """One extension of an RrtTree captured into a CUDA graph
+    (cs_rrt_graph_create): write the next B samples into `samples`, then
+    launch(); `nearest` and `edge_free` hold the last launch's results."""
+
+    def __init__(self, tree: RrtTree, B: int):
+        torch = _torch()
+        dev = tree.scene.device
+        self.tree = tree
+        self.samples = torch.zeros((B, 3), dtype=torch.float32, device=dev)
+        self.nearest = torch.empty(B, dtype=torch.int32, device=dev)
+        self.edge_free = torch.empty(B, dtype=torch.uint8, device=dev)
+        d = abi.cs_rrt_desc()
+        d.B, d.M, d.step, d.radius, d.nsigma, d.capacity = B, tree.M, tree.step, tree.radius, tree.nsigma, \
+            tree.capacity
+        self._h = ctypes.c_void_p()
+        check(abi.cs_rrt_graph_create(tree.scene.handle, d, tree.nodes, tree.parent, tree.count, self.samples,
+                                      self.nearest, self.edge_free, tree.params.to_c(), self._h))
+        self.kernels = abi.cs_graph_kernels(self._h)
+
+    def launch(self, stream=None):
+        check(abi.cs_graph_launch(self._h, stream))
+
+    def sync(self, stream=None):
+        check(abi.cs_graph_sync(self._h, stream))
+
+    def close(self):
+        if self._h:
+            check(abi.cs_graph_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _set_events(p, events):

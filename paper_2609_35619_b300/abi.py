@@ -204,6 +204,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(cs_params), ctypes.POINTER(_P)]),
     "cs_mppi_graph_create": (ctypes.c_int, [_P, ctypes.POINTER(cs_mppi_desc), _P, _P, _P, _P, _P, _P, _P,
                                             ctypes.POINTER(cs_params), ctypes.POINTER(_P)]),
+    "cs_rrt_graph_create": (ctypes.c_int, [_P, ctypes.POINTER(cs_rrt_desc), _P, _P, _P, _P, _P, _P,
+                                           ctypes.POINTER(cs_params), ctypes.POINTER(_P)]),
     "cs_graph_launch": (ctypes.c_int, [_P, _P]),
     "cs_graph_sync": (ctypes.c_int, [_P, _P]),
     "cs_graph_kernels": (ctypes.c_int64, [_P]),
@@ -359,6 +361,13 @@ def cs_graph_create(scene, prim_type, prims, Q, conservatism, out_metric, out_co
     return load().cs_graph_create(scene, prim_type, ptr(prims), int(Q), float(conservatism), ptr(out_metric),
                                   ptr(out_collide), ptr(grad_out), ptr(grad_centres),
                                   None if params is None else ctypes.byref(params), ctypes.byref(out))
+
+
+def cs_rrt_graph_create(scene, desc, nodes, parent, count, samples, nearest, edge_free, params,
+                        out: ctypes.c_void_p) -> int:
+    return load().cs_rrt_graph_create(scene, ctypes.byref(desc), ptr(nodes), ptr(parent), ptr(count), ptr(samples),
+                                      ptr(nearest), ptr(edge_free), None if params is None else ctypes.byref(params),
+                                      ctypes.byref(out))
 
 
 def cs_mppi_graph_create(scene, desc, x0, U, eps, U_out, cost, weights, collide, params,

@@ -151,6 +151,27 @@ cs_status cs_mppi_graph_create(const cs_scene *scene, const cs_mppi_desc *desc, 
                          out);
 }
 
+cs_status cs_rrt_graph_create(const cs_scene *scene, const cs_rrt_desc *desc, float *nodes, int32_t *parent,
+                              int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
+                              const cs_params *params, cs_graph **out) {
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    cs_status st = rrt_check(scene, desc, nodes, parent, count, samples);
+    if (st != CS_OK) return st;
+    cs_params p;
+    if (params) p = *params;
+    else cs_params_init(&p);
+    if (p.host_io) return invalid("an RRT graph takes device buffers only (host_io must be 0)");
+    if ((st = check_params(p)) != CS_OK) return st;
+    p.eval_events[0] = p.eval_events[1] = nullptr;
+    return capture_graph([&](Workspace *w) { return rrt_reserve(w, desc->B, desc->M); },
+                         [&](cudaStream_t s, Workspace *w) {
+                             p.stream = s;
+                             return rrt_common(scene, desc, nodes, parent, count, samples, nearest, edge_free, &p, w);
+                         },
+                         out);
+}
+
 cs_status cs_graph_launch(cs_graph *h, void *stream) {
     cs_status st = check_graph(h);
     if (st != CS_OK) return st;

@@ -172,6 +172,14 @@ cs_status mppi_reserve(Workspace *w, int64_t K, int64_t T);
 cs_status mppi_check(const cs_scene *scene, const cs_mppi_desc *d, const float *x0, const float *U,
                      const float *eps, const float *U_out);
 
+// One batched RRT extension (cs_rrt_extend); own_ws = scratch owned by a graph.
+cs_status rrt_common(const cs_scene *scene, const cs_rrt_desc *d, float *nodes, int32_t *parent, int32_t *count,
+                     const float *samples, int32_t *nearest, uint8_t *edge_free, const cs_params *params,
+                     Workspace *own_ws);
+cs_status rrt_reserve(Workspace *w, int B, int M);
+cs_status rrt_check(const cs_scene *scene, const cs_rrt_desc *d, const float *nodes, const int32_t *parent,
+                    const int32_t *count, const float *samples);
+
 // ------------------------------------------------------- launch accounting
 // Host-side count of kernel launches (cs_launch_count); every launcher adds
 // the number of kernels it enqueues.

@@ -125,15 +125,26 @@ __global__ void __launch_bounds__(1024) k_rrt_insert(float *__restrict__ nodes, 
 
 }  // namespace
 
-}  // namespace cs
+// Scratch of an extension of B samples x M edge points, grown before use so
+// that a captured extension allocates nothing: edge points [B M, 4], new
+// nodes [B, 4], nearest [B], edge flags [B].
+cs_status rrt_reserve(Workspace *w, int B, int M) {
+    const int64_t Q = (int64_t)B * M;
+    cs_status st = grow_workspace(w, (size_t)Q, false);
+    if (st != CS_OK) return st;
+    const size_t need = 4 * (size_t)Q + 4 * (size_t)B + (size_t)B + ((size_t)B + 3) / 4;
+    if (w->cap_rrt < need) {
+        if (w->rrt) CS_CUDA(cudaFree(w->rrt));
+        w->rrt = nullptr;
+        w->cap_rrt = 0;
+        CS_CUDA(cudaMalloc(&w->rrt, 4 * need));
+        w->cap_rrt = need;
+    }
+    return CS_OK;
+}
 
-using namespace cs;
-
-extern "C" {
-
-cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *d, float *nodes, int32_t *parent,
-                        int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
-                        const cs_params *params) {
+cs_status rrt_check(const cs_scene *scene, const cs_rrt_desc *d, const float *nodes, const int32_t *parent,
+                    const int32_t *count, const float *samples) {
     cs_status st = check_scene(scene);
     if (st != CS_OK) return st;
     if (!d) return invalid("desc is NULL");
@@ -145,6 +156,14 @@ cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *d, float *node
     if (!(d->nsigma >= 0.f) || !isfinite(d->nsigma)) return invalid("nsigma must be finite and >= 0");
     if (d->capacity < 1) return invalid("capacity must be >= 1");
     if (!nodes || !parent || !count || !samples) return invalid("nodes, parent, count and samples are required");
+    return CS_OK;
+}
+
+cs_status rrt_common(const cs_scene *scene, const cs_rrt_desc *d, float *nodes, int32_t *parent, int32_t *count,
+                     const float *samples, int32_t *nearest, uint8_t *edge_free, const cs_params *params,
+                     Workspace *own_ws) {
+    cs_status st = rrt_check(scene, d, nodes, parent, count, samples);
+    if (st != CS_OK) return st;
     cs_params p;
     if (params) p = *params;
     else cs_params_init(&p);
@@ -154,17 +173,9 @@ cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *d, float *node
     cudaStream_t s = (cudaStream_t)p.stream;
     const int64_t Q = (int64_t)d->B * d->M;
 
-    // scratch: edge points [Q,4], new nodes [B,4], nearest [B], edge flags [B]
-    Workspace *w = nullptr;
-    if ((st = get_workspace(sc->device, s, (size_t)Q, false, &w)) != CS_OK) return st;
-    const size_t need = 4 * (size_t)Q + 4 * (size_t)d->B + (size_t)d->B + ((size_t)d->B + 3) / 4;
-    if (w->cap_rrt < need) {
-        if (w->rrt) CS_CUDA(cudaFree(w->rrt));
-        w->rrt = nullptr;
-        w->cap_rrt = 0;
-        CS_CUDA(cudaMalloc(&w->rrt, 4 * need));
-        w->cap_rrt = need;
-    }
+    Workspace *w = own_ws;
+    if (!w && (st = get_workspace(sc->device, s, (size_t)Q, false, &w)) != CS_OK) return st;
+    if ((st = rrt_reserve(w, d->B, d->M)) != CS_OK) return st;
     float4 *pts = reinterpret_cast<float4 *>(w->rrt);
     float4 *newn = pts + Q;
     int32_t *near = reinterpret_cast<int32_t *>(newn + d->B);
@@ -196,6 +207,18 @@ cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *d, float *node
     count_launches(1);
     CS_CUDA(cudaGetLastError());
     return CS_OK;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *d, float *nodes, int32_t *parent,
+                        int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
+                        const cs_params *params) {
+    return rrt_common(scene, d, nodes, parent, count, samples, nearest, edge_free, params, nullptr);
 }
 
 }  // extern "C"

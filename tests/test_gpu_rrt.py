@@ -87,3 +87,34 @@ def test_capacity_and_arguments(cs, room):
     with pytest.raises(cs.CsError):
         tree.M = 1
         tree.extend(np.zeros((2, 3), np.float32))
+
+
+def test_captured_extension_grows_the_same_tree(cs, room):
+    """Replays of the captured extension (cs_rrt_graph_create), the samples
+    rewritten before each launch, grow the same tree bit for bit as the same
+    loop of cs_rrt_extend calls."""
+    _, scene = room
+    # the root: the first of a few seeded points that a query finds free
+    cand = np.random.default_rng(11).uniform([0.5, 0.5, 0.5], [5.5, 4.5, 2.5], (64, 3)).astype(np.float32)
+    res = scene.query(torch.as_tensor(np.c_[cand, np.full(64, 0.05, np.float32)], device="cuda"), 1.0)
+    torch.cuda.synchronize()
+    root = cand[np.flatnonzero(res["collide"].cpu().numpy() == 0)[0]]
+    kw = dict(capacity=4096, step=0.3, radius=0.05, nsigma=1.0, M=8)
+    a = cs.RrtTree(scene, root, **kw)
+    b = cs.RrtTree(scene, root, **kw)
+    g = b.graph(32)
+    assert g.kernels > 0
+    rng = np.random.default_rng(21)
+    for _ in range(12):
+        s = torch.as_tensor(rng.uniform([0.1, 0.1, 0.1], [5.9, 4.9, 2.9], (32, 3)).astype(np.float32), device="cuda")
+        ra = a.extend(s)
+        g.samples.copy_(s)
+        g.launch()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ra["nearest"].cpu().numpy(), g.nearest.cpu().numpy())
+        np.testing.assert_array_equal(ra["edge_free"].cpu().numpy(), g.edge_free.cpu().numpy())
+    n = int(a.count.item())
+    assert n == int(b.count.item()) and n > 1
+    np.testing.assert_array_equal(a.nodes[:n].cpu().numpy(), b.nodes[:n].cpu().numpy())
+    np.testing.assert_array_equal(a.parent[:n].cpu().numpy(), b.parent[:n].cpu().numpy())
+    g.close()
