@@ -162,6 +162,16 @@ typedef struct cs_params {
                                   then runs the default tile shape of its batch size and the
                                   adjoint its default shape (tile_config is ignored).
                                   Default 0. */
+    int32_t sweep_count;       /* >= 2: a conservatism sweep in one launch.  cs_query then
+                                  evaluates each of the Q rows at every n_sigma of
+                                  sweep_nsigma[0 .. sweep_count) (conservatism and
+                                  nsigma_per_query are unused) and writes S = sweep_count
+                                  blocks: out_metric, out_collide, out_count [S*Q] with row
+                                  s*Q + j for value s; group outputs [S*ceil(Q/G)], groups
+                                  formed within each block.  Every value gives the same bits
+                                  as its own cs_query call.  Not for cs_query_grad, the
+                                  flags mode or host_io.  0 or 1 = no sweep (default). */
+    float sweep_nsigma[8];     /* the sweep's n_sigma values, each finite and >= 0 */
 } cs_params;
 
 /* Scene information returned by cs_scene_info. */

@@ -45,6 +45,7 @@ class QueryParams:
     group_size: int = 0
     tile_config: int = 0
     exact_variance: bool = False
+    sweep: tuple = ()  # n_sigma values of a conservatism sweep in one launch (2 .. 8 of them)
 
     def to_c(self) -> abi.cs_params:
         p = abi.cs_params()
@@ -52,6 +53,11 @@ class QueryParams:
         p.gamma, p.d_max, p.s_min, p.eps, p.tau = self.gamma, self.d_max, self.s_min, self.eps, self.tau
         p.k_thr, p.mode, p.group_size, p.tile_config = self.k_thr, self.mode, self.group_size, self.tile_config
         p.exact_variance = 1 if self.exact_variance else 0
+        if len(self.sweep) > 8:
+            raise ValueError("a sweep takes at most 8 n_sigma values")
+        p.sweep_count = len(self.sweep) if len(self.sweep) >= 2 else 0
+        for k, v in enumerate(self.sweep):
+            p.sweep_nsigma[k] = float(v)
         return p
 
 
@@ -131,9 +137,10 @@ class Scene:
         cols = 4 if prim_type == CS_PRIM_SPHERE else 10
         prims = _as_f32(prims, self.device).reshape(-1, cols)
         Q = prims.shape[0]
+        S = len(params.sweep) if len(params.sweep) >= 2 else 1  # outputs: S blocks of Q rows
         if out is None:
-            out = {"metric": torch.empty(Q, dtype=torch.float32, device=self.device),
-                   "collide": torch.empty(Q, dtype=torch.uint8, device=self.device)}
+            out = {"metric": torch.empty(S * Q, dtype=torch.float32, device=self.device),
+                   "collide": torch.empty(S * Q, dtype=torch.uint8, device=self.device)}
         p = params.to_c()
         _set_events(p, eval_events)
         p.stream = abi.stream_handle(stream)
@@ -143,10 +150,10 @@ class Scene:
             p.nsigma_per_query = abi.ptr(nsq)
         if want_count:
             if "count" not in out:
-                out["count"] = torch.empty(Q, dtype=torch.int32, device=self.device)
+                out["count"] = torch.empty(S * Q, dtype=torch.int32, device=self.device)
             p.out_count = abi.ptr(out["count"])
         if params.group_size > 0:
-            ng = (Q + params.group_size - 1) // params.group_size
+            ng = S * ((Q + params.group_size - 1) // params.group_size)
             if "group_metric" not in out:
                 out["group_metric"] = torch.empty(ng, dtype=torch.float32, device=self.device)
                 out["group_collide"] = torch.empty(ng, dtype=torch.uint8, device=self.device)

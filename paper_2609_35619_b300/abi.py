@@ -61,6 +61,8 @@ class cs_params(ctypes.Structure):
         ("eval_events", ctypes.c_void_p * 2),
         ("out_kernel_stats", ctypes.c_void_p),
         ("exact_variance", ctypes.c_int32),
+        ("sweep_count", ctypes.c_int32),
+        ("sweep_nsigma", ctypes.c_float * 8),
     ]
 
 

@@ -54,7 +54,7 @@ constexpr int64_t kMaxRows = (int64_t)1 << 30;
 static void free_ws(Workspace *w) {
     void *ptrs[] = {w->keys[0], w->keys[1], w->vals[0], w->vals[1], w->sort_hist, w->scan_tmp,
                     w->qrec, w->qns, w->io_prims, w->io_ns, w->io_metric, w->io_collide,
-                    w->io_count, w->io_grad, w->io_gout, w->io_gm, w->io_gc, w->mppi, w->rrt, w->rnd, w->rnd2, w->err};
+                    w->io_count, w->io_grad, w->io_gout, w->io_gm, w->io_gc, w->mppi, w->rrt, w->rnd, w->rnd2, w->sweep_rec, w->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete w;
@@ -111,6 +111,21 @@ cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io,
     }
     *out = w;
     return grow_workspace(w, Q, host_io);
+}
+
+cs_status sweep_reserve(Workspace *w, int64_t Q, int prim_type, int S) {
+    cs_status st = grow_workspace(w, (size_t)(Q * S), false);
+    if (st != CS_OK) return st;
+    const size_t need = (size_t)(prim_type == CS_PRIM_SPHERE ? 1 : 3) * (size_t)std::max<int64_t>(Q, 1);
+    if (w->cap_sweep < need) {
+        if (w->sweep_rec) CS_CUDA(cudaFree(w->sweep_rec));
+        w->sweep_rec = nullptr;
+        w->cap_sweep = 0;
+        const size_t cap = std::max(need, w->cap_sweep + w->cap_sweep / 2);
+        CS_CUDA(cudaMalloc(&w->sweep_rec, sizeof(float4) * cap));
+        w->cap_sweep = cap;
+    }
+    return CS_OK;
 }
 
 cs_status grow_workspace(Workspace *w, size_t Q, bool host_io) {
@@ -171,6 +186,10 @@ cs_status check_params(const cs_params &p) {
     if (p.group_size < 0) return invalid("group_size must be >= 0");
     if (p.host_io != 0 && p.host_io != 1) return invalid("host_io must be 0 or 1");
     if (p.exact_variance != 0 && p.exact_variance != 1) return invalid("exact_variance must be 0 or 1");
+    if (p.sweep_count < 0 || p.sweep_count > 8) return invalid("sweep_count must lie in [0, 8]");
+    for (int k = 0; k < p.sweep_count && p.sweep_count >= 2; ++k)
+        if (!(p.sweep_nsigma[k] >= 0.f) || !isfinite(p.sweep_nsigma[k]))
+            return invalid("sweep_nsigma values must be finite and >= 0");
     if (p.tile_config != 0 && p.tile_config != CS_TILE_TUNED) {
         int32_t ids[32];
         int n = tile_configs(ids, 32);
@@ -295,8 +314,16 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
         auto it = sc->tuned.find(tune_key(prim_type, p.mode, Q));
         p.tile_config = it == sc->tuned.end() ? 0 : it->second;
     }
-    if (!p.nsigma_per_query && (!(conservatism >= 0.f) || !isfinite(conservatism)))
+    const int S = sweep_blocks(p);
+    if (S > 1) {
+        if (grad) return invalid("a conservatism sweep has no gradient");
+        if (p.mode == CS_METRIC_FLAGS) return invalid("the flags mode takes no conservatism sweep");
+        if (p.host_io) return invalid("a conservatism sweep takes device buffers (host_io must be 0)");
+        if (p.nsigma_per_query) return invalid("a conservatism sweep takes no nsigma_per_query");
+        if (Q * S > kMaxRows) return invalid("Q * sweep_count out of range [0, 2^30]");
+    } else if (!p.nsigma_per_query && (!(conservatism >= 0.f) || !isfinite(conservatism))) {
         return invalid("conservatism (n_sigma) must be finite and >= 0");
+    }
     const bool flags = p.mode == CS_METRIC_FLAGS;
     if (flags && grad) return invalid("the flags mode has no gradient");
     if (flags) {  // only collision flags are computed
@@ -331,12 +358,13 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     } else if ((st = get_workspace(sc->device, stream, (size_t)Q, p.host_io != 0, &ws)) != CS_OK) {
         return st;
     }
+    if (S > 1 && (st = sweep_reserve(ws, Q, prim_type, S)) != CS_OK) return st;
 
     const float *d_prims = prims, *d_ns = p.nsigma_per_query, *d_gout = grad_out;
     float *d_metric = out_metric, *d_grad = grad_centres, *d_gm = p.out_group_metric;
     uint8_t *d_col = out_collide, *d_gc = p.out_group_collide;
     int32_t *d_cnt = p.out_count;
-    const int ng = p.group_size > 0 ? (int)((Q + p.group_size - 1) / p.group_size) : 0;
+    const int ng = p.group_size > 0 ? (int)((Q + p.group_size - 1) / p.group_size) : 0;  // per n_sigma block
     if (p.host_io) {
         CS_CUDA(cudaMemcpyAsync(ws->io_prims, prims, 4 * stride * Q, cudaMemcpyHostToDevice, stream));
         d_prims = ws->io_prims;
@@ -362,18 +390,38 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     }
 
     uint32_t *perm = nullptr;
-    launch_prep(d_prims, prim_type, (int)Q, sc->dev, conservatism, d_ns, *ws, &perm, stream);
+    launch_prep(d_prims, prim_type, (int)Q, sc->dev, S > 1 ? 0.f : conservatism, d_ns, *ws, &perm, stream);
     CS_CUDA(cudaGetLastError());
+    const float4 *rows = ws->qrec;
+    const float *rows_ns = ws->qns;
+    int64_t Qrows = Q;
+    if (S > 1) {
+        // the S copies of every sorted row next to each other: one tile holds
+        // all n_sigma values of its primitives, which share staged chunks
+        const int recs = prim_type == CS_PRIM_SPHERE ? 1 : 3;
+        CS_CUDA(cudaMemcpyAsync(ws->sweep_rec, ws->qrec, sizeof(float4) * recs * (size_t)Q, cudaMemcpyDeviceToDevice,
+                                stream));
+        uint32_t *perm2 = perm == ws->vals[0] ? ws->vals[1] : ws->vals[0];
+        float *ns2 = reinterpret_cast<float *>(ws->keys[0]);
+        launch_sweep_expand(ws->sweep_rec, perm, (int)Q, recs, S, p.sweep_nsigma, ws->qrec, ns2, perm2, stream);
+        CS_CUDA(cudaGetLastError());
+        perm = perm2;
+        rows_ns = ns2;
+        Qrows = Q * S;
+    }
     unsigned *gflags = nullptr;  // flags mode: a row of the group collides (early exit of the others)
     if (flags && p.group_size > 0) {
         gflags = reinterpret_cast<unsigned *>(ws->io_metric);
         CS_CUDA(cudaMemsetAsync(gflags, 0, 4 * (size_t)ng, stream));
     }
-    CS_CUDA(run_eval(prim_type, sc->dev, ws->qrec, ws->qns, perm, (int)Q, p, grad ? nullptr : d_metric,
+    CS_CUDA(run_eval(prim_type, sc->dev, rows, rows_ns, perm, (int)Qrows, p, grad ? nullptr : d_metric,
                      grad ? nullptr : d_col, grad ? nullptr : d_cnt, d_gout, grad ? d_grad : nullptr,
                      ws->err, sc->num_sms, kWaitPolls, stream, gflags));
     if (!grad && has_group) {
-        launch_group(d_metric, d_col, (int)Q, p.group_size, d_gm, d_gc, stream);
+        for (int b = 0; b < S; ++b)  // groups within each n_sigma block
+            launch_group(d_metric ? d_metric + (size_t)b * Q : nullptr, d_col ? d_col + (size_t)b * Q : nullptr,
+                         (int)Q, p.group_size, d_gm ? d_gm + (size_t)b * ng : nullptr,
+                         d_gc ? d_gc + (size_t)b * ng : nullptr, stream);
         CS_CUDA(cudaGetLastError());
     }
     if (p.host_io) {

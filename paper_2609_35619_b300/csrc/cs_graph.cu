@@ -122,7 +122,12 @@ cs_status cs_graph_create(const cs_scene *scene, int32_t prim_type, const float 
     if (grad && (out_metric || out_collide))
         return invalid("an adjoint graph takes grad_centres only (out_metric, out_collide NULL)");
     p.eval_events[0] = p.eval_events[1] = nullptr;
-    return capture_graph([&](Workspace *w) { return grow_workspace(w, (size_t)Q, false); },
+    if ((st = check_params(p)) != CS_OK) return st;
+    const int S = sweep_blocks(p);
+    return capture_graph([&](Workspace *w) {
+                             cs_status r = grow_workspace(w, (size_t)Q, false);
+                             return (r != CS_OK || S == 1) ? r : sweep_reserve(w, Q, prim_type, S);
+                         },
                          [&](cudaStream_t s, Workspace *w) {
                              p.stream = s;
                              return query_common(scene, prim_type, prims, Q, conservatism, &p, grad, out_metric,

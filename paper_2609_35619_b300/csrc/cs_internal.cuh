@@ -114,6 +114,8 @@ struct Workspace {
     // rendering scratch (cs_render): projections, instance lists, sort buffers
     void *rnd = nullptr;             size_t cap_rnd = 0;   // bytes: per (view, slot)
     void *rnd2 = nullptr;            size_t cap_rnd2 = 0;  // bytes: per instance
+    // conservatism sweep (cs_params.sweep_count): the prepared rows before expansion
+    float4 *sweep_rec = nullptr;     size_t cap_sweep = 0; // float4
     unsigned *err = nullptr;         // device error word
 };
 
@@ -191,6 +193,17 @@ cs_status cuda_fail(cudaError_t e, const char *what);
 cs_status invalid(const char *msg);
 cs_status check_scene(const cs_scene *s);
 cs_status check_params(const cs_params &p);
+// The number of n_sigma blocks of a call (1 without a sweep).
+inline int sweep_blocks(const cs_params &p) { return p.sweep_count >= 2 ? p.sweep_count : 1; }
+struct SweepNs {
+    float v[8];
+};
+// Scratch of a sweep over Q rows (workspace for S Q rows, the unexpanded rows).
+cs_status sweep_reserve(Workspace *w, int64_t Q, int prim_type, int S);
+// Expand Q prepared rows (sorted) into S consecutive rows each: records,
+// n_sigma of block s, output row s Q + perm[p].
+void launch_sweep_expand(const float4 *rec_in, const uint32_t *perm_in, int Q, int recs, int S, const float *ns,
+                         float4 *rec_out, float *ns_out, uint32_t *perm_out, cudaStream_t s);
 
 #define CS_CUDA(call)                                                  \
     do {                                                               \

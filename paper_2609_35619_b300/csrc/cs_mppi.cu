@@ -250,6 +250,7 @@ cs_status mppi_common(const cs_scene *scene, const cs_mppi_desc *d, const float 
     cs_params q = p;
     q.mode = CS_METRIC_MEAN_COST;
     q.group_size = d->T;
+    q.sweep_count = 0;
     q.nsigma_per_query = nullptr;
     q.out_count = nullptr;
     q.out_group_metric = col;
@@ -333,6 +334,7 @@ cs_status cs_path_refine(const cs_scene *scene, const cs_refine_desc *d, const f
     cs_params q = p;
     q.mode = CS_METRIC_MEAN_COST;
     q.group_size = (int32_t)P;
+    q.sweep_count = 0;
     q.nsigma_per_query = nullptr;
     q.out_count = nullptr;
     q.out_group_metric = col;

@@ -91,6 +91,7 @@ extern "C" cs_status cs_query_noalloc(const cs_scene *scene, int32_t prim_type, 
     else cs_params_init(&p);
     if ((st = check_params(p)) != CS_OK) return st;
     if (p.host_io) return invalid("cs_query_noalloc takes device pointers only (host_io must be 0)");
+    if (p.sweep_count >= 2) return invalid("cs_query_noalloc takes no conservatism sweep");
     if (prim_type != CS_PRIM_SPHERE && prim_type != CS_PRIM_ELLIPSOID)
         return invalid("prim_type must be CS_PRIM_SPHERE or CS_PRIM_ELLIPSOID");
     if (Q < 0 || Q > (int64_t)kRows)

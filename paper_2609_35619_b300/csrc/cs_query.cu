@@ -1494,6 +1494,30 @@ void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, f
     *perm_out = perm;
 }
 
+// Row e = p S + s of a sweep: sorted row p at n_sigma value s, written to
+// output row s Q + perm[p].
+__global__ void k_sweep_expand(const float4 *__restrict__ rec_in, const uint32_t *__restrict__ perm_in, int Q,
+                               int recs, int S, SweepNs ns, float4 *__restrict__ rec_out, float *__restrict__ ns_out,
+                               uint32_t *__restrict__ perm_out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)Q * S) return;
+    const int64_t p = e / S;
+    const int s = (int)(e - p * S);
+    for (int r = 0; r < recs; ++r) rec_out[e * recs + r] = rec_in[p * recs + r];
+    ns_out[e] = ns.v[s];
+    perm_out[e] = (uint32_t)s * (uint32_t)Q + perm_in[p];
+}
+
+void launch_sweep_expand(const float4 *rec_in, const uint32_t *perm_in, int Q, int recs, int S, const float *ns,
+                         float4 *rec_out, float *ns_out, uint32_t *perm_out, cudaStream_t s) {
+    SweepNs v;
+    for (int k = 0; k < 8; ++k) v.v[k] = k < S ? ns[k] : 0.f;
+    const int64_t n = (int64_t)Q * S;
+    k_sweep_expand<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec_in, perm_in, Q, recs, S, v, rec_out, ns_out,
+                                                               perm_out);
+    count_launches(1);
+}
+
 void launch_group(const float *metric, const uint8_t *collide, int Q, int G, float *gm, uint8_t *gc,
                   cudaStream_t s) {
     const int64_t ng = (Q + G - 1) / G;

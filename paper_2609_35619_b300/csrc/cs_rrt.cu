@@ -195,6 +195,7 @@ cs_status rrt_common(const cs_scene *scene, const cs_rrt_desc *d, float *nodes, 
     cs_params q = p;
     q.mode = CS_METRIC_FLAGS;
     q.group_size = d->M;
+    q.sweep_count = 0;
     q.nsigma_per_query = nullptr;
     q.out_count = nullptr;
     q.out_group_metric = nullptr;

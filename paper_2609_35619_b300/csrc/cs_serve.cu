@@ -390,6 +390,7 @@ cs_status cs_server_create(cs_scene *const *scenes, int32_t n_scenes, const cs_s
     p.tile_config = c.tile_config;
     cs_status st = check_params(p);
     if (st != CS_OK) return st;
+    if (p.sweep_count >= 2) return invalid("the server takes no conservatism sweep (n_sigma is per request)");
     Server *srv = new Server();
     srv->cfg = c;
     for (int i = 0; i < n_scenes; ++i) {

@@ -409,3 +409,39 @@ def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
                 np.testing.assert_array_equal(a.view(np.uint8), b.view(np.uint8), err_msg=f"{mode} {v} {k}")
             np.testing.assert_array_equal(one["group_metric"][i * (Q // 64):(i + 1) * (Q // 64)].cpu().numpy(),
                                           sep["group_metric"].cpu().numpy())
+
+
+@pytest.mark.parametrize("prim_type", [0, 1])
+def test_sweep_parameter_equals_separate_calls(cs, prim_type):
+    """cs_params.sweep_count: one call over Q rows at S n_sigma values gives
+    block s exactly the bits of its own call (metric, flag, count, groups
+    within each block, with a ragged last group), in every metric mode."""
+    sc = S.tiny_scene(n=3000)
+    scene = _scene(cs, sc)
+    rng = np.random.default_rng(90 + prim_type)
+    Q, G = 1003, 10
+    c = rng.uniform(0, 2, (Q, 3))
+    q = (np.c_[c, rng.uniform(0.05, 0.25, Q)] if prim_type == 0
+         else S.ellipsoid_queries(91, c, semi_lo=0.04, semi_hi=0.2)).astype(np.float32)
+    sweep = (0.0, 0.5, 1.0, 2.0, 1.25)
+    ng = (Q + G - 1) // G
+    for mode in (0, 1, 2, 3):
+        one = scene.query(torch.as_tensor(q), 0.0, prim_type=prim_type, want_count=True,
+                          params=cs.QueryParams(mode=mode, group_size=G, sweep=sweep))
+        torch.cuda.synchronize()
+        assert one["metric"].shape[0] == len(sweep) * Q and one["group_metric"].shape[0] == len(sweep) * ng
+        for s, ns in enumerate(sweep):
+            sep = scene.query(torch.as_tensor(q), ns, prim_type=prim_type, want_count=True,
+                              params=cs.QueryParams(mode=mode, group_size=G))
+            torch.cuda.synchronize()
+            for k in ("metric", "collide", "count"):
+                np.testing.assert_array_equal(one[k][s * Q:(s + 1) * Q].cpu().numpy().view(np.uint8),
+                                              sep[k].cpu().numpy().view(np.uint8), err_msg=f"{mode} {ns} {k}")
+            for k in ("group_metric", "group_collide"):
+                np.testing.assert_array_equal(one[k][s * ng:(s + 1) * ng].cpu().numpy().view(np.uint8),
+                                              sep[k].cpu().numpy().view(np.uint8), err_msg=f"{mode} {ns} {k}")
+    with pytest.raises(cs.CsError):  # no adjoint for a sweep
+        scene.query_grad(torch.as_tensor(q), 0.0, prim_type=prim_type, params=cs.QueryParams(sweep=sweep))
+    with pytest.raises(cs.CsError):  # no flags mode for a sweep
+        scene.query(torch.as_tensor(q), 0.0, prim_type=prim_type,
+                    params=cs.QueryParams(mode=cs.CS_METRIC_FLAGS, sweep=sweep))
