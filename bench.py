@@ -42,7 +42,7 @@ OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes
 TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": 42.114e6 + 0.038e6,
            "case": "262,144 arm spheres, tile 22, n_sigma 1"}
 WORKLOAD = ("tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres "
-            "fwd+adjoint (the arm sweep as one launch with n_sigma per row)")
+            "fwd+adjoint (each batch's conservatism sweep as one launch)")
 
 
 def parse():
@@ -163,11 +163,6 @@ def run_ours(args, rank, world):
     with torch.cuda.stream(stream):
         d_scene = {k: torch.as_tensor(v, device=dev) for k, v in scene_h.items()}
         d_arm = torch.as_tensor(arm_h, device=dev)
-        # the arm sweep in one launch: the batch once per n_sigma, n_sigma per row
-        # (the same bits per row as separate launches; copies of a sparse batch
-        # share tiles and staged chunks)
-        d_arm_sw = d_arm.repeat(len(NSIGMAS), 1).contiguous()
-        d_ns_arm = torch.as_tensor(np.repeat(np.asarray(NSIGMAS, np.float32), arm_h.shape[0]), device=dev)
         d_edge = torch.as_tensor(edge_h, device=dev)
         d_poses = torch.as_tensor(poses_h, device=dev)
         d_offs = torch.as_tensor(offs_h, device=dev)
@@ -175,8 +170,8 @@ def run_ours(args, rank, world):
         n_pose = poses_h.shape[0]
         ones = torch.ones(n_pose, dtype=torch.float32, device=dev)
         outs = {}
-        for name, q, G in (("arm", d_arm_sw, 64), ("edge", d_edge, 1024)):
-            Q = q.shape[0]
+        for name, q, G in (("arm", d_arm, 64), ("edge", d_edge, 1024)):
+            Q = len(NSIGMAS) * q.shape[0]  # one block of outputs per n_sigma of the sweep
             outs[name] = {"metric": torch.empty(Q, device=dev), "collide": torch.empty(Q, dtype=torch.uint8, device=dev),
                           "group_metric": torch.empty((Q + G - 1) // G, device=dev),
                           "group_collide": torch.empty((Q + G - 1) // G, dtype=torch.uint8, device=dev)}
@@ -195,8 +190,9 @@ def run_ours(args, rank, world):
     else:
         tune_scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
                               device=dev, stream=stream)
-        tiles = {"arm": tune_scene.autotune(d_arm_sw, 1.0, reps=2, stream=stream)[0],
-                 "edge": tune_scene.autotune(d_edge, 1.0, reps=1, stream=stream)[0],
+        sw = cs.QueryParams(sweep=NSIGMAS)
+        tiles = {"arm": tune_scene.autotune(d_arm, 0.0, params=sw, reps=2, stream=stream)[0],
+                 "edge": tune_scene.autotune(d_edge, 0.0, params=sw, reps=1, stream=stream)[0],
                  "pose": tune_scene.autotune(d_arm, 1.0, reps=2, stream=stream)[0], "source": "cs_autotune"}
         tune_scene.close()
 
@@ -209,11 +205,11 @@ def run_ours(args, rank, world):
                          device=dev, stream=stream)
         if build_ev is not None:
             build_ev[1].record(stream)
-        scene.query(d_arm_sw, 0.0, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
-                    nsigma_per_query=d_ns_arm, eval_events=nxt(), out=outs["arm"], pair_stats=stats)
-        for ns in NSIGMAS:
-            scene.query(d_edge, ns, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"]), stream=stream,
-                        eval_events=nxt(), out=outs["edge"], pair_stats=stats)
+        # the conservatism sweep: one launch per batch for all four n_sigma values
+        scene.query(d_arm, 0.0, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"], sweep=NSIGMAS),
+                    stream=stream, eval_events=nxt(), out=outs["arm"], pair_stats=stats)
+        scene.query(d_edge, 0.0, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"], sweep=NSIGMAS),
+                    stream=stream, eval_events=nxt(), out=outs["edge"], pair_stats=stats)
         with torch.cuda.stream(stream):
             sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
             scene.query(sph, 1.0, params=cs.QueryParams(group_size=K, tile_config=tiles["pose"]), stream=stream,
@@ -230,17 +226,16 @@ def run_ours(args, rank, world):
     cand_pairs, useful_pairs = (int(x) for x in stats.cpu().tolist())
     # forward sphere launches only (the roofline's kernel): rerun without the grad pass
     stats_fwd = torch.zeros(2, dtype=torch.int64, device=dev)
-    sc.query(d_arm_sw, 0.0, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"]), stream=stream,
-             nsigma_per_query=d_ns_arm, out=outs["arm"], pair_stats=stats_fwd)
-    for ns in NSIGMAS:
-        sc.query(d_edge, ns, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"]), stream=stream,
-                 out=outs["edge"], pair_stats=stats_fwd)
+    sc.query(d_arm, 0.0, params=cs.QueryParams(group_size=64, tile_config=tiles["arm"], sweep=NSIGMAS),
+             stream=stream, out=outs["arm"], pair_stats=stats_fwd)
+    sc.query(d_edge, 0.0, params=cs.QueryParams(group_size=1024, tile_config=tiles["edge"], sweep=NSIGMAS),
+             stream=stream, out=outs["edge"], pair_stats=stats_fwd)
     torch.cuda.synchronize(dev)
     fwd_cand, fwd_useful = (int(x) for x in stats_fwd.cpu().tolist())
     info = sc.info()
     sc.close()
     n_queries = len(NSIGMAS) * (arm_h.shape[0] + edge_h.shape[0]) + 2 * n_pose * K
-    n_fwd_launches = 1 + len(NSIGMAS)
+    n_fwd_launches = 2
 
     for _ in range(args.warmup):
         s, _ = step()
@@ -367,8 +362,7 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
     K = offs_h.shape[0]
     n_pose = poses_h.shape[0]
     copy = torch.cuda.Stream(dev)
-    d_ns_arm = torch.as_tensor(np.repeat(np.asarray(NSIGMAS, np.float32), h_arm.shape[0]), device=dev)
-    sizes = [(len(NSIGMAS) * h_arm.shape[0], 64)] + [(h_edge.shape[0], 1024)] * len(NSIGMAS)
+    sizes = [(len(NSIGMAS) * h_arm.shape[0], 64), (len(NSIGMAS) * h_edge.shape[0], 1024)]
     dev_out, host_out = [], []
     for Q, G in sizes:
         ng = (Q + G - 1) // G
@@ -395,16 +389,12 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
             d_arm = h_arm.to(dev, non_blocking=True)
             d_edge = h_edge.to(dev, non_blocking=True)
             d_poses = h_poses.to(dev, non_blocking=True)
-            d_arm_sw = d_arm.repeat(len(NSIGMAS), 1)
-        passes = [("arm", d_arm_sw, 64, 0.0, d_ns_arm)] + [("edge", d_edge, 1024, ns, None) for ns in NSIGMAS]
-        for i, (name, dq, G, ns, nsq) in enumerate(passes):
+        for i, (name, dq, G) in enumerate((("arm", d_arm, 64), ("edge", d_edge, 1024))):
             o = dev_out[i]
-            p = cs.QueryParams(group_size=G, tile_config=tiles[name]).to_c()
+            p = cs.QueryParams(group_size=G, tile_config=tiles[name], sweep=NSIGMAS).to_c()
             p.stream = sh
             p.out_group_metric, p.out_group_collide = o["group_metric"].data_ptr(), o["group_collide"].data_ptr()
-            if nsq is not None:
-                p.nsigma_per_query = nsq.data_ptr()
-            cs.check(cs.abi.cs_query(h, 0, dq, dq.shape[0], ns, o["metric"], o["collide"], p))
+            cs.check(cs.abi.cs_query(h, 0, dq, dq.shape[0], 0.0, o["metric"], o["collide"], p))
             done = torch.cuda.Event()
             done.record(stream)
             copy.wait_event(done)
@@ -930,14 +920,13 @@ def run_eval_case(args):
     kstats = torch.zeros(16, dtype=torch.int64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     if args.sweep:
-        # one launch over the four copies (n_sigma per row) against four launches
+        # one launch over the four n_sigma values (cs_params sweep) against four launches
         Q = arm.shape[0]
-        rows = arm.repeat(len(NSIGMAS), 1).contiguous()
-        nsq = torch.as_tensor(np.repeat(np.asarray(NSIGMAS, np.float32), Q), device=dev)
+        qs = cs.QueryParams(group_size=G, tile_config=args.tile, sweep=tuple(NSIGMAS))
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         for _ in range(2):
-            o1 = scene.query(rows, 0.0, params=qp, prim_type=prim, nsigma_per_query=nsq)
-        scene.query(rows, 0.0, params=qp, prim_type=prim, nsigma_per_query=nsq, eval_events=ev1, out=o1)
+            o1 = scene.query(arm, 0.0, params=qs, prim_type=prim)
+        scene.query(arm, 0.0, params=qs, prim_type=prim, eval_events=ev1, out=o1)
         sep_ms = 0.0
         outs = []
         for ns in NSIGMAS:

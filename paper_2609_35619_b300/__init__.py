@@ -268,14 +268,15 @@ class QueryGraph:
             m = c = None
             g = self.out["grad_centres"]
         else:
-            m = self.out["metric"] = torch.empty(Q, dtype=torch.float32, device=dev)
-            c = self.out["collide"] = torch.empty(Q, dtype=torch.uint8, device=dev)
+            S = len(params.sweep) if len(params.sweep) >= 2 else 1  # n_sigma blocks of a sweep
+            m = self.out["metric"] = torch.empty(S * Q, dtype=torch.float32, device=dev)
+            c = self.out["collide"] = torch.empty(S * Q, dtype=torch.uint8, device=dev)
             g = None
             if want_count:
-                self.out["count"] = torch.empty(Q, dtype=torch.int32, device=dev)
+                self.out["count"] = torch.empty(S * Q, dtype=torch.int32, device=dev)
                 p.out_count = abi.ptr(self.out["count"])
             if params.group_size > 0:
-                ng = (Q + params.group_size - 1) // params.group_size
+                ng = S * ((Q + params.group_size - 1) // params.group_size)
                 self.out["group_metric"] = torch.empty(ng, dtype=torch.float32, device=dev)
                 self.out["group_collide"] = torch.empty(ng, dtype=torch.uint8, device=dev)
                 p.out_group_metric = abi.ptr(self.out["group_metric"])

@@ -311,7 +311,7 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     if (Q < 0 || Q > kMaxRows) return invalid("Q out of range [0, 2^30]");
     if (p.tile_config == CS_TILE_TUNED) {
         std::lock_guard<std::mutex> lk(sc->tune_mu);
-        auto it = sc->tuned.find(tune_key(prim_type, p.mode, Q));
+        auto it = sc->tuned.find(tune_key(prim_type, p.mode, Q * sweep_blocks(p)));  // the launch's rows
         p.tile_config = it == sc->tuned.end() ? 0 : it->second;
     }
     const int S = sweep_blocks(p);

@@ -237,6 +237,9 @@ cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, in
     cudaStream_t s = (cudaStream_t)p.stream;
     Workspace *ws = nullptr;
     if ((st = get_workspace(sc->device, s, (size_t)Q, false, &ws)) != CS_OK) return st;
+    // a sweep's scratch first: the per-row output below must not move afterwards
+    const int S = sweep_blocks(p);
+    if (S > 1 && (st = sweep_reserve(ws, Q, prim_type, S)) != CS_OK) return st;
     // timed launches write to scratch only: per-row metric, no groups
     p.group_size = 0;
     p.out_count = nullptr;
@@ -285,7 +288,7 @@ cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, in
     if (st != CS_OK) return st;
     {
         std::lock_guard<std::mutex> lk(sc->tune_mu);
-        sc->tuned[tune_key(prim_type, p.mode, Q)] = best_id;
+        sc->tuned[tune_key(prim_type, p.mode, Q * S)] = best_id;  // keyed by the launch's rows
     }
     *best = best_id;
     return CS_OK;

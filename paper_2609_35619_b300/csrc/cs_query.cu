@@ -41,6 +41,7 @@ struct QueryConsts {
     int mode;
     int group_size;
     int exact;      // sigma^2 is the exact variance of the quadratic form (Eq. 5)
+    int sweep;      // n_sigma blocks of a conservatism sweep (1: none)
 };
 
 struct EvalArgs {
@@ -635,21 +636,30 @@ struct LaneG2 {
 // the Eq. 11 exponent in packed FP32x2: the same operations in the same
 // order as pair_update, hence the same bits; half 0 is accumulated before
 // half 1, so each lane still adds its Gaussians in increasing order.
-template <int QW, bool EX>
-__device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, const LaneG2 &g,
-                                               const float4 *qd, const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
+// The geometry part: |d|^2 and sqrt(d^T Sigma d [+ trace term]) for the
+// sphere of `qd` and the lane's two Gaussians (it depends on the sphere's
+// centre only, not on its n_sigma).
+template <bool EX>
+__device__ __forceinline__ void geom_g2(const LaneG2 &g, const float4 *qd, f32x2 &r2, f32x2 &sq) {
     const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&qd[0]);  // -cx, -cy
     const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
-    const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
     const f32x2 dx = add2(g.x, pa.x), dy = add2(g.y, pa.y), dz = add2(g.z, pb.x);
-    const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     const f32x2 t1 = fma2(g.sxz2, dz, fma2(g.sxy2, dy, mul2(g.sxx, dx)));
     const f32x2 t2 = fma2(g.syz2, dz, mul2(g.syy, dy));
     const f32x2 zz = mul2(g.szz, dz);
     const f32x2 u = fma2(dx, t1, fma2(dy, t2, EX ? fma2(dz, zz, g.f) : mul2(dz, zz)));
     float u0, u1;
     upk2(u, u0, u1);
-    const f32x2 sq = pk2(sqrt_approx(fmaxf(u0, 0.f)), sqrt_approx(fmaxf(u1, 0.f)));
+    sq = pk2(sqrt_approx(fmaxf(u0, 0.f)), sqrt_approx(fmaxf(u1, 0.f)));
+}
+
+// The rest for row j with its own n_sigma (qd[2]) and scale (qd[1]).
+template <int QW>
+__device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2, f32x2 sq, const float4 *qd,
+                                        const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
+    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
+    const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
     float r0, r1;
     upk2(fma2(nns2, sq, r2), r0, r1);
     const f32x2 st = mul2(pk2(fmaxf(r0, 0.f), fmaxf(r1, 0.f)), pb.y);
@@ -662,6 +672,14 @@ __device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, c
     A.cin[j] += ((s0 < k.T_in) ? 1 : 0) + ((s1 < k.T_in) ? 1 : 0);
     A.sum[j] += nb0 ? dc0 : 0.f;
     A.sum[j] += nb1 ? dc1 : 0.f;
+}
+
+template <int QW, bool EX>
+__device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, const LaneG2 &g,
+                                               const float4 *qd, const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
+    f32x2 r2, sq;
+    geom_g2<EX>(g, qd, r2, sq);
+    tail_g2<QW>(A, j, r2, sq, qd, k, nG2, Gs2);
 }
 
 // Lane l of a staged chunk: its slot l (padding slots already hold a point
@@ -683,11 +701,11 @@ __device__ __forceinline__ void lane_gaussian(const ChunkBlock &B, const SlotMet
 // `qmask` (the primitives reaching either chunk): lane l holds Gaussian l of
 // each chunk in the two halves of packed registers; spheres are evaluated in
 // groups of GROUP (a member reaching neither chunk adds exactly nothing).
-template <int QW, int GROUP, bool EX>
+template <int QW, int GROUP, bool EX, bool SH>
 __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, const SlotMeta mt0,
                                                 const ChunkBlock &B1, const SlotMeta mt1, unsigned qmask,
                                                 float4 (*wqd)[3], const QueryConsts &k, int lane,
-                                                unsigned &cand, unsigned &c_hits) {
+                                                unsigned &cand, unsigned &c_hits, unsigned same) {
     if (qmask == 0u) return;
     LaneG g0, g1;
     lane_gaussian(B0, mt0, lane, g0);
@@ -711,8 +729,18 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 #pragma unroll
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
         if ((gm >> j0) & 1u) {
+            if (SH && GROUP == 2 && ((same >> j0) & 1u)) {
+                // rows j0 and j0 + 1 are the same sphere (n_sigma copies of a
+                // sweep): the geometry once, then each row's own n_sigma; the
+                // same operations per row as apart, hence the same bits
+                f32x2 r2, sq;
+                geom_g2<EX>(g2, wqd[j0], r2, sq);
+                tail_g2<QW>(A, j0, r2, sq, wqd[j0], k, nG2, Gs2);
+                tail_g2<QW>(A, j0 + 1, r2, sq, wqd[j0 + 1], k, nG2, Gs2);
+            } else {
 #pragma unroll
-            for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW, EX>(A, j, g2, wqd[j], k, nG2, Gs2);
+                for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW, EX>(A, j, g2, wqd[j], k, nG2, Gs2);
+            }
         }
     }
 }
@@ -757,7 +785,7 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
     }
 }
 
-template <int PRIM, class C, int MODE, bool GRAD, bool EX>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX, bool SH>
 __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int warp, bool abort) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int QW = C::QW;
@@ -817,6 +845,19 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         wqd[lane][2] = make_float4(-b.x, -b.x, 0.f, 0.f);
     }
     __syncwarp();
+    // bit j (j even): rows j and j + 1 are the same sphere (centre and radius
+    // bit for bit, both valid), so the packed evaluation shares their geometry
+    unsigned same = 0u;
+    if (SH && PRIM == 0) {
+        bool eq = false;
+        if (lane < QW && (lane & 1) == 0) {
+            const float4 a = wq[lane][0], b = wq[lane + 1][0];
+            eq = ((wvalid >> lane) & 3u) == 3u && __float_as_uint(a.x) == __float_as_uint(b.x) &&
+                 __float_as_uint(a.y) == __float_as_uint(b.y) && __float_as_uint(a.z) == __float_as_uint(b.z) &&
+                 __float_as_uint(a.w) == __float_as_uint(b.w);
+        }
+        same = __ballot_sync(0xffffffffu, eq);
+    }
     // the warp's box of primitive centres and its largest reach parameters:
     // a chunk outside box + reach is out of reach of every primitive here
     float wlx = INFINITY, wly = INFINITY, wlz = INFINITY, whx = -INFINITY, why = -INFINITY, whz = -INFINITY;
@@ -957,9 +998,9 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     }
                     const unsigned qa = __shfl_sync(0xffffffffu, myq, sa);
                     const unsigned qb = sb >= 0 ? __shfl_sync(0xffffffffu, myq, sb) : 0u;
-                    eval_chunk_pair<QW, C::GROUP, EX>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
+                    eval_chunk_pair<QW, C::GROUP, EX, SH>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
                                                   sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd, k,
-                                                  lane, cand, c_hits);
+                                                  lane, cand, c_hits, same);
                 }
             } else {
 #pragma unroll 1
@@ -1070,7 +1111,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     }
 }
 
-template <int PRIM, class C, int MODE, bool GRAD, bool EX = false>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, bool SH = false>
 __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     EvalSmem<C> *sm = reinterpret_cast<EvalSmem<C> *>(smem_raw);
@@ -1090,7 +1131,7 @@ __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalA
     if (warp == C::NCW) {
         if (!abort) producer_warp<PRIM, C, EX>(a, sm, tile, MODE == 3);
     } else {
-        consumer_warp<PRIM, C, MODE, GRAD, EX>(a, sm, tile, warp, abort);
+        consumer_warp<PRIM, C, MODE, GRAD, EX, SH>(a, sm, tile, warp, abort);
     }
 }
 
@@ -1251,6 +1292,7 @@ QueryConsts make_consts(const cs_params &p) {
     k.mode = p.mode;
     k.group_size = p.group_size;
     k.exact = p.exact_variance;
+    k.sweep = sweep_blocks(p);
     return k;
 }
 
@@ -1318,12 +1360,12 @@ int tile_configs(int32_t *ids, int32_t cap) {
     return n;
 }
 
-template <int PRIM, class C, int MODE, bool GRAD, bool EX = false>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, bool SH = false>
 static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
     constexpr int TQ = C::NCW * C::QW;
     const int ntiles = (a.Q + TQ - 1) / TQ;
     const size_t smem = sizeof(EvalSmem<C>);
-    auto kern = k_eval<PRIM, C, MODE, GRAD, EX>;
+    auto kern = k_eval<PRIM, C, MODE, GRAD, EX, SH>;
     static bool attr = false;  // once per instantiation (idempotent)
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1345,6 +1387,18 @@ static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
     if (mode == 0) return launch_eval_t<PRIM, C, 0, false>(a, s);
     if (mode == 1) return launch_eval_t<PRIM, C, 1, false>(a, s);
     return launch_eval_t<PRIM, C, 2, false>(a, s);
+}
+
+// A conservatism sweep's sphere cost launches on the shapes whose warps take
+// consecutive row pairs (the n_sigma copies of a primitive) share the
+// copies' geometry; every other launch keeps the plain evaluation.
+template <int PRIM, class C>
+static cudaError_t launch_mode_sweep(const EvalArgs &a, cudaStream_t s) {
+    if constexpr (PRIM == 0 && C::GROUP == 2 && C::IL != 1) {
+        const bool cost = a.k.mode == CS_METRIC_MEAN_COST || a.k.mode == CS_METRIC_SUM_COST;
+        if (a.k.sweep > 1 && cost) return launch_eval_t<PRIM, C, 0, false, false, true>(a, s);
+    }
+    return launch_mode<PRIM, C>(a, s);
 }
 
 template <int PRIM, class C>
@@ -1402,12 +1456,12 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 15: return launch_mode<PRIM, Cfg15>(a, s);
         case 16: return launch_mode<PRIM, Cfg16>(a, s);
         case 17: return launch_mode<PRIM, Cfg17>(a, s);
-        case 18: return launch_mode<PRIM, Cfg18>(a, s);
-        case 19: return launch_mode<PRIM, Cfg19>(a, s);
+        case 18: return launch_mode_sweep<PRIM, Cfg18>(a, s);
+        case 19: return launch_mode_sweep<PRIM, Cfg19>(a, s);
         case 20: return launch_mode<PRIM, Cfg20>(a, s);
         case 21: return launch_mode<PRIM, Cfg21>(a, s);
-        case 22: return launch_mode<PRIM, Cfg22>(a, s);
-        case 23: return launch_mode<PRIM, Cfg23>(a, s);
+        case 22: return launch_mode_sweep<PRIM, Cfg22>(a, s);
+        case 23: return launch_mode_sweep<PRIM, Cfg23>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }

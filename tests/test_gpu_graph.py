@@ -129,3 +129,21 @@ def test_autotune_records_a_listed_shape(cs, table):
     chosen = scene.query(q, 1.0, params=cs.QueryParams(tile_config=best), want_count=True)
     torch.cuda.synchronize()
     _same(tuned, chosen, ["metric", "collide", "count"])
+
+
+def test_sweep_graph_replays_the_call(cs, table):
+    """A captured conservatism sweep (cs_params.sweep_count) replays the
+    call bit for bit, groups included."""
+    _, scene = table
+    sweep = (0.0, 0.5, 1.0, 2.0)
+    d = torch.as_tensor(S.arm_queries(configs=625), device="cuda").contiguous()  # 40,000 spheres
+    params = cs.QueryParams(group_size=64, sweep=sweep)
+    g = cs.QueryGraph(scene, d, 0.0, params=params, want_count=True)
+    out = g.launch()
+    torch.cuda.synchronize()
+    ref = scene.query(d, 0.0, params=params, want_count=True)
+    torch.cuda.synchronize()
+    for k in ("metric", "collide", "count", "group_metric", "group_collide"):
+        np.testing.assert_array_equal(out[k].cpu().numpy().view(np.uint8), ref[k].cpu().numpy().view(np.uint8),
+                                      err_msg=k)
+    g.close()
