@@ -36,11 +36,13 @@ sys.path.insert(0, ROOT)
 
 NSIGMAS = (0.0, 0.5, 1.0, 2.0)
 OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes)
-# DRAM bytes (read + write) of one forward launch of the fused kernel, from the
-# ncu capture of that case summarised under profiles/, valid for the library
-# version it was taken with (reported as null otherwise)
-TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": 42.114e6 + 0.038e6,
-           "case": "262,144 arm spheres, tile 22, n_sigma 1"}
+# DRAM bytes (read + write) per forward launch of the fused kernel: the mean of
+# the step's two sweep launches from the ncu captures summarised under
+# profiles/ (arm 63.81 MB, edge 316.84 MB), valid for the library version they
+# were taken with (reported as null otherwise)
+TRAFFIC = {"version": "cs_b300 0.5 (sm_103a)", "bytes": (63.813632e6 + 316.836608e6) / 2,
+           "case": "mean of the step's two forward sweep launches, tile 18 (arm 262,144 x 4 rows: 63.8 MB; "
+                   "edge 2,097,152 x 4 rows: 316.8 MB)"}
 WORKLOAD = ("tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres "
             "fwd+adjoint (each batch's conservatism sweep as one launch)")
 
