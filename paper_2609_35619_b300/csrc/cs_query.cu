@@ -76,16 +76,24 @@ struct Cfg {
     static constexpr int NCW = NCW_, QW = QW_, NS = NS_, CHB = CHB_, MINB = MINB_, GROUP = GROUP_;
     // IL = 0: consumer warp w takes rows w QW .. w QW + QW - 1 of the tile (a
     // compact warp box); IL = 1: rows w, w + NCW, ...; IL = 2: row pairs
-    // (2w, 2w + 1), (2w + 2 NCW, 2w + 2 NCW + 1), ...  Spreading a warp's
-    // primitives over the tile evens out the warps' loads (they share the
-    // stage ring, so the slowest sets the pace); pairs keep the two
-    // primitives evaluated together close.
+    // (2w, 2w + 1), (2w + 2 NCW, 2w + 2 NCW + 1), ...; IL = 4: row quads
+    // (4w .. 4w + 3), (4w + 4 NCW ..), ...  Spreading a warp's primitives
+    // over the tile evens out the warps' loads (they share the stage ring, so
+    // the slowest sets the pace); pairs and quads keep the primitives
+    // evaluated together close (the four n_sigma copies of a sweep).
     static constexpr int IL = IL_;
     __device__ static int row(int warp, int j) {
-        return IL == 1 ? j * NCW + warp : IL == 2 ? (j >> 1) * 2 * NCW + 2 * warp + (j & 1) : warp * QW + j;
+        return IL == 1 ? j * NCW + warp
+             : IL == 2 ? (j >> 1) * 2 * NCW + 2 * warp + (j & 1)
+             : IL == 4 ? (j >> 2) * 4 * NCW + 4 * warp + (j & 3)
+                       : warp * QW + j;
     }
     static_assert(CHB <= 32, "one lane tests each chunk slot of a stage");
     static_assert(QW == 8 || QW == 16, "primitive masks are tested 32 / QW chunks per round");
+    static_assert(IL == 0 || IL == 1 || IL == 2 || IL == 4, "row layouts");
+    // warp rows j and j + 2 (j even) are consecutive tile rows: a sweep's
+    // copies can share their geometry over four rows, not just two
+    static constexpr bool QUAD = IL == 0 || IL == 4;
 };
 
 struct SlotMeta {
@@ -701,11 +709,11 @@ __device__ __forceinline__ void lane_gaussian(const ChunkBlock &B, const SlotMet
 // `qmask` (the primitives reaching either chunk): lane l holds Gaussian l of
 // each chunk in the two halves of packed registers; spheres are evaluated in
 // groups of GROUP (a member reaching neither chunk adds exactly nothing).
-template <int QW, int GROUP, bool EX, bool SH>
+template <int QW, int GROUP, bool EX, bool SH, bool QUAD>
 __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, const SlotMeta mt0,
                                                 const ChunkBlock &B1, const SlotMeta mt1, unsigned qmask,
                                                 float4 (*wqd)[3], const QueryConsts &k, int lane,
-                                                unsigned &cand, unsigned &c_hits, unsigned same) {
+                                                unsigned &cand, unsigned &c_hits, unsigned same, unsigned link) {
     if (qmask == 0u) return;
     LaneG g0, g1;
     lane_gaussian(B0, mt0, lane, g0);
@@ -726,21 +734,29 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
     const unsigned ng = (unsigned)__popc(gm) * (unsigned)GROUP;
     c_hits += ng;
     cand += ng * (unsigned)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo));
+    // geometry of the last group evaluated through the shared branch
+    f32x2 r2, sq;
+    bool have = false;
 #pragma unroll
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
         if ((gm >> j0) & 1u) {
             if (SH && GROUP == 2 && ((same >> j0) & 1u)) {
                 // rows j0 and j0 + 1 are the same sphere (n_sigma copies of a
                 // sweep): the geometry once, then each row's own n_sigma; the
-                // same operations per row as apart, hence the same bits
-                f32x2 r2, sq;
-                geom_g2<EX>(g2, wqd[j0], r2, sq);
+                // same operations per row as apart, hence the same bits.
+                // With QUAD, the geometry of group j0 - 2 serves this group
+                // too when row j0 - 1 is the same sphere as row j0.
+                if (!(QUAD && have && ((link >> j0) & 1u))) geom_g2<EX>(g2, wqd[j0], r2, sq);
                 tail_g2<QW>(A, j0, r2, sq, wqd[j0], k, nG2, Gs2);
                 tail_g2<QW>(A, j0 + 1, r2, sq, wqd[j0 + 1], k, nG2, Gs2);
+                have = true;
             } else {
 #pragma unroll
                 for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW, EX>(A, j, g2, wqd[j], k, nG2, Gs2);
+                have = false;
             }
+        } else {
+            have = false;
         }
     }
 }
@@ -845,18 +861,21 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         wqd[lane][2] = make_float4(-b.x, -b.x, 0.f, 0.f);
     }
     __syncwarp();
-    // bit j (j even): rows j and j + 1 are the same sphere (centre and radius
-    // bit for bit, both valid), so the packed evaluation shares their geometry
-    unsigned same = 0u;
+    // same, bit j (j even): rows j and j + 1 are the same sphere (centre and
+    // radius bit for bit, both valid), so the packed evaluation shares their
+    // geometry; link, bit j (j even, j > 0): rows j - 1 and j are too
+    unsigned same = 0u, link = 0u;
     if (SH && PRIM == 0) {
         bool eq = false;
-        if (lane < QW && (lane & 1) == 0) {
+        if (lane < QW - 1) {
             const float4 a = wq[lane][0], b = wq[lane + 1][0];
             eq = ((wvalid >> lane) & 3u) == 3u && __float_as_uint(a.x) == __float_as_uint(b.x) &&
                  __float_as_uint(a.y) == __float_as_uint(b.y) && __float_as_uint(a.z) == __float_as_uint(b.z) &&
                  __float_as_uint(a.w) == __float_as_uint(b.w);
         }
-        same = __ballot_sync(0xffffffffu, eq);
+        const unsigned e = __ballot_sync(0xffffffffu, eq);
+        same = e & 0x55555555u;
+        link = (e & 0xAAAAAAAAu) << 1;
     }
     // the warp's box of primitive centres and its largest reach parameters:
     // a chunk outside box + reach is out of reach of every primitive here
@@ -998,9 +1017,9 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     }
                     const unsigned qa = __shfl_sync(0xffffffffu, myq, sa);
                     const unsigned qb = sb >= 0 ? __shfl_sync(0xffffffffu, myq, sb) : 0u;
-                    eval_chunk_pair<QW, C::GROUP, EX, SH>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
+                    eval_chunk_pair<QW, C::GROUP, EX, SH, C::QUAD>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
                                                   sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd, k,
-                                                  lane, cand, c_hits, same);
+                                                  lane, cand, c_hits, same, link);
                 }
             } else {
 #pragma unroll 1
@@ -1315,6 +1334,8 @@ QueryConsts make_consts(const cs_params &p) {
 //   20, 21: shape 18 evaluating sphere primitives one at a time / in groups of 4
 //   22: 2 x 8, 2 stages x 12 chunks, 6 CTAs/SM (small or sparse batches: more, tighter tiles)
 //   23: 1 x 8, 2 stages x 10 chunks, 8 CTAs/SM
+//   24: shape 18 with row quads interleaved over the consumer warps (a
+//       sweep's four n_sigma copies of a sphere in one warp)
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1338,6 +1359,7 @@ using Cfg20 = Cfg<8, 8, 2, 32, 2, 1, 2>;
 using Cfg21 = Cfg<8, 8, 2, 32, 2, 4, 2>;
 using Cfg22 = Cfg<2, 8, 2, 12, 6, 2, 2>;
 using Cfg23 = Cfg<1, 8, 2, 10, 8, 2, 0>;
+using Cfg24 = Cfg<8, 8, 2, 32, 2, 2, 4>;
 // Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
 // three gradient sums per primitive, so its tiles hold fewer primitives
 //   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
@@ -1349,7 +1371,7 @@ using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
 constexpr int kDefaultGradTile = 2;
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24};
 constexpr int kDefaultTile = 18;
 constexpr int kSmallBatchTile = 23;
 constexpr int kSmallBatchQ = 1 << 17;
@@ -1391,7 +1413,8 @@ static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
 
 // A conservatism sweep's sphere cost launches on the shapes whose warps take
 // consecutive row pairs (the n_sigma copies of a primitive) share the
-// copies' geometry; every other launch keeps the plain evaluation.
+// copies' geometry (over row quads where the layout keeps them together);
+// every other launch keeps the plain evaluation.
 template <int PRIM, class C>
 static cudaError_t launch_mode_sweep(const EvalArgs &a, cudaStream_t s) {
     if constexpr (PRIM == 0 && C::GROUP == 2 && C::IL != 1) {
@@ -1453,7 +1476,7 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 12: return launch_mode<PRIM, Cfg12>(a, s);
         case 13: return launch_mode<PRIM, Cfg13>(a, s);
         case 14: return launch_mode<PRIM, Cfg14>(a, s);
-        case 15: return launch_mode<PRIM, Cfg15>(a, s);
+        case 15: return launch_mode_sweep<PRIM, Cfg15>(a, s);
         case 16: return launch_mode<PRIM, Cfg16>(a, s);
         case 17: return launch_mode<PRIM, Cfg17>(a, s);
         case 18: return launch_mode_sweep<PRIM, Cfg18>(a, s);
@@ -1462,6 +1485,7 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 21: return launch_mode<PRIM, Cfg21>(a, s);
         case 22: return launch_mode_sweep<PRIM, Cfg22>(a, s);
         case 23: return launch_mode_sweep<PRIM, Cfg23>(a, s);
+        case 24: return launch_mode_sweep<PRIM, Cfg24>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }

@@ -411,8 +411,15 @@ def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
                                           sep["group_metric"].cpu().numpy())
 
 
-@pytest.mark.parametrize("prim_type", [0, 1])
-def test_sweep_parameter_equals_separate_calls(cs, prim_type):
+@pytest.mark.parametrize("prim_type,tile,sweep", [
+    (0, 0, (0.0, 0.5, 1.0, 2.0, 1.25)), (1, 0, (0.0, 0.5, 1.0, 2.0, 1.25)),
+    # the shapes whose sweep launches share geometry over row pairs (18, 22)
+    # or row quads (15, 23, 24), with copies aligned to the quads (four
+    # values) or not (three, five)
+    (0, 15, (0.0, 0.5, 1.0, 2.0)), (0, 18, (0.0, 0.5, 1.0, 2.0)), (0, 24, (0.0, 0.5, 1.0, 2.0)),
+    (0, 24, (0.0, 0.5, 1.0, 2.0, 1.25)), (0, 24, (2.0, 0.0, 1.0)), (0, 23, (0.0, 0.5, 1.0, 2.0)),
+    (0, 22, (0.0, 0.5, 1.0, 2.0)), (0, 15, (1.0, 0.5, 0.0))])
+def test_sweep_parameter_equals_separate_calls(cs, prim_type, tile, sweep):
     """cs_params.sweep_count: one call over Q rows at S n_sigma values gives
     block s exactly the bits of its own call (metric, flag, count, groups
     within each block, with a ragged last group), in every metric mode."""
@@ -423,11 +430,11 @@ def test_sweep_parameter_equals_separate_calls(cs, prim_type):
     c = rng.uniform(0, 2, (Q, 3))
     q = (np.c_[c, rng.uniform(0.05, 0.25, Q)] if prim_type == 0
          else S.ellipsoid_queries(91, c, semi_lo=0.04, semi_hi=0.2)).astype(np.float32)
-    sweep = (0.0, 0.5, 1.0, 2.0, 1.25)
+    q[::97] = q[1::97]  # some primitives repeated within the batch
     ng = (Q + G - 1) // G
     for mode in (0, 1, 2, 3):
         one = scene.query(torch.as_tensor(q), 0.0, prim_type=prim_type, want_count=True,
-                          params=cs.QueryParams(mode=mode, group_size=G, sweep=sweep))
+                          params=cs.QueryParams(mode=mode, group_size=G, sweep=sweep, tile_config=tile))
         torch.cuda.synchronize()
         assert one["metric"].shape[0] == len(sweep) * Q and one["group_metric"].shape[0] == len(sweep) * ng
         for s, ns in enumerate(sweep):
