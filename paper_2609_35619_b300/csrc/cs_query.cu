@@ -42,6 +42,11 @@ struct QueryConsts {
     int group_size;
     int exact;      // sigma^2 is the exact variance of the quadratic form (Eq. 5)
     int sweep;      // n_sigma blocks of a conservatism sweep (1: none)
+    // The packed cost path leaves out the clamp max(., 0) of Eq. 8.  A
+    // negative unclamped st2 must then give what the clamped 0 gives:
+    float S_cut_u;  // S_cut, or -inf when S_cut < 0 (then 0 is no neighbour)
+    float T_in_u;   // T_in, or -inf when T_in <= 0
+    float E_cap;    // min(G s_min, 0), the cap of the Eq. 11 exponent
 };
 
 struct EvalArgs {
@@ -641,9 +646,10 @@ struct LaneG2 {
 
 // One sphere (cost reductions, forward) against the lane's two Gaussians
 // (one from each chunk of a chunk pair), with the geometry of Eq. 5, 7, 8 and
-// the Eq. 11 exponent in packed FP32x2: the same operations in the same
-// order as pair_update, hence the same bits; half 0 is accumulated before
-// half 1, so each lane still adds its Gaussians in increasing order.
+// the Eq. 11 exponent in packed FP32x2: the operations of pair_update in
+// its order (less the clamp of Eq. 8, which tail_g2 replaces exactly), hence
+// the same bits; half 0 is accumulated before half 1, so each lane still
+// adds its Gaussians in increasing order.
 // The geometry part: |d|^2 and sqrt(d^T Sigma d [+ trace term]) for the
 // sphere of `qd` and the lane's two Gaussians (it depends on the sphere's
 // centre only, not on its n_sigma).
@@ -663,21 +669,27 @@ __device__ __forceinline__ void geom_g2(const LaneG2 &g, const float4 *qd, f32x2
 }
 
 // The rest for row j with its own n_sigma (qd[2]) and scale (qd[1]).
+// st2 is not clamped at 0 here; the outputs still equal those of the clamped
+// value bit for bit.  Where st2 >= 0 nothing changes.  Where st2 < 0 (the
+// clamped value is 0):
+//   - e = -G st2 + G s_min >= G s_min, so min(e, min(G s_min, 0)) is
+//     min(G s_min, 0), the capped exponent of st2 = 0 (for st2 >= 0,
+//     e <= G s_min and the cap leaves min(e, 0));
+//   - st2 <= S_cut_u and st2 < T_in_u hold exactly when 0 <= S_cut and
+//     0 < T_in, as for the clamped value.
 template <int QW>
 __device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2, f32x2 sq, const float4 *qd,
                                         const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
     const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
     const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
-    float r0, r1;
-    upk2(fma2(nns2, sq, r2), r0, r1);
-    const f32x2 st = mul2(pk2(fmaxf(r0, 0.f), fmaxf(r1, 0.f)), pb.y);
+    const f32x2 st = mul2(fma2(nns2, sq, r2), pb.y);
     float e0, e1, s0, s1;
     upk2(fma2(st, nG2, Gs2), e0, e1);
     upk2(st, s0, s1);
-    const float dc0 = ex2_approx(fminf(e0, 0.f)), dc1 = ex2_approx(fminf(e1, 0.f));
-    const bool nb0 = s0 <= k.S_cut, nb1 = s1 <= k.S_cut;
+    const float dc0 = ex2_approx(fminf(e0, k.E_cap)), dc1 = ex2_approx(fminf(e1, k.E_cap));
+    const bool nb0 = s0 <= k.S_cut_u, nb1 = s1 <= k.S_cut_u;
     A.cnt[j] += (nb0 ? 1 : 0) + (nb1 ? 1 : 0);
-    A.cin[j] += ((s0 < k.T_in) ? 1 : 0) + ((s1 < k.T_in) ? 1 : 0);
+    A.cin[j] += ((s0 < k.T_in_u) ? 1 : 0) + ((s1 < k.T_in_u) ? 1 : 0);
     A.sum[j] += nb0 ? dc0 : 0.f;
     A.sum[j] += nb1 ? dc1 : 0.f;
 }
@@ -1300,8 +1312,11 @@ QueryConsts make_consts(const cs_params &p) {
     k.S_cut = (float)S_cut;
     k.S_reach = (float)std::max(S_cut, 1.0);
     k.T_in = S_cut >= 1.0 ? 1.f : nextafterf(k.S_cut, INFINITY);
+    k.S_cut_u = k.S_cut >= 0.f ? k.S_cut : -INFINITY;
+    k.T_in_u = k.T_in > 0.f ? k.T_in : -INFINITY;
     k.G = (float)((double)p.gamma * 1.4426950408889634);
     k.Gsmin = (float)((double)p.gamma * 1.4426950408889634 * (double)p.s_min);
+    k.E_cap = std::min(k.Gsmin, 0.f);
     k.s_min = p.s_min;
     k.d_max = p.d_max;
     k.gamma = p.gamma;

@@ -110,6 +110,27 @@ def test_nondefault_metric_parameters(cs):
                 f"params mode={mode}")
 
 
+@pytest.mark.parametrize("s_min", [-1.0, -2.5, -10.0])
+def test_negative_s_min(cs, s_min):
+    """s_min below 0: Eq. 11 is then below d_max even at st^2 = 0, the cutoff
+    S_cut = s_min + ln(1/eps)/gamma drops below 1 (-2.5) or below 0 (-10:
+    no neighbours at all).  The packed cost path, which does not clamp st^2 at
+    0, must still give the clamped answers where st^2 would be negative."""
+    sc = S.tiny_scene()
+    q = S.tiny_queries()
+    q[:, 3] *= 3.0  # large spheres: many pairs with st^2 clamped to 0
+    kw = dict(s_min=s_min)
+    scene = _scene(cs, sc)
+    for mode in (0, 1, 3):
+        out = _run(cs, scene, q, 2.0, mode=mode, **kw)
+        orc = oracle.query(sc, q, 0, 2.0, oracle.Params(**kw))
+        compare(out, orc, mode, oracle.Params(**kw), f"s_min={s_min} mode={mode}")
+        if s_min == -10.0:
+            assert (out["count"] == 0).all() and (out["collide"] == 0).all()
+        elif mode == 0:
+            assert (orc["count_nbr"] > 0).mean() > 0.3
+
+
 def test_group_outputs(cs):
     sc = S.tiny_scene()
     q = S.tiny_queries(q=1000)
