@@ -193,9 +193,11 @@ def run_ours(args, rank, world):
         tune_scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
                               device=dev, stream=stream)
         sw = cs.QueryParams(sweep=NSIGMAS)
+        with torch.cuda.stream(stream):
+            tune_pose = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)  # the step's own pose spheres
         tiles = {"arm": tune_scene.autotune(d_arm, 0.0, params=sw, reps=2, stream=stream)[0],
                  "edge": tune_scene.autotune(d_edge, 0.0, params=sw, reps=1, stream=stream)[0],
-                 "pose": tune_scene.autotune(d_arm, 1.0, reps=2, stream=stream)[0], "source": "cs_autotune"}
+                 "pose": tune_scene.autotune(tune_pose, 1.0, reps=2, stream=stream)[0], "source": "cs_autotune"}
         tune_scene.close()
 
     def step(events=None, stats=None, build_ev=None):
