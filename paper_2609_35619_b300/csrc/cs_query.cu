@@ -108,6 +108,13 @@ struct SlotMeta {
     int pad;
 };
 
+// Variants of the sphere cost kernels (the SH template parameter, bit flags):
+// kShGeom: the n_sigma copies of a conservatism sweep share their pair
+// geometry; kShK0: k_thr = 0, so a row collides iff its smallest st2 is
+// below T_in, and a running minimum replaces the in-collision count.
+constexpr int kShGeom = 1;
+constexpr int kShK0 = 2;
+
 // Per-primitive data in shared memory, 4 float4 (QREC) per primitive:
 //   sphere:    (c, 1/r^2) (2n, alpha, beta, live) - -
 //   ellipsoid: (c, 2n) (Axx, Ayy, Azz, Axy) (Axz, Ayz, alpha, beta) (live, 1/a_min, - -)
@@ -131,6 +138,9 @@ struct __align__(16) EvalSmem {
     // spheres, each value duplicated for packed evaluation against two
     // Gaussians at once: (-cx, -cx, -cy, -cy) (-cz, -cz, 1/r^2, 1/r^2) (-2n, -2n, 0, 0)
     float4 qd[C::NCW * C::QW][3];
+    // per consumer warp: the stage's slots that pass the warp test, by rank
+    // (the quad tests of sweep launches)
+    int slots[C::NCW][32];
 };
 
 template <int PRIM> struct PrimTraits;
@@ -441,6 +451,9 @@ struct Acc {
     float gx[GRAD ? QW : 1], gy[GRAD ? QW : 1], gz[GRAD ? QW : 1];
     int cnt[MODE == 3 ? 1 : QW];
     int cin[GRAD ? 1 : QW];
+    // sphere cost launches with k_thr = 0: the smallest st2 instead of the
+    // in-collision count (a row collides iff it is below T_in)
+    float mst[(MODE == 0 && !GRAD && PRIM == 0) ? QW : 1];
 };
 
 // Lane-local Gaussian of the current chunk slot (f: tr(Sigma^2)/2, set for
@@ -677,7 +690,7 @@ __device__ __forceinline__ void geom_g2(const LaneG2 &g, const float4 *qd, f32x2
 //     e <= G s_min and the cap leaves min(e, 0));
 //   - st2 <= S_cut_u and st2 < T_in_u hold exactly when 0 <= S_cut and
 //     0 < T_in, as for the clamped value.
-template <int QW>
+template <int QW, bool K0>
 __device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2, f32x2 sq, const float4 *qd,
                                         const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
     const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
@@ -689,17 +702,21 @@ __device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2
     const float dc0 = ex2_approx(fminf(e0, k.E_cap)), dc1 = ex2_approx(fminf(e1, k.E_cap));
     const bool nb0 = s0 <= k.S_cut_u, nb1 = s1 <= k.S_cut_u;
     A.cnt[j] += (nb0 ? 1 : 0) + (nb1 ? 1 : 0);
-    A.cin[j] += ((s0 < k.T_in_u) ? 1 : 0) + ((s1 < k.T_in_u) ? 1 : 0);
+    if constexpr (K0) {
+        A.mst[j] = fminf(A.mst[j], fminf(s0, s1));
+    } else {
+        A.cin[j] += ((s0 < k.T_in_u) ? 1 : 0) + ((s1 < k.T_in_u) ? 1 : 0);
+    }
     A.sum[j] += nb0 ? dc0 : 0.f;
     A.sum[j] += nb1 ? dc1 : 0.f;
 }
 
-template <int QW, bool EX>
+template <int QW, bool EX, bool K0>
 __device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, const LaneG2 &g,
                                                const float4 *qd, const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
     f32x2 r2, sq;
     geom_g2<EX>(g, qd, r2, sq);
-    tail_g2<QW>(A, j, r2, sq, qd, k, nG2, Gs2);
+    tail_g2<QW, K0>(A, j, r2, sq, qd, k, nG2, Gs2);
 }
 
 // Lane l of a staged chunk: its slot l (padding slots already hold a point
@@ -721,11 +738,12 @@ __device__ __forceinline__ void lane_gaussian(const ChunkBlock &B, const SlotMet
 // `qmask` (the primitives reaching either chunk): lane l holds Gaussian l of
 // each chunk in the two halves of packed registers; spheres are evaluated in
 // groups of GROUP (a member reaching neither chunk adds exactly nothing).
-template <int QW, int GROUP, bool EX, bool SH, bool QUAD>
+template <int QW, int GROUP, bool EX, int SH, bool QUAD>
 __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, const SlotMeta mt0,
                                                 const ChunkBlock &B1, const SlotMeta mt1, unsigned qmask,
                                                 float4 (*wqd)[3], const QueryConsts &k, int lane,
                                                 unsigned &cand, unsigned &c_hits, unsigned same, unsigned link) {
+    constexpr bool K0 = (SH & kShK0) != 0;
     if (qmask == 0u) return;
     LaneG g0, g1;
     lane_gaussian(B0, mt0, lane, g0);
@@ -752,19 +770,24 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 #pragma unroll
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
         if ((gm >> j0) & 1u) {
-            if (SH && GROUP == 2 && ((same >> j0) & 1u)) {
+            if ((SH & kShGeom) && GROUP == 4 && ((same >> j0) & (same >> (j0 + 2)) & (link >> (j0 + 2)) & 1u)) {
+                // rows j0 .. j0 + 3 are one sphere: the geometry once, four tails
+                geom_g2<EX>(g2, wqd[j0], r2, sq);
+#pragma unroll
+                for (int j = j0; j < j0 + 4; ++j) tail_g2<QW, K0>(A, j, r2, sq, wqd[j], k, nG2, Gs2);
+            } else if ((SH & kShGeom) && GROUP == 2 && ((same >> j0) & 1u)) {
                 // rows j0 and j0 + 1 are the same sphere (n_sigma copies of a
                 // sweep): the geometry once, then each row's own n_sigma; the
                 // same operations per row as apart, hence the same bits.
                 // With QUAD, the geometry of group j0 - 2 serves this group
                 // too when row j0 - 1 is the same sphere as row j0.
                 if (!(QUAD && have && ((link >> j0) & 1u))) geom_g2<EX>(g2, wqd[j0], r2, sq);
-                tail_g2<QW>(A, j0, r2, sq, wqd[j0], k, nG2, Gs2);
-                tail_g2<QW>(A, j0 + 1, r2, sq, wqd[j0 + 1], k, nG2, Gs2);
+                tail_g2<QW, K0>(A, j0, r2, sq, wqd[j0], k, nG2, Gs2);
+                tail_g2<QW, K0>(A, j0 + 1, r2, sq, wqd[j0 + 1], k, nG2, Gs2);
                 have = true;
             } else {
 #pragma unroll
-                for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW, EX>(A, j, g2, wqd[j], k, nG2, Gs2);
+                for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2<QW, EX, K0>(A, j, g2, wqd[j], k, nG2, Gs2);
                 have = false;
             }
         } else {
@@ -813,7 +836,7 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
     }
 }
 
-template <int PRIM, class C, int MODE, bool GRAD, bool EX, bool SH>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX, int SH>
 __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int warp, bool abort) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int QW = C::QW;
@@ -877,7 +900,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     // radius bit for bit, both valid), so the packed evaluation shares their
     // geometry; link, bit j (j even, j > 0): rows j - 1 and j are too
     unsigned same = 0u, link = 0u;
-    if (SH && PRIM == 0) {
+    if ((SH & kShGeom) && PRIM == 0) {
         bool eq = false;
         if (lane < QW - 1) {
             const float4 a = wq[lane][0], b = wq[lane + 1][0];
@@ -888,6 +911,32 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         const unsigned e = __ballot_sync(0xffffffffu, eq);
         same = e & 0x55555555u;
         link = (e & 0xAAAAAAAAu) << 1;
+    }
+    // Quads of a sweep evaluated as groups of four: when every quad of the
+    // warp is one sphere, one reach test per quad replaces the four row
+    // tests.  The test takes the largest alpha and beta of the quad's rows,
+    // so it reaches at least as far as each row; a row that does not reach a
+    // chunk adds nothing, so the outputs do not change.
+    constexpr bool QT = (SH & kShGeom) && PRIM == 0 && C::GROUP == 4 && C::IL == 4 && MODE == 0 && !GRAD;
+    constexpr int NQ = QW / 4;  // quads per warp
+    float4 qrec[2];             // lane l: quad l % NQ as one record
+    bool quadok = false;
+    if constexpr (QT) {
+        const int qi = lane % NQ;
+        qrec[0] = wq[4 * qi][0];
+        qrec[1] = wq[4 * qi][1];
+#pragma unroll
+        for (int m = 1; m < 4; ++m) {
+            const float4 b = wq[4 * qi + m][1];
+            qrec[1].y = fmaxf(qrec[1].y, b.y);
+            qrec[1].z = fmaxf(qrec[1].z, b.z);
+            qrec[1].w = fmaxf(qrec[1].w, b.w);
+        }
+        unsigned whole = 0u;
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq)
+            whole |= ((same >> (4 * qq)) & (same >> (4 * qq + 2)) & (link >> (4 * qq + 2)) & 1u) << qq;
+        quadok = whole == (1u << NQ) - 1u;
     }
     // the warp's box of primitive centres and its largest reach parameters:
     // a chunk outside box + reach is out of reach of every primitive here
@@ -921,6 +970,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if constexpr (MODE != 3) A.cnt[j] = 0;
         if (!GRAD) A.cin[j] = 0;
         if (MODE == 0 && !GRAD) { A.sum[j] = 0.f; if (PRIM == 1) A.sumb[j] = 0.f; }
+        if (PRIM == 0 && MODE == 0 && !GRAD) A.mst[j] = INFINITY;
         if (MODE == 1) A.mn[j] = INFINITY;
         if (MODE == 2) { A.sm_m[j] = k.S_cut; A.sm_acc[j] = 0.f; }
         if (GRAD) { A.gx[j] = 0.f; A.gy[j] = 0.f; A.gz[j] = 0.f; }
@@ -997,6 +1047,32 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             constexpr int CPR = 32 / QW;
             constexpr unsigned QMASK = (1u << QW) - 1u;
             unsigned myq = 0u;
+            if (QT && quadok) {
+                // lane l: quad l % NQ against the passing slot of rank
+                // base + l / NQ; slot t's quad bits become its row bits
+                constexpr int CPRQ = 32 / NQ;
+                const int rank = __popc(pmask & ((1u << lane) - 1u));
+                const bool mine = (pmask >> lane) & 1u;
+                const int npass = __popc(pmask);
+                if (mine) sm->slots[warp][rank] = lane;
+                __syncwarp();
+                for (int base = 0; base < npass; base += CPRQ) {
+                    const int kq = base + lane / NQ;
+                    bool qp = false;
+                    if (kq < npass) {
+                        const int my = sm->slots[warp][kq];
+                        qp = reaches<0, EX>(qrec, sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs, k.S_reach);
+                    }
+                    const unsigned hits = __ballot_sync(0xffffffffu, qp);
+                    if (mine && rank >= base && rank < base + CPRQ) {
+                        const unsigned qb = hits >> ((rank - base) * NQ);
+#pragma unroll
+                        for (int qq = 0; qq < NQ; ++qq) myq |= ((qb >> qq) & 1u) ? 0xFu << (4 * qq) : 0u;
+                    }
+                }
+                __syncwarp();  // every lane has read the list before the next stage rewrites it
+                pmask = 0u;
+            }
             while (pmask) {
                 int sl[CPR];
 #pragma unroll
@@ -1067,7 +1143,12 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         } else {
         const int cntj = __reduce_add_sync(0xffffffffu, (unsigned)A.cnt[j]);
         if (!GRAD) {
-            const int cinj = __reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
+            int cinj;
+            if constexpr ((SH & kShK0) && PRIM == 0 && MODE == 0) {
+                cinj = warp_min(A.mst[j]) < k.T_in_u ? 1 : 0;  // k_thr = 0: any pair in collision
+            } else {
+                cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
+            }
             float metric = 0.f;
             if (MODE == 0) {
                 const float tot = warp_sum(PRIM == 1 ? A.sum[j] + A.sumb[j] : A.sum[j]);
@@ -1142,7 +1223,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     }
 }
 
-template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, bool SH = false>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, int SH = 0>
 __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     EvalSmem<C> *sm = reinterpret_cast<EvalSmem<C> *>(smem_raw);
@@ -1351,6 +1432,7 @@ QueryConsts make_consts(const cs_params &p) {
 //   23: 1 x 8, 2 stages x 10 chunks, 8 CTAs/SM
 //   24: shape 18 with row quads interleaved over the consumer warps (a
 //       sweep's four n_sigma copies of a sphere in one warp)
+//   25: shape 24 evaluating sphere primitives in groups of 4 (a quad)
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1375,6 +1457,7 @@ using Cfg21 = Cfg<8, 8, 2, 32, 2, 4, 2>;
 using Cfg22 = Cfg<2, 8, 2, 12, 6, 2, 2>;
 using Cfg23 = Cfg<1, 8, 2, 10, 8, 2, 0>;
 using Cfg24 = Cfg<8, 8, 2, 32, 2, 2, 4>;
+using Cfg25 = Cfg<8, 8, 2, 32, 2, 4, 4>;
 // Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
 // three gradient sums per primitive, so its tiles hold fewer primitives
 //   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
@@ -1386,7 +1469,7 @@ using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
 constexpr int kDefaultGradTile = 2;
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25};
 constexpr int kDefaultTile = 18;
 constexpr int kSmallBatchTile = 23;
 constexpr int kSmallBatchQ = 1 << 17;
@@ -1397,7 +1480,7 @@ int tile_configs(int32_t *ids, int32_t cap) {
     return n;
 }
 
-template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, bool SH = false>
+template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, int SH = 0>
 static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
     constexpr int TQ = C::NCW * C::QW;
     const int ntiles = (a.Q + TQ - 1) / TQ;
@@ -1429,12 +1512,19 @@ static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
 // A conservatism sweep's sphere cost launches on the shapes whose warps take
 // consecutive row pairs (the n_sigma copies of a primitive) share the
 // copies' geometry (over row quads where the layout keeps them together);
-// every other launch keeps the plain evaluation.
+// sphere cost launches with k_thr = 0 keep a running minimum instead of the
+// in-collision count; every other launch keeps the plain evaluation.
 template <int PRIM, class C>
 static cudaError_t launch_mode_sweep(const EvalArgs &a, cudaStream_t s) {
-    if constexpr (PRIM == 0 && C::GROUP == 2 && C::IL != 1) {
+    if constexpr (PRIM == 0 && (C::GROUP == 2 || (C::GROUP == 4 && C::IL == 4)) && C::IL != 1) {
         const bool cost = a.k.mode == CS_METRIC_MEAN_COST || a.k.mode == CS_METRIC_SUM_COST;
-        if (a.k.sweep > 1 && cost) return launch_eval_t<PRIM, C, 0, false, false, true>(a, s);
+        if (a.k.sweep > 1 && cost)
+            return a.k.k_thr == 0 ? launch_eval_t<PRIM, C, 0, false, false, kShGeom | kShK0>(a, s)
+                                  : launch_eval_t<PRIM, C, 0, false, false, kShGeom>(a, s);
+    }
+    if constexpr (PRIM == 0) {
+        const bool cost = a.k.mode == CS_METRIC_MEAN_COST || a.k.mode == CS_METRIC_SUM_COST;
+        if (cost && a.k.k_thr == 0) return launch_eval_t<PRIM, C, 0, false, false, kShK0>(a, s);
     }
     return launch_mode<PRIM, C>(a, s);
 }
@@ -1501,6 +1591,7 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 22: return launch_mode_sweep<PRIM, Cfg22>(a, s);
         case 23: return launch_mode_sweep<PRIM, Cfg23>(a, s);
         case 24: return launch_mode_sweep<PRIM, Cfg24>(a, s);
+        case 25: return launch_mode_sweep<PRIM, Cfg25>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }

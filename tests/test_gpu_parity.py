@@ -432,15 +432,19 @@ def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
                                           sep["group_metric"].cpu().numpy())
 
 
-@pytest.mark.parametrize("prim_type,tile,sweep", [
-    (0, 0, (0.0, 0.5, 1.0, 2.0, 1.25)), (1, 0, (0.0, 0.5, 1.0, 2.0, 1.25)),
+@pytest.mark.parametrize("prim_type,tile,sweep,k_thr", [
+    (0, 0, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (1, 0, (0.0, 0.5, 1.0, 2.0, 1.25), 0),
     # the shapes whose sweep launches share geometry over row pairs (18, 22)
-    # or row quads (15, 23, 24), with copies aligned to the quads (four
+    # or row quads (15, 23, 24, 25), with copies aligned to the quads (four
     # values) or not (three, five)
-    (0, 15, (0.0, 0.5, 1.0, 2.0)), (0, 18, (0.0, 0.5, 1.0, 2.0)), (0, 24, (0.0, 0.5, 1.0, 2.0)),
-    (0, 24, (0.0, 0.5, 1.0, 2.0, 1.25)), (0, 24, (2.0, 0.0, 1.0)), (0, 23, (0.0, 0.5, 1.0, 2.0)),
-    (0, 22, (0.0, 0.5, 1.0, 2.0)), (0, 15, (1.0, 0.5, 0.0))])
-def test_sweep_parameter_equals_separate_calls(cs, prim_type, tile, sweep):
+    (0, 15, (0.0, 0.5, 1.0, 2.0), 0), (0, 18, (0.0, 0.5, 1.0, 2.0), 0), (0, 24, (0.0, 0.5, 1.0, 2.0), 0),
+    (0, 24, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 24, (2.0, 0.0, 1.0), 0), (0, 23, (0.0, 0.5, 1.0, 2.0), 0),
+    (0, 22, (0.0, 0.5, 1.0, 2.0), 0), (0, 15, (1.0, 0.5, 0.0), 0),
+    # quads evaluated as one group of four, with one reach test per quad (25)
+    (0, 25, (0.0, 0.5, 1.0, 2.0), 0), (0, 25, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 25, (2.0, 0.0, 1.0), 0),
+    # k_thr > 0: in-collision counts instead of the smallest st^2
+    (0, 25, (0.0, 0.5, 1.0, 2.0), 2), (0, 24, (0.0, 0.5, 1.0, 2.0), 1), (0, 0, (0.0, 1.0, 2.0), 3)])
+def test_sweep_parameter_equals_separate_calls(cs, prim_type, tile, sweep, k_thr):
     """cs_params.sweep_count: one call over Q rows at S n_sigma values gives
     block s exactly the bits of its own call (metric, flag, count, groups
     within each block, with a ragged last group), in every metric mode."""
@@ -455,12 +459,13 @@ def test_sweep_parameter_equals_separate_calls(cs, prim_type, tile, sweep):
     ng = (Q + G - 1) // G
     for mode in (0, 1, 2, 3):
         one = scene.query(torch.as_tensor(q), 0.0, prim_type=prim_type, want_count=True,
-                          params=cs.QueryParams(mode=mode, group_size=G, sweep=sweep, tile_config=tile))
+                          params=cs.QueryParams(mode=mode, group_size=G, sweep=sweep, tile_config=tile,
+                                                k_thr=k_thr))
         torch.cuda.synchronize()
         assert one["metric"].shape[0] == len(sweep) * Q and one["group_metric"].shape[0] == len(sweep) * ng
         for s, ns in enumerate(sweep):
             sep = scene.query(torch.as_tensor(q), ns, prim_type=prim_type, want_count=True,
-                              params=cs.QueryParams(mode=mode, group_size=G))
+                              params=cs.QueryParams(mode=mode, group_size=G, k_thr=k_thr))
             torch.cuda.synchronize()
             for k in ("metric", "collide", "count"):
                 np.testing.assert_array_equal(one[k][s * Q:(s + 1) * Q].cpu().numpy().view(np.uint8),
