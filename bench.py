@@ -931,6 +931,7 @@ def run_eval_case(args):
         for _ in range(2):
             o1 = scene.query(arm, 0.0, params=qs, prim_type=prim)
         scene.query(arm, 0.0, params=qs, prim_type=prim, eval_events=ev1, out=o1)
+        scene.query(arm, 0.0, params=qs, prim_type=prim, kernel_stats=kstats)
         sep_ms = 0.0
         outs = []
         for ns in NSIGMAS:
@@ -942,9 +943,11 @@ def run_eval_case(args):
             outs.append(o["metric"].clone())
         torch.cuda.synchronize()
         same = all(torch.equal(o1["metric"][i * Q:(i + 1) * Q], outs[i]) for i in range(len(NSIGMAS)))
+        ks = kstats.cpu().tolist()
         print(json.dumps({"case": "eval", "sweep": True, "batch": args.batch, "tile": args.tile,
                           "queries": 4 * Q, "one_launch_ms": ev1[0].elapsed_time(ev1[1]),
-                          "four_launches_ms": sep_ms, "bitwise_equal": bool(same)}))
+                          "four_launches_ms": sep_ms, "bitwise_equal": bool(same),
+                          "consumer_wait_frac": ks[9] / max(ks[8], 1), "producer_wait_frac": ks[11] / max(ks[10], 1)}))
         return
     if args.grad:
         up = torch.ones(arm.shape[0] // G + (arm.shape[0] % G > 0), device=dev)

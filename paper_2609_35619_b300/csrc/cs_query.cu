@@ -1433,6 +1433,8 @@ QueryConsts make_consts(const cs_params &p) {
 //   24: shape 18 with row quads interleaved over the consumer warps (a
 //       sweep's four n_sigma copies of a sphere in one warp)
 //   25: shape 24 evaluating sphere primitives in groups of 4 (a quad)
+//   26: shape 19 with row quads evaluated in groups of 4
+//   27: 4 x 16, 2 stages x 24 chunks, 3 CTAs/SM, row quads in groups of 4
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1458,6 +1460,8 @@ using Cfg22 = Cfg<2, 8, 2, 12, 6, 2, 2>;
 using Cfg23 = Cfg<1, 8, 2, 10, 8, 2, 0>;
 using Cfg24 = Cfg<8, 8, 2, 32, 2, 2, 4>;
 using Cfg25 = Cfg<8, 8, 2, 32, 2, 4, 4>;
+using Cfg26 = Cfg<4, 16, 3, 16, 3, 4, 4>;
+using Cfg27 = Cfg<4, 16, 2, 24, 3, 4, 4>;
 // Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
 // three gradient sums per primitive, so its tiles hold fewer primitives
 //   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
@@ -1469,7 +1473,7 @@ using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
 constexpr int kDefaultGradTile = 2;
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27};
 constexpr int kDefaultTile = 18;
 constexpr int kSmallBatchTile = 23;
 constexpr int kSmallBatchQ = 1 << 17;
@@ -1592,6 +1596,8 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 23: return launch_mode_sweep<PRIM, Cfg23>(a, s);
         case 24: return launch_mode_sweep<PRIM, Cfg24>(a, s);
         case 25: return launch_mode_sweep<PRIM, Cfg25>(a, s);
+        case 26: return launch_mode_sweep<PRIM, Cfg26>(a, s);
+        case 27: return launch_mode_sweep<PRIM, Cfg27>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }

@@ -435,12 +435,14 @@ def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
 @pytest.mark.parametrize("prim_type,tile,sweep,k_thr", [
     (0, 0, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (1, 0, (0.0, 0.5, 1.0, 2.0, 1.25), 0),
     # the shapes whose sweep launches share geometry over row pairs (18, 22)
-    # or row quads (15, 23, 24, 25), with copies aligned to the quads (four
+    # or row quads (15, 23-27), with copies aligned to the quads (four
     # values) or not (three, five)
     (0, 15, (0.0, 0.5, 1.0, 2.0), 0), (0, 18, (0.0, 0.5, 1.0, 2.0), 0), (0, 24, (0.0, 0.5, 1.0, 2.0), 0),
     (0, 24, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 24, (2.0, 0.0, 1.0), 0), (0, 23, (0.0, 0.5, 1.0, 2.0), 0),
     (0, 22, (0.0, 0.5, 1.0, 2.0), 0), (0, 15, (1.0, 0.5, 0.0), 0),
-    # quads evaluated as one group of four, with one reach test per quad (25)
+    # quads evaluated as one group of four, with one reach test per quad (25-27)
+    (0, 26, (0.0, 0.5, 1.0, 2.0), 0), (0, 26, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 26, (2.0, 0.0, 1.0), 0),
+    (0, 27, (0.0, 0.5, 1.0, 2.0), 0), (0, 27, (1.0, 0.5, 0.0), 0), (0, 26, (0.0, 0.5, 1.0, 2.0), 2),
     (0, 25, (0.0, 0.5, 1.0, 2.0), 0), (0, 25, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 25, (2.0, 0.0, 1.0), 0),
     # k_thr > 0: in-collision counts instead of the smallest st^2
     (0, 25, (0.0, 0.5, 1.0, 2.0), 2), (0, 24, (0.0, 0.5, 1.0, 2.0), 1), (0, 0, (0.0, 1.0, 2.0), 3)])
