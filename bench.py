@@ -44,7 +44,7 @@ TRAFFIC = {"version": "cs_b300 0.9 (sm_103a)", "bytes": (62.672640e6 + 315.48134
            "case": "mean of the step's two forward sweep launches, tile 27 (arm 262,144 x 4 rows: 62.7 MB; "
                    "edge 2,097,152 x 4 rows: 315.5 MB)"}
 WORKLOAD = ("tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres "
-            "fwd+adjoint (each batch's conservatism sweep as one launch)")
+            "fwd+adjoint (each batch's conservatism sweep as one launch; the pose forward and adjoint as one fused launch)")
 
 
 def parse():
@@ -180,24 +180,22 @@ def run_ours(args, rank, world):
         pose_out = {"metric": torch.empty(n_pose * K, device=dev),
                     "collide": torch.empty(n_pose * K, dtype=torch.uint8, device=dev),
                     "group_metric": torch.empty(n_pose, device=dev),
-                    "group_collide": torch.empty(n_pose, dtype=torch.uint8, device=dev)}
-        gbuf = torch.empty((n_pose * K, 3), device=dev)
+                    "group_collide": torch.empty(n_pose, dtype=torch.uint8, device=dev),
+                    "grad": torch.empty((n_pose * K, 3), device=dev)}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
 
     # tile shapes for the two batch classes from the autotuner (untimed)
     if args.tiles:
         tt = [int(x) for x in args.tiles.split(",")]
-        tiles = {"arm": tt[0], "edge": tt[1], "pose": tt[2] if len(tt) > 2 else tt[0], "source": "--tiles"}
+        tiles = {"arm": tt[0], "edge": tt[1], "source": "--tiles"}
     else:
         tune_scene = cs.Scene(d_scene["means"], d_scene["scales"], d_scene["quats"], d_scene["opacity"],
                               device=dev, stream=stream)
         sw = cs.QueryParams(sweep=NSIGMAS)
-        with torch.cuda.stream(stream):
-            tune_pose = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)  # the step's own pose spheres
         tiles = {"arm": tune_scene.autotune(d_arm, 0.0, params=sw, reps=2, stream=stream)[0],
                  "edge": tune_scene.autotune(d_edge, 0.0, params=sw, reps=1, stream=stream)[0],
-                 "pose": tune_scene.autotune(tune_pose, 1.0, reps=2, stream=stream)[0], "source": "cs_autotune"}
+                 "source": "cs_autotune"}
         tune_scene.close()
 
     def step(events=None, stats=None, build_ev=None):
@@ -216,11 +214,10 @@ def run_ours(args, rank, world):
                     stream=stream, eval_events=nxt(), out=outs["edge"], pair_stats=stats)
         with torch.cuda.stream(stream):
             sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
-            scene.query(sph, 1.0, params=cs.QueryParams(group_size=K, tile_config=tiles["pose"]), stream=stream,
-                        eval_events=nxt(), out=pose_out, pair_stats=stats)
-            scene.query_grad(sph, 1.0, grad_out=ones, params=cs.QueryParams(group_size=K), stream=stream,
-                             eval_events=nxt(), out=gbuf)
-            gp = cs.pose_spheres_grad(d_poses, d_offs, gbuf, stream=stream)
+            # forward (metric, flag, per-pose cost) and adjoint in one fused launch
+            scene.query_fwd_grad(sph, 1.0, grad_out=ones, params=cs.QueryParams(group_size=K), stream=stream,
+                                 eval_events=nxt(), out=pose_out, pair_stats=stats)
+            gp = cs.pose_spheres_grad(d_poses, d_offs, pose_out["grad"], stream=stream)
         return scene, gp
 
     # ---- pair counts of one step (untimed, with the stats counters on)
@@ -408,16 +405,14 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
         with torch.cuda.stream(stream):
             sph = cs.pose_spheres(d_poses, d_offs, radius, stream=stream)
             Q = sph.shape[0]
-            p = cs.QueryParams(group_size=K, tile_config=tiles["pose"]).to_c()
+            # forward (the per-pose cost) and adjoint in one fused launch
+            p = cs.QueryParams(group_size=K).to_c()
             p.stream = sh
             gm = torch.empty(n_pose, device=dev)
             p.out_group_metric = gm.data_ptr()
-            cs.check(cs.abi.cs_query(h, 0, sph, Q, 1.0, None, None, p))
             g = torch.empty((Q, 3), device=dev)
             ones = torch.ones(n_pose, device=dev)
-            p = cs.QueryParams(group_size=K).to_c()
-            p.stream = sh
-            cs.check(cs.abi.cs_query_grad(h, 0, sph, Q, 1.0, ones, g, p))
+            cs.check(cs.abi.cs_query_fwd_grad(h, 0, sph, Q, 1.0, ones, None, None, g, p))
             gp = cs.pose_spheres_grad(d_poses, d_offs, g, stream=stream)
             h_gpose.copy_(gp, non_blocking=True)
             h_posecost.copy_(gm, non_blocking=True)

@@ -265,6 +265,22 @@ CS_API cs_status cs_query_grad(const cs_scene *scene, int32_t prim_type, const f
                         float conservatism, const float *grad_out, float *grad_centres,
                         const cs_params *params);
 
+/* Forward and adjoint of cs_query in one fused launch (spheres; the mean or
+ * sum cost mode): out_metric, out_collide and params->out_count,
+ * out_group_metric and out_group_collide as cs_query writes them (any may be
+ * NULL), and grad_centres as cs_query_grad writes it (required).  The launch
+ * evaluates every pair once for both.  grad_centres has the bits of
+ * cs_query_grad; the forward outputs come from the adjoint's arithmetic (the
+ * square root of Eq. 8 as u rsqrt(u)), so they agree with cs_query within
+ * the metric's FP32 tolerance, not bit for bit, and a pair at the edge of the
+ * neighbour set or the in-collision test may be counted on the other side.
+ * The adjoint's default tile shape is used whatever params->tile_config says.
+ * Other primitive types or modes return CS_ERR_INVALID_ARG; a conservatism
+ * sweep is rejected as for cs_query_grad.  host_io and streams as cs_query. */
+CS_API cs_status cs_query_fwd_grad(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
+                                   float conservatism, const float *grad_out, float *out_metric,
+                                   uint8_t *out_collide, float *grad_centres, const cs_params *params);
+
 /* Pose chain for sphere robots (device pointers): for P poses (t, w) with w
  * an axis-angle rotation (Rodrigues) and K body-frame offsets p_k,
  *   out_spheres[p*K + k] = (t_p + R(w_p) p_k, radius)      [P*K, 4]  */

@@ -189,6 +189,47 @@ class Scene:
         check(abi.cs_query_grad(self._h, prim_type, prims, Q, float(nsigma), go, g, p))
         return g
 
+    def query_fwd_grad(self, prims, nsigma=1.0, *, grad_out=None, params: QueryParams | None = None,
+                       nsigma_per_query=None, want_count=False, pair_stats=None, stream=None, eval_events=None,
+                       out=None) -> dict:
+        """cs_query_fwd_grad: the forward outputs of query() (spheres, mean or
+        sum cost) and d metric / d centre ("grad", [Q,3]) from one fused
+        launch; returns a dict of device tensors."""
+        torch = _torch()
+        params = params or QueryParams()
+        prims = _as_f32(prims, self.device).reshape(-1, 4)
+        Q = prims.shape[0]
+        if out is None:
+            out = {"metric": torch.empty(Q, dtype=torch.float32, device=self.device),
+                   "collide": torch.empty(Q, dtype=torch.uint8, device=self.device)}
+        if "grad" not in out:
+            out["grad"] = torch.empty((Q, 3), dtype=torch.float32, device=self.device)
+        p = params.to_c()
+        _set_events(p, eval_events)
+        p.stream = abi.stream_handle(stream)
+        keep = []
+        if nsigma_per_query is not None:
+            nsq = _as_f32(nsigma_per_query, self.device).reshape(Q)
+            keep.append(nsq)
+            p.nsigma_per_query = abi.ptr(nsq)
+        if want_count:
+            if "count" not in out:
+                out["count"] = torch.empty(Q, dtype=torch.int32, device=self.device)
+            p.out_count = abi.ptr(out["count"])
+        if params.group_size > 0:
+            ng = (Q + params.group_size - 1) // params.group_size
+            if "group_metric" not in out:
+                out["group_metric"] = torch.empty(ng, dtype=torch.float32, device=self.device)
+                out["group_collide"] = torch.empty(ng, dtype=torch.uint8, device=self.device)
+            p.out_group_metric = abi.ptr(out["group_metric"])
+            p.out_group_collide = abi.ptr(out["group_collide"])
+        if pair_stats is not None:
+            p.out_pair_stats = abi.ptr(pair_stats)
+        go = None if grad_out is None else _as_f32(grad_out, self.device).reshape(-1)
+        check(abi.cs_query_fwd_grad(self._h, CS_PRIM_SPHERE, prims, Q, float(nsigma), go, out["metric"],
+                                    out["collide"], out["grad"], p))
+        return out
+
     def sync(self, stream=None):
         check(abi.cs_sync(self._h, stream))
 

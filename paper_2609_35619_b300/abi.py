@@ -199,6 +199,8 @@ _SIGNATURES = {
                                      ctypes.POINTER(cs_params)]),
     "cs_query_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P,
                                         ctypes.POINTER(cs_params)]),
+    "cs_query_fwd_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, _P,
+                                         ctypes.POINTER(cs_params)]),
     "cs_pose_spheres": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_float, _P, _P]),
     "cs_pose_spheres_grad": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, _P, _P, _P]),
     "cs_sync": (ctypes.c_int, [_P, _P]),
@@ -342,6 +344,13 @@ def cs_query_grad(scene, prim_type, prims, Q, conservatism, grad_out, grad_centr
     return load().cs_query_grad(scene, prim_type, ptr(prims), int(Q), float(conservatism),
                                 ptr(grad_out), ptr(grad_centres),
                                 None if params is None else ctypes.byref(params))
+
+
+def cs_query_fwd_grad(scene, prim_type, prims, Q, conservatism, grad_out, out_metric, out_collide, grad_centres,
+                      params) -> int:
+    return load().cs_query_fwd_grad(scene, prim_type, ptr(prims), int(Q), float(conservatism), ptr(grad_out),
+                                    ptr(out_metric), ptr(out_collide), ptr(grad_centres),
+                                    None if params is None else ctypes.byref(params))
 
 
 def cs_pose_spheres(poses, P, offsets, K, radius, out_spheres, stream) -> int:

@@ -298,7 +298,7 @@ namespace cs {
 cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims, int64_t Q,
                        float conservatism, const cs_params *params, bool grad, float *out_metric,
                        uint8_t *out_collide, const float *grad_out, float *grad_centres,
-                       Workspace *own_ws) {
+                       Workspace *own_ws, bool fused) {
     cs_status st = check_scene(s);
     if (st != CS_OK) return st;
     Scene *sc = reinterpret_cast<Scene *>(const_cast<cs_scene *>(s));
@@ -326,6 +326,9 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     }
     const bool flags = p.mode == CS_METRIC_FLAGS;
     if (flags && grad) return invalid("the flags mode has no gradient");
+    if (fused && prim_type != CS_PRIM_SPHERE) return invalid("the fused forward and adjoint takes spheres");
+    if (fused && p.mode != CS_METRIC_MEAN_COST && p.mode != CS_METRIC_SUM_COST)
+        return invalid("the fused forward and adjoint takes the mean or sum cost mode");
     if (flags) {  // only collision flags are computed
         out_metric = nullptr;
         p.out_count = nullptr;
@@ -384,7 +387,8 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
         if (d_gm) d_gm = ws->io_gm;
         if (d_gc) d_gc = ws->io_gc;
     }
-    if (!grad && has_group) {
+    const bool fwd_out = !grad || fused;  // the launch writes forward outputs
+    if (fwd_out && has_group) {
         if (d_gm && !d_metric) d_metric = ws->io_metric;
         if (d_gc && !d_col) d_col = ws->io_collide;
     }
@@ -414,10 +418,10 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
         gflags = reinterpret_cast<unsigned *>(ws->io_metric);
         CS_CUDA(cudaMemsetAsync(gflags, 0, 4 * (size_t)ng, stream));
     }
-    CS_CUDA(run_eval(prim_type, sc->dev, rows, rows_ns, perm, (int)Qrows, p, grad ? nullptr : d_metric,
-                     grad ? nullptr : d_col, grad ? nullptr : d_cnt, d_gout, grad ? d_grad : nullptr,
+    CS_CUDA(run_eval(prim_type, sc->dev, rows, rows_ns, perm, (int)Qrows, p, fwd_out ? d_metric : nullptr,
+                     fwd_out ? d_col : nullptr, fwd_out ? d_cnt : nullptr, d_gout, grad ? d_grad : nullptr,
                      ws->err, sc->num_sms, kWaitPolls, stream, gflags));
-    if (!grad && has_group) {
+    if (fwd_out && has_group) {
         for (int b = 0; b < S; ++b)  // groups within each n_sigma block
             launch_group(d_metric ? d_metric + (size_t)b * Q : nullptr, d_col ? d_col + (size_t)b * Q : nullptr,
                          (int)Q, p.group_size, d_gm ? d_gm + (size_t)b * ng : nullptr,
@@ -425,9 +429,8 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
         CS_CUDA(cudaGetLastError());
     }
     if (p.host_io) {
-        if (grad) {
-            CS_CUDA(cudaMemcpyAsync(grad_centres, d_grad, 12 * Q, cudaMemcpyDeviceToHost, stream));
-        } else {
+        if (grad) CS_CUDA(cudaMemcpyAsync(grad_centres, d_grad, 12 * Q, cudaMemcpyDeviceToHost, stream));
+        if (fwd_out) {
             if (out_metric) CS_CUDA(cudaMemcpyAsync(out_metric, d_metric, 4 * Q, cudaMemcpyDeviceToHost, stream));
             if (out_collide) CS_CUDA(cudaMemcpyAsync(out_collide, d_col, Q, cudaMemcpyDeviceToHost, stream));
             if (p.out_count) CS_CUDA(cudaMemcpyAsync(p.out_count, d_cnt, 4 * Q, cudaMemcpyDeviceToHost, stream));
@@ -456,6 +459,13 @@ cs_status cs_query_grad(const cs_scene *scene, int32_t prim_type, const float *p
                         const cs_params *params) {
     return query_common(scene, prim_type, prims, Q, conservatism, params, true, nullptr, nullptr,
                         grad_out, grad_centres, nullptr);
+}
+
+cs_status cs_query_fwd_grad(const cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
+                            float conservatism, const float *grad_out, float *out_metric, uint8_t *out_collide,
+                            float *grad_centres, const cs_params *params) {
+    return query_common(scene, prim_type, prims, Q, conservatism, params, true, out_metric, out_collide,
+                        grad_out, grad_centres, nullptr, true);
 }
 
 cs_status cs_pose_spheres(const float *poses, int64_t P, const float *offsets, int32_t K,

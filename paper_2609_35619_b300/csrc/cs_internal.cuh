@@ -162,7 +162,7 @@ inline uint32_t tune_key(int32_t prim_type, int32_t mode, int64_t Q) {
 cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims, int64_t Q,
                        float conservatism, const cs_params *params, bool grad, float *out_metric,
                        uint8_t *out_collide, const float *grad_out, float *grad_centres,
-                       Workspace *own_ws);
+                       Workspace *own_ws, bool fused = false);
 int tile_configs(int32_t *ids, int32_t cap);
 int64_t launch_total();
 

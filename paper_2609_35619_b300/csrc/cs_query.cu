@@ -114,6 +114,9 @@ struct SlotMeta {
 // below T_in, and a running minimum replaces the in-collision count.
 constexpr int kShGeom = 1;
 constexpr int kShK0 = 2;
+// kShFwd (adjoint launches, spheres, cost modes): the same launch also writes
+// the forward outputs (metric, flag, count) from the pairs it evaluates.
+constexpr int kShFwd = 4;
 
 // Per-primitive data in shared memory, 4 float4 (QREC) per primitive:
 //   sphere:    (c, 1/r^2) (2n, alpha, beta, live) - -
@@ -444,13 +447,13 @@ template <int PRIM, int QW, int MODE, bool GRAD>
 struct Acc {
     // cost partial over the current chunk group (ellipsoids; spheres sum directly)
     float sumb[(MODE == 0 && !GRAD && PRIM == 1) ? QW : 1];
-    float sum[(MODE == 0 && !GRAD) ? QW : 1];
+    float sum[(MODE == 0) ? QW : 1];  // (adjoint: only with kShFwd)
     float mn[(MODE == 1) ? QW : 1];
     float sm_m[(MODE == 2) ? QW : 1];
     float sm_acc[(MODE == 2) ? QW : 1];
     float gx[GRAD ? QW : 1], gy[GRAD ? QW : 1], gz[GRAD ? QW : 1];
     int cnt[MODE == 3 ? 1 : QW];
-    int cin[GRAD ? 1 : QW];
+    int cin[(GRAD && PRIM == 1) ? 1 : QW];
     // sphere cost launches with k_thr = 0: the smallest st2 instead of the
     // in-collision count (a row collides iff it is below T_in)
     float mst[(MODE == 0 && !GRAD && PRIM == 0) ? QW : 1];
@@ -503,7 +506,7 @@ __device__ __forceinline__ float half_tr_ss(const LaneG &g) {
 // quadratic form, 4 w^T Sigma w + 2 tr((A Sigma)^2), i.e. u + tr((A Sigma)^2)/2
 // under the root (for a sphere A = I / r^2 and the trace term is the lane's
 // g.f = tr(Sigma^2)/2, scaled by 1/r^2 with the rest).
-template <int PRIM, int QW, int MODE, bool GRAD, bool EX = false>
+template <int PRIM, int QW, int MODE, bool GRAD, bool EX = false, bool FWD = false>
 __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j, const LaneG &g,
                                             const float4 *qd, const QueryConsts &k) {
     const float dx = g.x - qd[0].x, dy = g.y - qd[0].y, dz = g.z - qd[0].z;
@@ -590,6 +593,10 @@ __device__ __forceinline__ void pair_update(Acc<PRIM, QW, MODE, GRAD> &A, int j,
             const float ey = fmaf(rs, py, -2.f * wy) * live;
             const float ez = fmaf(rs, pz, -2.f * wz) * live;
             if (MODE == 0) {
+                if constexpr (FWD && PRIM == 0) {  // the forward reductions of the same pair
+                    A.cin[j] += (st2 < k.T_in) ? 1 : 0;
+                    A.sum[j] += nb ? dc : 0.f;
+                }
                 // Eq. 11 is flat (zero gradient) below s_min
                 const float w = (nb && st2 > k.s_min) ? dc : 0.f;
                 A.gx[j] = fmaf(w, ex, A.gx[j]);
@@ -799,7 +806,7 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 // One staged chunk against the primitives of `qmask`: lane l takes Gaussian
 // l of the chunk (lanes outside the staged range hold a point that meets no
 // primitive), then the primitives are evaluated two per basic block.
-template <int PRIM, int QW, int MODE, bool GRAD, bool EX>
+template <int PRIM, int QW, int MODE, bool GRAD, bool EX, bool FWD = false>
 __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const ChunkBlock &B, const SlotMeta &mt,
                                            unsigned qmask, float4 (*wq)[kQRec], const QueryConsts &k, int lane,
                                            int &group, unsigned &cand, unsigned &c_hits) {
@@ -825,12 +832,12 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
         for (int j = 0; j < QW; j += 2) {
             const bool p0 = (qmask >> j) & 1u, p1 = (qmask >> (j + 1)) & 1u;
             if (p0 && p1) {
-                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j, g, wq[j], k);
-                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j + 1, g, wq[j + 1], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX, FWD>(A, j, g, wq[j], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX, FWD>(A, j + 1, g, wq[j + 1], k);
             } else if (p0) {
-                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j, g, wq[j], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX, FWD>(A, j, g, wq[j], k);
             } else if (p1) {
-                pair_update<PRIM, QW, MODE, GRAD, EX>(A, j + 1, g, wq[j + 1], k);
+                pair_update<PRIM, QW, MODE, GRAD, EX, FWD>(A, j + 1, g, wq[j + 1], k);
             }
         }
     }
@@ -968,8 +975,9 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
         if constexpr (MODE != 3) A.cnt[j] = 0;
-        if (!GRAD) A.cin[j] = 0;
-        if (MODE == 0 && !GRAD) { A.sum[j] = 0.f; if (PRIM == 1) A.sumb[j] = 0.f; }
+        constexpr bool FWD = (SH & kShFwd) != 0;
+        if (!GRAD || FWD) A.cin[j] = 0;
+        if (MODE == 0 && (!GRAD || FWD)) { A.sum[j] = 0.f; if (PRIM == 1) A.sumb[j] = 0.f; }
         if (PRIM == 0 && MODE == 0 && !GRAD) A.mst[j] = INFINITY;
         if (MODE == 1) A.mn[j] = INFINITY;
         if (MODE == 2) { A.sm_m[j] = k.S_cut; A.sm_acc[j] = 0.f; }
@@ -1115,7 +1123,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     const int sl = __ffs(cmask) - 1;
                     cmask &= cmask - 1;
                     const unsigned q = __shfl_sync(0xffffffffu, myq, sl);
-                    eval_chunk<PRIM, QW, MODE, GRAD, EX>(A, sm->blk[s][sl], sm->meta[s][sl], q, wq, k, lane, group,
+                    eval_chunk<PRIM, QW, MODE, GRAD, EX, (SH & kShFwd) != 0>(A, sm->blk[s][sl], sm->meta[s][sl], q, wq, k, lane, group,
                                                          cand, c_hits);
                 }
             }
@@ -1190,6 +1198,20 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 const float acc = warp_sum(A.sm_acc[j] * sc_);
                 gx = warp_sum(A.gx[j] * sc_); gy = warp_sum(A.gy[j] * sc_); gz = warp_sum(A.gz[j] * sc_);
                 f = cntj > 0 ? 1.f / acc : 0.f;
+            }
+            if constexpr ((SH & kShFwd) != 0 && MODE == 0 && PRIM == 0) {
+                // the forward outputs of the same launch (as in the forward epilogue)
+                const int cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
+                const float tot = warp_sum(A.sum[j]);
+                const float metric = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? tot * k.d_max / (float)cntj : 0.f)
+                                                                     : tot * k.d_max;
+                if (lane == 0 && q < a.Q) {
+                    const uint32_t row = a.perm[q];
+                    const bool good = vq && ok;
+                    if (a.out_metric) a.out_metric[row] = good ? metric : __int_as_float(0x7fc00000);
+                    if (a.out_collide) a.out_collide[row] = (good && cinj > k.k_thr) ? 1 : 0;
+                    if (a.out_count) a.out_count[row] = good ? cntj : 0;
+                }
             }
             if (lane == 0 && q < a.Q) {
                 const uint32_t row = a.perm[q];
@@ -1540,11 +1562,17 @@ static cudaError_t launch_grad(const EvalArgs &a, int mode, cudaStream_t s) {
     return launch_eval_t<PRIM, C, 2, true>(a, s);
 }
 
+// An adjoint launch that also writes forward outputs (cs_query_fwd_grad).
+static bool fused_forward(const EvalArgs &a) { return a.out_metric || a.out_collide || a.out_count; }
+
 // The exact variance (cs_params.exact_variance) runs the default shapes only:
 // shape 23 up to 2^17 rows, 18 above (flags mode likewise), adjoint shape 2.
 template <int PRIM>
 static cudaError_t launch_exact(const EvalArgs &a, bool grad, cudaStream_t s) {
     const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
+    if constexpr (PRIM == 0) {
+        if (grad && mode == 0 && fused_forward(a)) return launch_eval_t<PRIM, CfgGrad2, 0, true, true, kShFwd>(a, s);
+    }
     if (grad) {
         if (mode == 0) return launch_eval_t<PRIM, CfgGrad2, 0, true, true>(a, s);
         if (mode == 1) return launch_eval_t<PRIM, CfgGrad2, 1, true, true>(a, s);
@@ -1565,6 +1593,10 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
     if (a.k.exact) return launch_exact<PRIM>(a, grad, s);
     if (grad) {
         const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
+        if constexpr (PRIM == 0) {
+            // forward outputs in the same launch: the default adjoint shape
+            if (mode == 0 && fused_forward(a)) return launch_eval_t<PRIM, CfgGrad2, 0, true, false, kShFwd>(a, s);
+        }
         const int gt = (tile >= 1 && tile <= 4) ? tile : kDefaultGradTile;
         if (gt == 1) return launch_grad<PRIM, CfgGrad1>(a, mode, s);
         if (gt == 3) return launch_grad<PRIM, CfgGrad3>(a, mode, s);
