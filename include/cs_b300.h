@@ -65,7 +65,7 @@ typedef enum cs_status {
     CS_ERR_CUDA = -3,        /* a CUDA runtime call failed (message in cs_last_error) */
     CS_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
     CS_ERR_BAD_HANDLE = -5,  /* NULL or destroyed scene handle */
-    CS_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+    CS_ERR_UNSUPPORTED = -6  /* valid request the library does not implement */
 } cs_status;
 
 typedef enum cs_prim_type {
