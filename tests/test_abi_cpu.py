@@ -52,6 +52,7 @@ def test_argument_errors_without_device():
     # bad handles
     assert abi.cs_query(None, 0, None, 1, 1.0, None, None, None) == abi.CS_ERR_BAD_HANDLE
     assert abi.cs_query_grad(None, 0, None, 1, 1.0, None, None, None) == abi.CS_ERR_BAD_HANDLE
+    assert abi.cs_query_fwd_grad(None, 0, None, 1, 1.0, None, None, None, None, None) == abi.CS_ERR_BAD_HANDLE
     assert abi.cs_sync(None, 0) == abi.CS_ERR_BAD_HANDLE
     assert abi.cs_scene_destroy(None) == abi.CS_OK  # NULL is a no-op
     # scene description checks
