@@ -351,7 +351,8 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
             useful_pairs, world, tiles):
     """The same step end to end through the C ABI from pinned host memory:
     the scene built from host arrays (the library copies them in), the step's
-    query batches copied in once, the same queries as the device-timed step
+    query batches copied in once on a second stream while the scene is
+    built, the same queries as the device-timed step
     (same tile shapes) on device buffers, and every pass's outputs copied back
     to pinned host memory on a second stream while the next pass computes."""
     import ctypes
@@ -379,6 +380,15 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
     sh = stream.cuda_stream
 
     def step():
+        # the query batches travel on the copy stream while the scene is built
+        with torch.cuda.stream(copy):
+            d_arm = h_arm.to(dev, non_blocking=True)
+            d_edge = h_edge.to(dev, non_blocking=True)
+            d_poses = h_poses.to(dev, non_blocking=True)
+        for t in (d_arm, d_edge, d_poses):
+            t.record_stream(stream)
+        uploaded = torch.cuda.Event()
+        uploaded.record(copy)
         d = cs.abi.cs_scene_desc()
         d.n = scene_h["means"].shape[0]
         d.means, d.scales = h_scene["means"].data_ptr(), h_scene["scales"].data_ptr()
@@ -386,10 +396,7 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
         d.on_device, d.use_filter, d.opacity_min, d.extent_max = 0, 1, 0.05, 0.1
         h = ctypes.c_void_p()
         cs.check(cs.abi.cs_scene_create(d, sh, h))
-        with torch.cuda.stream(stream):
-            d_arm = h_arm.to(dev, non_blocking=True)
-            d_edge = h_edge.to(dev, non_blocking=True)
-            d_poses = h_poses.to(dev, non_blocking=True)
+        stream.wait_event(uploaded)
         for i, (name, dq, G) in enumerate((("arm", d_arm, 64), ("edge", d_edge, 1024))):
             o = dev_out[i]
             p = cs.QueryParams(group_size=G, tile_config=tiles[name], sweep=NSIGMAS).to_c()
@@ -431,8 +438,9 @@ def run_e2e(args, cs, torch, dev, stream, scene_h, arm_h, edge_h, poses_h, offs_
     ms = 1e3 * sum(times) / len(times)
     return {"value": world * useful_pairs / (ms * 1e-3), "unit": "pairs/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "note": "scene built from pinned host arrays, query batches copied in once per step, outputs "
-                    "copied back per pass on a second stream; same tile shapes as the device-timed step"}
+            "note": "scene built from pinned host arrays, query batches copied in once per step on a second "
+                    "stream while the scene is built, outputs copied back per pass on that stream; same tile "
+                    "shapes as the device-timed step"}
 
 
 # ------------------------------------------------------------ serving
