@@ -76,6 +76,8 @@ def parse():
                     help="query batch for --case eval (arm_ellipsoids: 229,376 link ellipsoids, groups of 7)")
     ap.add_argument("--nsigma", type=float, default=1.0, help="n_sigma for --case eval")
     ap.add_argument("--grad", action="store_true", help="--case eval: time the adjoint kernel instead")
+    ap.add_argument("--fused", action="store_true",
+                    help="--case eval with --grad: the fused forward and adjoint (cs_query_fwd_grad)")
     ap.add_argument("--flags", action="store_true", help="--case eval: collision flags only (early exit)")
     ap.add_argument("--sweep", action="store_true",
                     help="--case eval: the four n_sigma values of the step in one launch (rows repeated, n_sigma "
@@ -954,6 +956,14 @@ def run_eval_case(args):
         return
     if args.grad:
         up = torch.ones(arm.shape[0] // G + (arm.shape[0] % G > 0), device=dev)
+        if args.fused:
+            fp = cs.QueryParams(group_size=G)
+            scene.query_fwd_grad(arm, ns, grad_out=up, params=fp)
+            scene.query_fwd_grad(arm, ns, grad_out=up, params=fp, eval_events=ev)
+            torch.cuda.synchronize()
+            print(json.dumps({"case": "eval", "grad": True, "fused": True, "batch": args.batch, "nsigma": ns,
+                              "queries": arm.shape[0], "eval_ms": ev[0].elapsed_time(ev[1])}))
+            return
         scene.query_grad(arm, ns, grad_out=up, params=qp, prim_type=prim)
         scene.query_grad(arm, ns, grad_out=up, params=qp, eval_events=ev, prim_type=prim)
         torch.cuda.synchronize()
