@@ -726,6 +726,63 @@ __device__ __forceinline__ void pair_update_g2(Acc<0, QW, 0, false> &A, int j, c
     tail_g2<QW, K0>(A, j, r2, sq, qd, k, nG2, Gs2);
 }
 
+// The adjoint (mean or sum cost, forward reductions too with FWD) of one
+// sphere against the lane's two Gaussians in packed FP32x2: the operations
+// of pair_update's adjoint body in its order (two scalar IEEE operations per
+// packed one, so the same bits), half 0 accumulated before half 1.
+template <int QW, bool FWD>
+__device__ __forceinline__ void pair_update_g2_grad(Acc<0, QW, 0, true> &A, int j, const LaneG2 &g,
+                                                    const float4 *qd, const QueryConsts &k) {
+    const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&qd[0]);  // -cx, -cy
+    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
+    const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
+    const f32x2 dx = add2(g.x, pa.x), dy = add2(g.y, pa.y), dz = add2(g.z, pb.x);
+    const f32x2 s2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    const f32x2 half = pk2(0.5f, 0.5f);
+    const f32x2 hxy = mul2(half, g.sxy2), hxz = mul2(half, g.sxz2), hyz = mul2(half, g.syz2);
+    const f32x2 vx = fma2(hxz, dz, fma2(hxy, dy, mul2(g.sxx, dx)));  // Sigma d
+    const f32x2 vy = fma2(hyz, dz, fma2(g.syy, dy, mul2(hxy, dx)));
+    const f32x2 vz = fma2(g.szz, dz, fma2(hyz, dy, mul2(hxz, dx)));
+    float u0, u1;
+    upk2(fma2(dx, vx, fma2(dy, vy, mul2(dz, vz))), u0, u1);
+    u0 = fmaxf(u0, 0.f);
+    u1 = fmaxf(u1, 0.f);
+    const f32x2 rsq = pk2(u0 > 0.f ? rsqrtf(u0) : 0.f, u1 > 0.f ? rsqrtf(u1) : 0.f);
+    const f32x2 sq = mul2(pk2(u0, u1), rsq);
+    float r0, r1;
+    upk2(fma2(nns2, sq, s2), r0, r1);  // Eq. 8 before the clamp
+    const f32x2 st = mul2(pk2(fmaxf(r0, 0.f), fmaxf(r1, 0.f)), pb.y);
+    float e0, e1, s0, s1;
+    upk2(fma2(st, pk2(-k.G, -k.G), pk2(k.Gsmin, k.Gsmin)), e0, e1);
+    upk2(st, s0, s1);
+    const float dc0 = ex2_approx(fminf(e0, 0.f)), dc1 = ex2_approx(fminf(e1, 0.f));
+    const bool nb0 = s0 <= k.S_cut, nb1 = s1 <= k.S_cut;
+    A.cnt[j] += (nb0 ? 1 : 0) + (nb1 ? 1 : 0);
+    if constexpr (FWD) {
+        A.cin[j] += ((s0 < k.T_in) ? 1 : 0) + ((s1 < k.T_in) ? 1 : 0);
+        A.sum[j] += nb0 ? dc0 : 0.f;
+        A.sum[j] += nb1 ? dc1 : 0.f;
+    }
+    // d st2 / d c = (-2 d + 2 n Sigma d / sqrt(d^T Sigma d)) / r^2 where the clamp is open
+    float ir, ir_dup;
+    upk2(pb.y, ir, ir_dup);
+    const f32x2 rs = mul2(mul2(nns2, pk2(-1.f, -1.f)), rsq);
+    const f32x2 live = pk2(r0 > 0.f ? ir : 0.f, r1 > 0.f ? ir : 0.f);
+    const f32x2 m2 = pk2(-2.f, -2.f);
+    float ex0, ex1, ey0, ey1, ez0, ez1;
+    upk2(mul2(fma2(rs, vx, mul2(m2, dx)), live), ex0, ex1);
+    upk2(mul2(fma2(rs, vy, mul2(m2, dy)), live), ey0, ey1);
+    upk2(mul2(fma2(rs, vz, mul2(m2, dz)), live), ez0, ez1);
+    // Eq. 11 is flat (zero gradient) below s_min
+    const float w0 = (nb0 && s0 > k.s_min) ? dc0 : 0.f, w1 = (nb1 && s1 > k.s_min) ? dc1 : 0.f;
+    A.gx[j] = fmaf(w0, ex0, A.gx[j]);
+    A.gy[j] = fmaf(w0, ey0, A.gy[j]);
+    A.gz[j] = fmaf(w0, ez0, A.gz[j]);
+    A.gx[j] = fmaf(w1, ex1, A.gx[j]);
+    A.gy[j] = fmaf(w1, ey1, A.gy[j]);
+    A.gz[j] = fmaf(w1, ez1, A.gz[j]);
+}
+
 // Lane l of a staged chunk: its slot l (padding slots already hold a point
 // that meets no primitive); an absent chunk (mt.hi == 0) gives that point on
 // every lane.
@@ -799,6 +856,38 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
             }
         } else {
             have = false;
+        }
+    }
+}
+
+// The adjoint counterpart of eval_chunk_pair (spheres, mean or sum cost).
+template <int QW, int GROUP, bool FWD>
+__device__ __forceinline__ void eval_chunk_pair_grad(Acc<0, QW, 0, true> &A, const ChunkBlock &B0,
+                                                     const SlotMeta mt0, const ChunkBlock &B1, const SlotMeta mt1,
+                                                     unsigned qmask, float4 (*wqd)[3], const QueryConsts &k,
+                                                     int lane, unsigned &cand, unsigned &c_hits) {
+    if (qmask == 0u) return;
+    LaneG g0, g1;
+    lane_gaussian(B0, mt0, lane, g0);
+    lane_gaussian(B1, mt1, lane, g1);
+    LaneG2 g2;
+    g2.x = pk2(g0.x, g1.x); g2.y = pk2(g0.y, g1.y); g2.z = pk2(g0.z, g1.z);
+    g2.sxx = pk2(g0.sxx, g1.sxx); g2.syy = pk2(g0.syy, g1.syy); g2.szz = pk2(g0.szz, g1.szz);
+    g2.sxy2 = pk2(g0.sxy2, g1.sxy2); g2.sxz2 = pk2(g0.sxz2, g1.sxz2); g2.syz2 = pk2(g0.syz2, g1.syz2);
+    unsigned gm = qmask;
+#pragma unroll
+    for (int sh = 1; sh < GROUP; sh <<= 1) gm |= gm >> sh;
+    constexpr unsigned LEAD = GROUP == 1 ? 0xFFFFFFFFu : GROUP == 2 ? 0x55555555u : GROUP == 4 ? 0x11111111u
+                                                                               : 0x01010101u;
+    gm &= LEAD;
+    const unsigned ng = (unsigned)__popc(gm) * (unsigned)GROUP;
+    c_hits += ng;
+    cand += ng * (unsigned)((mt0.hi - mt0.lo) + (mt1.hi - mt1.lo));
+#pragma unroll
+    for (int j0 = 0; j0 < QW; j0 += GROUP) {
+        if ((gm >> j0) & 1u) {
+#pragma unroll
+            for (int j = j0; j < j0 + GROUP; ++j) pair_update_g2_grad<QW, FWD>(A, j, g2, wqd[j], k);
         }
     }
 }
@@ -1116,6 +1205,22 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     eval_chunk_pair<QW, C::GROUP, EX, SH, C::QUAD>(A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
                                                   sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd, k,
                                                   lane, cand, c_hits, same, link);
+                }
+            } else if constexpr (PRIM == 0 && MODE == 0 && GRAD && !EX) {
+                // the sphere cost adjoint: the same chunk pairs in packed registers
+                while (cmask) {
+                    const int sa = __ffs(cmask) - 1;
+                    cmask &= cmask - 1;
+                    int sb = -1;
+                    if (cmask) {
+                        sb = __ffs(cmask) - 1;
+                        cmask &= cmask - 1;
+                    }
+                    const unsigned qa = __shfl_sync(0xffffffffu, myq, sa);
+                    const unsigned qb = sb >= 0 ? __shfl_sync(0xffffffffu, myq, sb) : 0u;
+                    eval_chunk_pair_grad<QW, C::GROUP, (SH & kShFwd) != 0>(
+                        A, sm->blk[s][sa], sm->meta[s][sa], sm->blk[s][sb >= 0 ? sb : sa],
+                        sb >= 0 ? sm->meta[s][sb] : SlotMeta{0, 0, 0, 0}, qa | qb, wqd, k, lane, cand, c_hits);
                 }
             } else {
 #pragma unroll 1
