@@ -547,6 +547,6 @@ int64_t cs_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 
 const char *cs_last_error(void) { return g_err.c_str(); }
 
-const char *cs_version(void) { return "cs_b300 1.0 (sm_103a)"; }
+const char *cs_version(void) { return "cs_b300 1.1 (sm_103a)"; }
 
 }  // extern "C"
