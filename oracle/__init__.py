@@ -61,7 +61,7 @@ class _Params(ctypes.Structure):
 class _Outputs(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "sum_cost", "mean_cost", "count_nbr", "count_in", "collide", "min_s2", "softmin",
-        "band_cut", "band_in", "cond", "min_cond", "band_kink")]
+        "band_cut", "band_in", "cond", "min_cond", "band_kink", "cond_cost")]
 
 
 @dataclass
@@ -162,6 +162,7 @@ def query(scene, prims, prim_type: int, nsigma, params: Params | None = None) ->
         "collide": np.zeros(Q, np.uint8), "min_s2": np.zeros(Q), "softmin": np.zeros(Q),
         "band_cut": np.zeros(Q, np.int64), "band_in": np.zeros(Q, np.int64),
         "cond": np.zeros(Q), "min_cond": np.zeros(Q), "band_kink": np.zeros(Q, np.int64),
+        "cond_cost": np.zeros(Q),
     }
     outs = _Outputs(*[res[k].ctypes.data for k, _ in _Outputs._fields_])
     rc = lib.orc_query(means.shape[0], _ptr(means), _ptr(scales), _ptr(quats), _ptr(op), prim_type,

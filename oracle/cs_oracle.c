@@ -74,6 +74,9 @@ typedef struct {
     double *min_cond;   /* s^2 + n_sigma sqrt(sigma^2) of the argmin pair */
     int64_t *band_kink; /* pairs near a kink of the gradient: |st^2 - s_min| <= band or
                            the Eq. 8 clamp within band of its switching point */
+    double *cond_cost;  /* max of s^2 + n_sigma sqrt(sigma^2) over the pairs of N_j whose
+                           Eq. 11 cost can feel it: st^2 >= s_min - band (s^2 + n sqrt(sigma^2));
+                           below s_min the cost is flat (d_max), so rounding there is harmless */
 } orc_outputs;
 
 /* ---- geometry -------------------------------------------------------- */
@@ -264,7 +267,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
         double c[3], A[3][3];
         if (robot_primitive(prim_type, prims + (size_t)stride * j, c, A) != 0) { bad += 1; continue; }
         double ns = nsigma[j];
-        double sum = 0.0, mn = INFINITY, mn_cond = 0.0, cond = 0.0;
+        double sum = 0.0, mn = INFINITY, mn_cond = 0.0, cond = 0.0, ccost = 0.0;
         int64_t cnt = 0, cin = 0, bcut = 0, bin = 0, bkink = 0;
         /* softmin: shift by the running minimum so the sum stays in range */
         double sm_m = INFINITY, sm_acc = 0.0;
@@ -286,6 +289,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
             if (t.st2 < 1.0) ++cin;
             double cnd = t.s2 + ns * sqrt(t.var);
             if (cnd > cond) cond = cnd;
+            if (t.st2 >= prm->s_min - band * cnd && cnd > ccost) ccost = cnd;
             if (t.st2 < mn) { mn = t.st2; mn_cond = cnd; }
             double x = t.st2 / prm->tau;
             if (x < sm_m) { sm_acc = sm_acc * exp(x - sm_m) + 1.0; sm_m = x; }
@@ -303,6 +307,7 @@ int orc_query(int64_t n, const float *means, const float *scales, const float *q
         if (out->cond) out->cond[j] = cond;
         if (out->min_cond) out->min_cond[j] = mn_cond;
         if (out->band_kink) out->band_kink[j] = bkink;
+        if (out->cond_cost) out->cond_cost[j] = ccost;
     }
     free(Sig);
     free(keep);

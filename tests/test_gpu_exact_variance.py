@@ -27,6 +27,9 @@ torch = pytest.importorskip("torch")
 EXACT = oracle.Params(exact_variance=True)
 U32 = 2.0 ** -24
 COND = 10.0
+# rows above COND take the widened cancellation bound; measured with the oracle on
+# these batches: at most 46 % of the rows at n_sigma 2 (exact variance), 34 % (disks)
+CANCEL_CAP = 0.5
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +60,8 @@ def test_spheres_all_modes(cs, tiny, nsigma, mode):
     q = np.c_[rng.uniform(0, 2, (Q, 3)), rng.uniform(0.03, 0.3, Q)].astype(np.float32)
     out = _run(cs, scene, q, nsigma, mode=mode)
     orc = oracle.query(sc, q, 0, nsigma, EXACT)
-    rep = compare(out, orc, mode, EXACT, f"exact spheres ns={nsigma} mode={mode}", cond_strict=COND)
+    rep = compare(out, orc, mode, EXACT, f"exact spheres ns={nsigma} mode={mode}", cond_strict=COND,
+                  max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.9 * rep["Q"], rep
     # the trace term matters here: the linearised oracle disagrees somewhere
     lin = oracle.query(sc, q, 0, nsigma)
@@ -74,7 +78,8 @@ def test_ellipsoids(cs, tiny, mode):
     band = max(1e-5, 24 * U32 * kappa.max() * max(cond.max(), 4.0))
     orc = oracle.query(sc, e, 1, 1.0, oracle.Params(exact_variance=True, band=band))
     out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode)
-    rep = compare(out, orc, mode, EXACT, f"exact ellipsoids mode={mode}", kappa=kappa, cond_strict=COND)
+    rep = compare(out, orc, mode, EXACT, f"exact ellipsoids mode={mode}", kappa=kappa, cond_strict=COND,
+                  max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.5 * rep["Q"], rep
 
 
@@ -87,7 +92,8 @@ def test_large_batch_shape_sampled(cs, tiny):
     out = _run(cs, scene, q, 1.0)
     idx = np.sort(rng.choice(Q, 3000, replace=False))
     orc = oracle.query(sc, q[idx], 0, 1.0, EXACT)
-    rep = compare({k: v[idx] for k, v in out.items()}, orc, 0, EXACT, "exact large batch", cond_strict=COND)
+    rep = compare({k: v[idx] for k, v in out.items()}, orc, 0, EXACT, "exact large batch", cond_strict=COND,
+                  max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.9 * rep["Q"], rep
 
 

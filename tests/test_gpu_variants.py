@@ -28,6 +28,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 U32 = 2.0 ** -24
 COND = 10.0
+# rows above COND take the widened cancellation bound; measured with the oracle on
+# these batches: at most 46 % of the rows at n_sigma 2 (exact variance), 34 % (disks)
+CANCEL_CAP = 0.5
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +87,7 @@ def test_disk_scene_spheres(cs, mode, nsigma):
     q = np.c_[rng.uniform(0, 2, (2500, 3)), rng.uniform(0.03, 0.3, 2500)].astype(np.float32)
     out = _run(cs, _scene(cs, sc), q, nsigma, mode=mode)
     rep = compare(out, oracle.query(sc, q, 0, nsigma), mode, oracle.Params(), f"disks mode={mode} ns={nsigma}",
-                  cond_strict=COND)
+                  cond_strict=COND, max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.9 * rep["Q"], rep
 
 
@@ -96,13 +99,14 @@ def test_disk_scene_ellipsoids_and_exact_variance(cs, mode):
     e = S.ellipsoid_queries(211, rng.uniform(0, 2, (1500, 3)), semi_lo=0.03, semi_hi=0.2)
     orc, kappa = _ellipsoid_case(sc, e, 1.0)
     rep = compare(_run(cs, scene, e, 1.0, prim_type=1, mode=mode), orc, mode, oracle.Params(),
-                  f"disks ellipsoids mode={mode}", kappa=kappa, cond_strict=COND)
+                  f"disks ellipsoids mode={mode}", kappa=kappa, cond_strict=COND,
+                  max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.5 * rep["Q"], rep
     # the exact variance with disks: tr((A Sigma)^2) of a singular Sigma
     orc, kappa = _ellipsoid_case(sc, e, 1.0, exact_variance=True)
     rep = compare(_run(cs, scene, e, 1.0, prim_type=1, mode=mode, exact_variance=True), orc, mode,
                   oracle.Params(exact_variance=True), f"disks ellipsoids exact mode={mode}", kappa=kappa,
-                  cond_strict=COND)
+                  cond_strict=COND, max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.5 * rep["Q"], rep
 
 
@@ -116,7 +120,8 @@ def test_point_cloud_scene(cs, mode):
     rng = np.random.default_rng(220 + mode)
     q = np.c_[rng.uniform(0, 2, (2500, 3)), rng.uniform(0.03, 0.3, 2500)].astype(np.float32)
     out0 = _run(cs, scene, q, 0.0, mode=mode)
-    rep = compare(out0, oracle.query(sc, q, 0, 0.0), mode, oracle.Params(), f"points mode={mode}", cond_strict=COND)
+    rep = compare(out0, oracle.query(sc, q, 0, 0.0), mode, oracle.Params(), f"points mode={mode}", cond_strict=COND,
+                  max_cancel=CANCEL_CAP)
     assert rep["checked"] > 0.9 * rep["Q"], rep
     for ns in (1.0, 2.5):
         o = _run(cs, scene, q, ns, mode=mode)
@@ -161,7 +166,7 @@ def test_tabletop_variant_full_size(cs, kind):
     idx = np.unique(np.r_[_sample(q.shape[0], 96, 240), _touching(out, 64, 241)])
     orc = oracle.query(sc, q[idx], 0, 1.0)
     rep = compare({k: v[idx] for k, v in out.items() if v.shape[0] == q.shape[0]}, orc, 0, oracle.Params(),
-                  f"tabletop {kind}", cond_strict=COND)
+                  f"tabletop {kind}", cond_strict=COND, max_cancel=CANCEL_CAP)
     assert rep["checked"] > 100, rep
 
 
@@ -193,7 +198,8 @@ def test_ellipsoid_arm_full_size(cs, mode):
     idx = np.unique(np.r_[_sample(e.shape[0], 256, 251), _touching(out, 160, 252)])
     orc, kappa = _ellipsoid_case(sc, e[idx], 1.0)
     rep = compare({k: v[idx] for k, v in out.items() if v.shape[0] == e.shape[0]}, orc, 0, oracle.Params(),
-                  "ellipsoid arm", kappa=kappa, cond_strict=COND)
+                  "ellipsoid arm", kappa=kappa, cond_strict=COND,
+                  max_cancel=CANCEL_CAP)
     assert rep["checked"] > 150, rep
     np.testing.assert_allclose(out["group_metric"], out["metric"].reshape(-1, 7).astype(np.float64).sum(1),
                                rtol=1e-5)

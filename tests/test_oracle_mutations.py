@@ -25,6 +25,25 @@ MUTATIONS = {
                         "double P[3] = {ax * ax, bx * bx, cx * cx};"),
     "exact_var_half_trace": ("if (exact) t.var += 2.0 * trace_asas(A, Sig);",
                              "if (exact) t.var += trace_asas(A, Sig);"),
+    # the diagnostics that set the parity tests' exclusions and tolerances
+    "cond_no_root": ("double cnd = t.s2 + ns * sqrt(t.var);", "double cnd = t.s2 + ns * t.var;"),
+    "cond_scaled": ("double cnd = t.s2 + ns * sqrt(t.var);", "double cnd = t.s2 + 2.0 * ns * sqrt(t.var);"),
+    "min_cond_running_max": ("if (t.st2 < mn) { mn = t.st2; mn_cond = cnd; }",
+                             "if (t.st2 < mn) { mn = t.st2; mn_cond = cond; }"),
+    "band_cut_unscaled": ("if (fabs(t.st2 - S_cut) <= band * S_cut) ++bcut;",
+                          "if (fabs(t.st2 - S_cut) <= band) ++bcut;"),
+    "band_in_scaled": ("if (fabs(t.st2 - 1.0) <= band) ++bin;", "if (fabs(t.st2 - 1.0) <= band * S_cut) ++bin;"),
+    "band_kink_no_clamp": ("(fabs(t.st2 - prm->s_min) <= band * fmax(1.0, fabs(prm->s_min)) ||\n"
+                           "                 fabs(t.raw) <= band * (t.s2 + ns * sqrt(t.var))))",
+                           "(fabs(t.st2 - prm->s_min) <= band * fmax(1.0, fabs(prm->s_min))))"),
+    "band_kink_at_one": ("(fabs(t.st2 - prm->s_min) <= band", "(fabs(t.st2 - 1.0) <= band"),
+    "cond_cost_all_pairs": ("if (t.st2 >= prm->s_min - band * cnd && cnd > ccost) ccost = cnd;",
+                            "if (cnd > ccost) ccost = cnd;"),
+    "cond_cost_no_margin": ("if (t.st2 >= prm->s_min - band * cnd && cnd > ccost) ccost = cnd;",
+                            "if (t.st2 >= prm->s_min && cnd > ccost) ccost = cnd;"),
+    "gscale_twice": ("mag += prm->gamma * dc * gm;", "mag += 2.0 * prm->gamma * dc * gm;"),
+    "gscale_not_averaged": ("if (cnt > 0) mag /= (double)cnt;", "if (cnt > 0) mag /= 1.0;"),
+    "gscale_norm_of_sum": ("*gmag = sqrt(m1) + sqrt(m2);", "*gmag = sqrt(m1 + m2);"),
 }
 
 
@@ -41,6 +60,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, CS_ORACLE_LIB=str(lib))
     proc = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                            os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                           os.path.join(ROOT, "tests", "test_oracle_diagnostics.py"),
                            os.path.join(ROOT, "tests", "test_oracle_exact_variance.py")],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert proc.returncode != 0, f"pins did not catch {name}:\n{proc.stdout[-2000:]}"
