@@ -13,9 +13,11 @@
 // Host code only ever sees a host-side stand-in for its name, so the device
 // address is resolved once per device with cudaGetSymbolAddress (on the first
 // call on that device, which therefore has to come before any stream capture)
-// and passed to the kernels.  All calls share the one area and it keeps the
-// last call's contents: calls whose work overlaps on the GPU race with each
-// other and must be serialised by the caller.
+// and passed to the kernels.  The address belongs to the device's current
+// context: after cudaDeviceReset (or under another context on the same
+// device) the next call resolves it again.  All calls share the one area and
+// it keeps the last call's contents: calls whose work overlaps on the GPU race
+// with each other and must be serialised by the caller.
 #include <mutex>
 
 #include <algorithm>
@@ -27,7 +29,7 @@ namespace cs {
 void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, float ns_scalar,
                  const float *ns_rows, Workspace &ws, uint32_t **perm_out, cudaStream_t s);
 void launch_group(const float *metric, const uint8_t *collide, int Q, int G, float *gm, uint8_t *gc,
-                  cudaStream_t s);
+                  cudaStream_t s, unsigned *err = nullptr);
 cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, const float *qns,
                      const uint32_t *perm, int Q, const cs_params &p, float *out_metric,
                      uint8_t *out_collide, int32_t *out_count, const float *grad_out,
@@ -60,16 +62,37 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_base[kMaxDevices] = {};
+void *g_ctx[kMaxDevices] = {};  // the context g_base[d] was resolved in
 
-// Device address of the scratch on `device` (which must be current).
+// The current driver context (an opaque handle; nullptr when the driver call
+// is unavailable, and then the first address per device is kept).
+void *current_context() {
+    using Fn = int (*)(void **);
+    static Fn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<Fn>(f);
+    }();
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of the scratch on `device` (which must be current): resolved
+// once per device and context.
 cs_status scratch_base(int device, unsigned char **out) {
     if (device < 0 || device >= kMaxDevices) return invalid("device ordinal out of range");
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[device]) {
+    void *ctx = current_context();
+    if (!g_base[device] || (ctx && ctx != g_ctx[device])) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
         g_base[device] = static_cast<unsigned char *>(p);
+        g_ctx[device] = current_context();  // the lookup may have created the primary context
     }
     *out = g_base[device];
     return CS_OK;
@@ -98,6 +121,12 @@ extern "C" cs_status cs_query_noalloc(const cs_scene *scene, int32_t prim_type, 
         return invalid("Q out of range: cs_query_noalloc takes at most CS_QUERY_NOALLOC_MAX_ROWS (65536) rows");
     if (!p.nsigma_per_query && (!(conservatism >= 0.f) || !isfinite(conservatism)))
         return invalid("conservatism (n_sigma) must be finite and >= 0");
+    const bool flags = p.mode == CS_METRIC_FLAGS;
+    if (flags) {  // only collision flags are computed, as in cs_query
+        out_metric = nullptr;
+        p.out_count = nullptr;
+        p.out_group_metric = nullptr;
+    }
     if (Q == 0) return CS_OK;
     if (!prims) return invalid("prims is NULL");
     const bool has_group = p.group_size > 0 && (p.out_group_metric || p.out_group_collide);
@@ -137,11 +166,20 @@ extern "C" cs_status cs_query_noalloc(const cs_scene *scene, int32_t prim_type, 
         if (p.out_group_metric && !d_metric) d_metric = w.io_metric;
         if (p.out_group_collide && !d_col) d_col = w.io_collide;
     }
+    // flags mode with groups: one word per group, set once a row of it
+    // collides (the other rows then stop); it must start at zero.  The
+    // per-row metric part of the area is free in this mode.
+    unsigned *gflags = nullptr;
+    if (flags && p.group_size > 0) {
+        gflags = reinterpret_cast<unsigned *>(w.io_metric);
+        const size_t ng = (size_t)((Q + p.group_size - 1) / p.group_size);
+        CS_CUDA(cudaMemsetAsync(gflags, 0, 4 * ng, stream));
+    }
     uint32_t *perm = nullptr;
     launch_prep(prims, prim_type, (int)Q, sc->dev, conservatism, p.nsigma_per_query, w, &perm, stream);
     CS_CUDA(cudaGetLastError());
     CS_CUDA(run_eval(prim_type, sc->dev, w.qrec, w.qns, perm, (int)Q, p, d_metric, d_col, p.out_count,
-                     nullptr, nullptr, w.err, sc->num_sms, kWaitPolls, stream));
+                     nullptr, nullptr, w.err, sc->num_sms, kWaitPolls, stream, gflags));
     if (has_group) {
         launch_group(d_metric, d_col, (int)Q, p.group_size, p.out_group_metric, p.out_group_collide, stream);
         CS_CUDA(cudaGetLastError());
