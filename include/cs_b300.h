@@ -65,7 +65,9 @@ typedef enum cs_status {
     CS_ERR_CUDA = -3,        /* a CUDA runtime call failed (message in cs_last_error) */
     CS_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
     CS_ERR_BAD_HANDLE = -5,  /* NULL or destroyed scene handle */
-    CS_ERR_UNSUPPORTED = -6  /* valid request the library does not implement */
+    CS_ERR_UNSUPPORTED = -6, /* valid request the library does not implement */
+    CS_ERR_BOUNDS = -7       /* a device-side index check failed (builds compiled with
+                                CS_DEBUG only; the access was skipped, no trap) */
 } cs_status;
 
 typedef enum cs_prim_type {
@@ -244,7 +246,12 @@ CS_API cs_status cs_query(const cs_scene *scene, int32_t prim_type, const float 
  *   - device pointers only (params->host_io = 1 returns CS_ERR_INVALID_ARG);
  *     the scene's device must be current;
  *   - the first call on a device resolves the area's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     The address belongs to the device's context: after cudaDeviceReset the
+ *     next call resolves it again (again before any capture);
+ *   - CS_METRIC_FLAGS behaves as in cs_query: out_metric, params->out_count
+ *     and params->out_group_metric are not written, and with group_size > 0
+ *     rows stop once their group collides (out_collide 2);
  *   - every call shares the area and it keeps the last call's contents:
  *     calls whose work overlaps on the GPU (other streams, other threads)
  *     race and corrupt each other's rows, so the caller serialises them;
@@ -351,6 +358,16 @@ CS_API cs_status cs_graph_destroy(cs_graph *graph);
 CS_API cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
                              float conservatism, const cs_params *params, int32_t reps,
                              int32_t *best, float *ms, int32_t cap);
+
+/* Autotuner log.  The paper has no counterpart.  After this call every
+ * cs_autotune call (any thread) appends one JSON line to the file at `path`:
+ *   {"n_gaussians", "prim_type", "mode", "exact_variance", "rows" (Q),
+ *    "sweep" (n_sigma blocks), "launch_rows", "reps",
+ *    "ms": {"<tile id>": mean ms per launch, ...}, "best": <tile id>}
+ * The file is opened, appended and closed per line; a file that cannot be
+ * opened is skipped silently.  path == NULL or "" stops logging.  The path
+ * is copied.  Always returns CS_OK. */
+CS_API cs_status cs_autotune_log(const char *path);
 
 /* ------------------------------------------------------------------------
  * One MPPI iteration (Section II-D) for a robot that is one sphere under

@@ -13,15 +13,18 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcs_b300.so")
+# CS_B300_LIBRARY may name the bounds-checked build of the same sources
+# (libcs_b300_debug.so, `python -m paper_2609_35619_b300.build --debug`)
+LIB_PATH = os.environ.get("CS_B300_LIBRARY") or os.path.join(HERE, "libcs_b300.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libcs_b300_debug.so")
 
 CS_OK, CS_ERR_INVALID_ARG, CS_ERR_NO_MEMORY, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_BAD_HANDLE, \
-    CS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+    CS_ERR_UNSUPPORTED, CS_ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 CS_PRIM_SPHERE, CS_PRIM_ELLIPSOID = 0, 1
 CS_METRIC_MEAN_COST, CS_METRIC_SUM_COST, CS_METRIC_MIN_S2, CS_METRIC_SOFTMIN_S2, CS_METRIC_FLAGS = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "CS_OK", -1: "CS_ERR_INVALID_ARG", -2: "CS_ERR_NO_MEMORY", -3: "CS_ERR_CUDA",
-                -4: "CS_ERR_TIMEOUT", -5: "CS_ERR_BAD_HANDLE", -6: "CS_ERR_UNSUPPORTED"}
+                -4: "CS_ERR_TIMEOUT", -5: "CS_ERR_BAD_HANDLE", -6: "CS_ERR_UNSUPPORTED", -7: "CS_ERR_BOUNDS"}
 
 
 class cs_scene_desc(ctypes.Structure):
@@ -217,6 +220,7 @@ _SIGNATURES = {
     "cs_autotune": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float,
                                    ctypes.POINTER(cs_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                    _P, ctypes.c_int32]),
+    "cs_autotune_log": (ctypes.c_int, [ctypes.c_char_p]),
     "cs_mppi_step": (ctypes.c_int, [_P, ctypes.POINTER(cs_mppi_desc), _P, _P, _P, _P, _P, _P, _P,
                                     ctypes.POINTER(cs_params)]),
     "cs_rrt_extend": (ctypes.c_int, [_P, ctypes.POINTER(cs_rrt_desc), _P, _P, _P, _P, _P, _P,
@@ -408,6 +412,10 @@ def cs_autotune(scene, prim_type, prims, Q, conservatism, params, reps, best: ct
     return load().cs_autotune(scene, prim_type, ptr(prims), int(Q), float(conservatism),
                               None if params is None else ctypes.byref(params), int(reps), ctypes.byref(best),
                               ptr(ms), int(cap))
+
+
+def cs_autotune_log(path) -> int:
+    return load().cs_autotune_log(None if path is None else os.fsencode(path))
 
 
 def cs_mppi_step(scene, desc: cs_mppi_desc, x0, U, eps, U_out, cost, weights, collide, params) -> int:

@@ -17,7 +17,7 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc);
 void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, float ns_scalar,
                  const float *ns_rows, Workspace &ws, uint32_t **perm_out, cudaStream_t s);
 void launch_group(const float *metric, const uint8_t *collide, int Q, int G, float *gm, uint8_t *gc,
-                  cudaStream_t s);
+                  cudaStream_t s, unsigned *err = nullptr);
 int tile_configs(int32_t *ids, int32_t cap);
 void launch_pose(const float *poses, int64_t P, const float *offsets, int K, float radius,
                  float *out, cudaStream_t s);
@@ -54,7 +54,7 @@ constexpr int64_t kMaxRows = (int64_t)1 << 30;
 static void free_ws(Workspace *w) {
     void *ptrs[] = {w->keys[0], w->keys[1], w->vals[0], w->vals[1], w->sort_hist, w->scan_tmp,
                     w->qrec, w->qns, w->io_prims, w->io_ns, w->io_metric, w->io_collide,
-                    w->io_count, w->io_grad, w->io_gout, w->io_gm, w->io_gc, w->mppi, w->rrt, w->rnd, w->rnd2, w->sweep_rec, w->err};
+                    w->io_count, w->io_grad, w->io_gout, w->io_gm, w->io_gc, w->mppi, w->rrt, w->rnd, w->rnd2, w->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete w;
@@ -85,8 +85,9 @@ Workspace *find_workspace(int device, cudaStream_t stream) {
 cs_status new_workspace(cudaStream_t stream, Workspace **out) {
     Workspace *w = new Workspace();
     w->stream = stream;
-    cudaError_t e = cudaMalloc(&w->err, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemsetAsync(w->err, 0, sizeof(unsigned), stream);
+    // the error word, then the tile counter of persistent kernel shapes
+    cudaError_t e = cudaMalloc(&w->err, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->err, 0, 2 * sizeof(unsigned), stream);
     if (e != cudaSuccess) {
         free_ws(w);
         return cuda_fail(e, "workspace error word");
@@ -114,18 +115,8 @@ cs_status get_workspace(int device, cudaStream_t stream, size_t Q, bool host_io,
 }
 
 cs_status sweep_reserve(Workspace *w, int64_t Q, int prim_type, int S) {
-    cs_status st = grow_workspace(w, (size_t)(Q * S), false);
-    if (st != CS_OK) return st;
-    const size_t need = (size_t)(prim_type == CS_PRIM_SPHERE ? 1 : 3) * (size_t)std::max<int64_t>(Q, 1);
-    if (w->cap_sweep < need) {
-        if (w->sweep_rec) CS_CUDA(cudaFree(w->sweep_rec));
-        w->sweep_rec = nullptr;
-        w->cap_sweep = 0;
-        const size_t cap = std::max(need, w->cap_sweep + w->cap_sweep / 2);
-        CS_CUDA(cudaMalloc(&w->sweep_rec, sizeof(float4) * cap));
-        w->cap_sweep = cap;
-    }
-    return CS_OK;
+    (void)prim_type;
+    return grow_workspace(w, (size_t)(Q * S), false);
 }
 
 cs_status grow_workspace(Workspace *w, size_t Q, bool host_io) {
@@ -221,6 +212,7 @@ cs_status cs_params_init(cs_params *p) {
 }
 
 cs_status cs_scene_create(const cs_scene_desc *desc, void *stream, cs_scene **out) {
+    NvtxRange range("cs.scene_create");
     if (!out) return invalid("out is NULL");
     *out = nullptr;
     if (!desc) return invalid("desc is NULL");
@@ -394,38 +386,34 @@ cs_status query_common(const cs_scene *s, int32_t prim_type, const float *prims,
     }
 
     uint32_t *perm = nullptr;
-    launch_prep(d_prims, prim_type, (int)Q, sc->dev, S > 1 ? 0.f : conservatism, d_ns, *ws, &perm, stream);
+    {
+        NvtxRange r("cs.query.prep");
+        launch_prep(d_prims, prim_type, (int)Q, sc->dev, S > 1 ? 0.f : conservatism, d_ns, *ws, &perm, stream);
+    }
     CS_CUDA(cudaGetLastError());
+    // a sweep's S copies of every sorted row are launch rows p S + s, made in
+    // the kernel from the one prepared row: one tile holds all n_sigma values
+    // of its primitives, which share staged chunks
     const float4 *rows = ws->qrec;
     const float *rows_ns = ws->qns;
-    int64_t Qrows = Q;
-    if (S > 1) {
-        // the S copies of every sorted row next to each other: one tile holds
-        // all n_sigma values of its primitives, which share staged chunks
-        const int recs = prim_type == CS_PRIM_SPHERE ? 1 : 3;
-        CS_CUDA(cudaMemcpyAsync(ws->sweep_rec, ws->qrec, sizeof(float4) * recs * (size_t)Q, cudaMemcpyDeviceToDevice,
-                                stream));
-        uint32_t *perm2 = perm == ws->vals[0] ? ws->vals[1] : ws->vals[0];
-        float *ns2 = reinterpret_cast<float *>(ws->keys[0]);
-        launch_sweep_expand(ws->sweep_rec, perm, (int)Q, recs, S, p.sweep_nsigma, ws->qrec, ns2, perm2, stream);
-        CS_CUDA(cudaGetLastError());
-        perm = perm2;
-        rows_ns = ns2;
-        Qrows = Q * S;
-    }
+    const int64_t Qrows = Q * S;
     unsigned *gflags = nullptr;  // flags mode: a row of the group collides (early exit of the others)
     if (flags && p.group_size > 0) {
         gflags = reinterpret_cast<unsigned *>(ws->io_metric);
         CS_CUDA(cudaMemsetAsync(gflags, 0, 4 * (size_t)ng, stream));
     }
-    CS_CUDA(run_eval(prim_type, sc->dev, rows, rows_ns, perm, (int)Qrows, p, fwd_out ? d_metric : nullptr,
-                     fwd_out ? d_col : nullptr, fwd_out ? d_cnt : nullptr, d_gout, grad ? d_grad : nullptr,
-                     ws->err, sc->num_sms, kWaitPolls, stream, gflags));
+    {
+        NvtxRange r(grad ? "cs.query.eval_adjoint" : "cs.query.eval");
+        CS_CUDA(run_eval(prim_type, sc->dev, rows, rows_ns, perm, (int)Qrows, p, fwd_out ? d_metric : nullptr,
+                         fwd_out ? d_col : nullptr, fwd_out ? d_cnt : nullptr, d_gout, grad ? d_grad : nullptr,
+                         ws->err, sc->num_sms, kWaitPolls, stream, gflags));
+    }
     if (fwd_out && has_group) {
+        NvtxRange r("cs.query.group");
         for (int b = 0; b < S; ++b)  // groups within each n_sigma block
             launch_group(d_metric ? d_metric + (size_t)b * Q : nullptr, d_col ? d_col + (size_t)b * Q : nullptr,
                          (int)Q, p.group_size, d_gm ? d_gm + (size_t)b * ng : nullptr,
-                         d_gc ? d_gc + (size_t)b * ng : nullptr, stream);
+                         d_gc ? d_gc + (size_t)b * ng : nullptr, stream, ws->err);
         CS_CUDA(cudaGetLastError());
     }
     if (p.host_io) {
@@ -505,6 +493,10 @@ cs_status cs_sync(const cs_scene *s, void *stream) {
         g_err = "a bounded device-side wait ran out";
         return CS_ERR_TIMEOUT;
     }
+    if (e & kErrBounds) {
+        g_err = "a device-side index check failed (CS_DEBUG build); the access was skipped";
+        return CS_ERR_BOUNDS;
+    }
     if (e & kErrInvalidQuery) {
         g_err = "invalid query rows (non-finite value, non-positive radius/axis or n_sigma < 0)";
         return CS_ERR_INVALID_ARG;
@@ -547,6 +539,6 @@ int64_t cs_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 
 const char *cs_last_error(void) { return g_err.c_str(); }
 
-const char *cs_version(void) { return "cs_b300 1.1 (sm_103a)"; }
+const char *cs_version(void) { return kDebugBuild ? "cs_b300 1.2 (sm_103a, CS_DEBUG)" : "cs_b300 1.2 (sm_103a)"; }
 
 }  // extern "C"

@@ -24,6 +24,7 @@ struct BuildStats {
     unsigned hist[kSigmaBins];
     int sigma_grid_max;   // ordered-int max scale over the main tier
     unsigned n_main;      // kept Gaussians in the main tier
+    unsigned dbg_err;     // kErrBounds: an index check of a CS_DEBUG build failed
 };
 
 __device__ __forceinline__ bool finite3(float a, float b, float c) {
@@ -161,9 +162,9 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float4 *__restrict__ po
 
 // Means in sorted order (input of the greedy chunking).
 __global__ void k_gather_pos(const uint32_t *__restrict__ perm, const float4 *__restrict__ pos, int n,
-                             float4 *__restrict__ spos) {
+                             float4 *__restrict__ spos, int n_in, unsigned *dbg) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n) spos[p] = pos[perm[p]];
+    if (p < n && CS_IDX_OK(perm[p] < (uint32_t)n_in, dbg)) spos[p] = pos[perm[p]];
 }
 
 // Greedy chunking, one thread per segment of kSegment sorted Gaussians
@@ -174,7 +175,7 @@ __global__ void k_gather_pos(const uint32_t *__restrict__ perm, const float4 *__
 // each Gaussian's slot = 32 * chunk + lane.
 __global__ void k_chunk_greedy(const float4 *__restrict__ spos, int n_main, int n_kept, int seg_main,
                                int nseg, float ext_main, float ext_large, const uint32_t *__restrict__ base,
-                               uint32_t *__restrict__ counts, uint32_t *__restrict__ slot) {
+                               uint32_t *__restrict__ counts, uint32_t *__restrict__ slot, unsigned *dbg) {
     const int sg = blockIdx.x * blockDim.x + threadIdx.x;
     if (sg >= nseg) return;
     int p0, p1;
@@ -213,7 +214,8 @@ __global__ void k_chunk_greedy(const float4 *__restrict__ spos, int n_main, int 
             if (k == 0) {
                 lx = hx = P.x; ly = hy = P.y; lz = hz = P.z;
             }
-            if (base) slot[p] = (c0 + c) * kChunk + (uint32_t)k;
+            // base[nseg] is the chunk count: every slot must lie below 32 times it
+            if (base && CS_IDX_OK(c0 + c < base[nseg], dbg)) slot[p] = (c0 + c) * kChunk + (uint32_t)k;
             ++k;
         }
     }
@@ -237,11 +239,13 @@ __global__ void k_scatter_slots(const uint32_t *__restrict__ slot_in, const uint
                                 int n_gauss, const float4 *__restrict__ pos, const float4 *__restrict__ covA,
                                 const float4 *__restrict__ covB, ChunkBlock *__restrict__ blocks,
                                 float *__restrict__ slot_smax, float *__restrict__ smax,
-                                int32_t *__restrict__ index, int32_t *__restrict__ slot_of) {
+                                int32_t *__restrict__ index, int32_t *__restrict__ slot_of, int nchunks,
+                                int n_in, unsigned *dbg) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_gauss) return;
     const uint32_t slot = slot_in[p];
     const uint32_t i = perm[p];
+    if (!CS_IDX_OK(slot < (uint32_t)nchunks * kChunk && i < (uint32_t)n_in, dbg)) return;
     const float4 P = pos[i], A = covA[i], B = covB[i];
     ChunkBlock &b = blocks[slot / kChunk];
     const int l = (int)(slot % kChunk);
@@ -446,9 +450,10 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     const float ext_main = h, ext_large = 4.f * h;
     CS_CUDA(cudaMemsetAsync(seg_cnt, 0, 4 * ((size_t)nseg + 1), s));
     if (n_kept > 0) {
-        k_gather_pos<<<blocks_for(n_kept), kThreads, 0, s>>>(vals[res], upos, (int)n_kept, spos);
+        k_gather_pos<<<blocks_for(n_kept), kThreads, 0, s>>>(vals[res], upos, (int)n_kept, spos, (int)n,
+                                                             &st->dbg_err);
         k_chunk_greedy<<<(nseg + 127) / 128, 128, 0, s>>>(spos, (int)n_main, (int)n_kept, seg_main, nseg, ext_main,
-                                                          ext_large, nullptr, seg_cnt, nullptr);
+                                                          ext_large, nullptr, seg_cnt, nullptr, &st->dbg_err);
         count_launches(2);
     }
     scan_exclusive(seg_cnt, seg_base, (size_t)nseg + 1, (uint32_t *)tmp_scan.p, s);
@@ -457,7 +462,7 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     CS_CUDA(cudaMemcpyAsync(&bounds[1], seg_base + nseg, 4, cudaMemcpyDeviceToHost, s));
     if (n_kept > 0) {
         k_chunk_greedy<<<(nseg + 127) / 128, 128, 0, s>>>(spos, (int)n_main, (int)n_kept, seg_main, nseg, ext_main,
-                                                          ext_large, seg_base, nullptr, slot);
+                                                          ext_large, seg_base, nullptr, slot, &st->dbg_err);
         count_launches(1);
     }
     CS_CUDA(cudaGetLastError());
@@ -514,7 +519,8 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
         k_fill_padding<<<(unsigned)(((int64_t)nchunks * kChunk + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             blocks, nchunks, slot_smax);
         k_scatter_slots<<<blocks_for(n_kept), kThreads, 0, s>>>(slot, vals[res], (int)n_kept, upos, ucovA, ucovB,
-                                                                blocks, slot_smax, smax, index, slot_of);
+                                                                blocks, slot_smax, smax, index, slot_of, nchunks,
+                                                                (int)n, &st->dbg_err);
         k_chunk_headers<<<(unsigned)(((int64_t)nchunks * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             blocks, nchunks, slot_smax, chead);
         count_launches(3);
@@ -532,6 +538,14 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     }
     CS_CUDA(cudaGetLastError());
     CS_CUDA(cudaStreamSynchronize(s));
+    if (kDebugBuild) {
+        unsigned dbg = 0;
+        CS_CUDA(cudaMemcpy(&dbg, &st->dbg_err, sizeof(dbg), cudaMemcpyDeviceToHost));
+        if (dbg) {
+            set_error("a device-side index check failed in the scene build (CS_DEBUG build)");
+            return CS_ERR_BOUNDS;
+        }
+    }
 
     sc->n_kept = n_kept;
     sc->n_grid = n_main;

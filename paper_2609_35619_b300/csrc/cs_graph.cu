@@ -10,11 +10,33 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
+#include <string>
 #include <vector>
 
 #include "cs_internal.cuh"
 
 namespace cs {
+
+// Autotuner log (cs_autotune_log): the file every cs_autotune call appends
+// one JSON line to, or empty.
+static std::mutex g_tune_log_mu;
+static std::string g_tune_log;
+
+static void append_tune_log(const Scene *sc, int prim_type, const cs_params &p, int64_t Q, int S, int reps,
+                            const int32_t *ids, const float *times, int n, int32_t best) {
+    std::lock_guard<std::mutex> lk(g_tune_log_mu);
+    if (g_tune_log.empty()) return;
+    FILE *f = fopen(g_tune_log.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"n_gaussians\": %lld, \"prim_type\": %d, \"mode\": %d, \"exact_variance\": %d, "
+               "\"rows\": %lld, \"sweep\": %d, \"launch_rows\": %lld, \"reps\": %d, \"ms\": {",
+            (long long)sc->n_kept, prim_type, (int)p.mode, (int)p.exact_variance, (long long)Q, S,
+            (long long)(Q * S), reps);
+    for (int i = 0; i < n; ++i) fprintf(f, "%s\"%d\": %.6f", i ? ", " : "", (int)ids[i], (double)times[i]);
+    fprintf(f, "}, \"best\": %d}\n", (int)best);
+    fclose(f);
+}
 
 constexpr uint32_t kGraphMagic = 0xC5B300A7u;
 
@@ -223,6 +245,7 @@ cs_status cs_graph_destroy(cs_graph *h) {
 cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, int64_t Q,
                       float conservatism, const cs_params *params, int32_t reps, int32_t *best,
                       float *ms, int32_t cap) {
+    NvtxRange range("cs.autotune");
     cs_status st = check_scene(scene);
     if (st != CS_OK) return st;
     if (!best) return invalid("best is NULL");
@@ -254,6 +277,7 @@ cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, in
         return cuda_fail(cudaErrorUnknown, "cudaEventCreate");
     }
     int32_t ids[32];
+    float times[32];
     const int n = tile_configs(ids, 32);
     float best_ms = INFINITY;
     int32_t best_id = 0;
@@ -277,6 +301,7 @@ cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, in
         }
         if (st != CS_OK) break;
         const float mean = (float)(total / reps);
+        times[i] = mean;
         if (ms && i < cap) ms[i] = mean;
         if (mean < best_ms) {
             best_ms = mean;
@@ -290,7 +315,14 @@ cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, in
         std::lock_guard<std::mutex> lk(sc->tune_mu);
         sc->tuned[tune_key(prim_type, p.mode, Q * S)] = best_id;  // keyed by the launch's rows
     }
+    append_tune_log(sc, prim_type, p, Q, S, reps, ids, times, n, best_id);
     *best = best_id;
+    return CS_OK;
+}
+
+cs_status cs_autotune_log(const char *path) {
+    std::lock_guard<std::mutex> lk(g_tune_log_mu);
+    g_tune_log = path ? path : "";
     return CS_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -23,9 +24,34 @@ constexpr float kSigmaLog2Lo = -32.f;  // histogram covers 2^-32 .. 2^32 in 1/8 
 constexpr float kSigmaBinsPerOctave = 8.f;
 constexpr float kReachPadRel = 1e-4f;  // relative padding of every cull radius
 
+// A named NVTX range over the enclosing scope (host timeline): scene build,
+// query preparation, the fused kernel, group epilogue, serving batches,
+// autotuning.  NVTX v3 is header-only and costs a branch unless a profiler
+// has attached, so the ranges are always compiled in.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // device error word bits
 constexpr unsigned kErrInvalidQuery = 1u;
 constexpr unsigned kErrTimeout = 2u;
+constexpr unsigned kErrBounds = 4u;    // an index check of a CS_DEBUG build failed
+
+// CS_IDX_OK(cond, err): in a CS_DEBUG build, evaluates the index condition
+// `cond`; when it is false, records kErrBounds in the error word `err` and
+// yields false so that the caller skips the access (no trap: the context
+// stays usable and cs_sync reports CS_ERR_BOUNDS).  In a normal build it is
+// `true` and the condition is not evaluated.
+#ifdef CS_DEBUG
+#define CS_IDX_OK(cond, err) ((cond) ? true : (atomicOr((err), ::cs::kErrBounds), false))
+constexpr bool kDebugBuild = true;
+#else
+#define CS_IDX_OK(cond, err) true
+constexpr bool kDebugBuild = false;
+#endif
 
 // bounded wait: polls of mbarrier.try_wait before giving up; the waits also
 // give up after one second of wall time
@@ -115,7 +141,6 @@ struct Workspace {
     void *rnd = nullptr;             size_t cap_rnd = 0;   // bytes: per (view, slot)
     void *rnd2 = nullptr;            size_t cap_rnd2 = 0;  // bytes: per instance
     // conservatism sweep (cs_params.sweep_count): the prepared rows before expansion
-    float4 *sweep_rec = nullptr;     size_t cap_sweep = 0; // float4
     unsigned *err = nullptr;         // device error word
 };
 
@@ -198,12 +223,9 @@ inline int sweep_blocks(const cs_params &p) { return p.sweep_count >= 2 ? p.swee
 struct SweepNs {
     float v[8];
 };
-// Scratch of a sweep over Q rows (workspace for S Q rows, the unexpanded rows).
+// Scratch of a sweep over Q rows: per-row outputs of S Q rows (group-only
+// requests); the Q rows themselves are prepared once and copied in the kernel.
 cs_status sweep_reserve(Workspace *w, int64_t Q, int prim_type, int S);
-// Expand Q prepared rows (sorted) into S consecutive rows each: records,
-// n_sigma of block s, output row s Q + perm[p].
-void launch_sweep_expand(const float4 *rec_in, const uint32_t *perm_in, int Q, int recs, int S, const float *ns,
-                         float4 *rec_out, float *ns_out, uint32_t *perm_out, cudaStream_t s);
 
 #define CS_CUDA(call)                                                  \
     do {                                                               \

@@ -275,6 +275,7 @@ extern "C" {
 cs_status cs_mppi_step(const cs_scene *scene, const cs_mppi_desc *desc, const float *x0, const float *U,
                        const float *eps, float *U_out, float *cost, float *weights, uint8_t *collide,
                        const cs_params *params) {
+    NvtxRange range("cs.mppi_step");
     return mppi_common(scene, desc, x0, U, eps, U_out, cost, weights, collide, params, nullptr);
 }
 
@@ -284,6 +285,7 @@ extern "C" {
 
 cs_status cs_path_refine(const cs_scene *scene, const cs_refine_desc *d, const float *ctrl, const float *eps,
                          float *ctrl_out, float *cost, float *weights, const cs_params *params) {
+    NvtxRange range("cs.path_refine");
     cs_status st = check_scene(scene);
     if (st != CS_OK) return st;
     if (!d) return invalid("desc is NULL");

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "cs_internal.cuh"
 
@@ -52,9 +53,21 @@ struct QueryConsts {
 struct EvalArgs {
     SceneDev sc;
     const float4 *qrec;      // prepared primitives, sorted order, RECS float4 each
-    const float *qns;        // n_sigma per sorted primitive
+    const float *qns;        // n_sigma per sorted primitive (not read by sweeps)
     const uint32_t *perm;    // sorted position -> input row
-    int Q;
+    int Q;                   // launch rows (S Qb for a sweep)
+    // A conservatism sweep (S > 1) evaluates S copies of each of the Qb
+    // prepared primitives: launch row q = p S + s is sorted primitive p at
+    // n_sigma sw.v[s], written to output row s Qb + perm[p].  The copies are
+    // made here, row by row, so no expanded records exist in memory.
+    int S;
+    int Qb;
+    SweepNs sw;
+    // persistent shapes: tiles are taken from this per-launch counter (zeroed
+    // before the launch), ntiles of them
+    int *tile_ctr;
+    int ntiles;
+    int num_sms;
     QueryConsts k;
     float *out_metric;
     uint8_t *out_collide;
@@ -68,6 +81,28 @@ struct EvalArgs {
     unsigned *gflags;        // flags mode with groups: per group, set once a row of it collides
 };
 
+// Launch row q: its prepared record, its n_sigma and its output row.
+template <int RECS>
+__device__ __forceinline__ const float4 *row_rec(const EvalArgs &a, int q) {
+    const int p = a.S > 1 ? q / a.S : q;
+    return a.qrec + (size_t)(CS_IDX_OK(p >= 0 && p < a.Qb, a.err) ? p : 0) * RECS;
+}
+__device__ __forceinline__ float row_ns(const EvalArgs &a, int q) {
+    return a.S > 1 ? a.sw.v[q % a.S] : a.qns[q];
+}
+__device__ __forceinline__ uint32_t row_out(const EvalArgs &a, int q) {
+    uint32_t r;
+    if (a.S > 1) {
+        const int p = q / a.S;
+        r = (uint32_t)(q - p * a.S) * (uint32_t)a.Qb + a.perm[p];
+    } else {
+        r = a.perm[q];
+    }
+    // an output row outside the launch's rows would be written out of range:
+    // a CS_DEBUG build records it and redirects the write to row 0
+    return CS_IDX_OK(r < (uint32_t)a.Q, a.err) ? r : 0u;
+}
+
 // Kernel shape: NCW consumer warps, each owning QW primitives of the tile,
 // one producer warp, NS pipeline stages of CHB chunk blocks each, and MINB
 // CTAs resident per SM (the register budget follows from it).
@@ -76,9 +111,14 @@ struct EvalArgs {
 // exactly nothing, st2 > S_cut); larger groups give the scheduler more
 // independent dependency chains per basic block.  GROUP == QW drops the
 // per-primitive test altogether.
-template <int NCW_, int QW_, int NS_, int CHB_, int MINB_, int GROUP_ = 2, int IL_ = 0>
+template <int NCW_, int QW_, int NS_, int CHB_, int MINB_, int GROUP_ = 2, int IL_ = 0, bool PERSIST_ = false>
 struct Cfg {
     static constexpr int NCW = NCW_, QW = QW_, NS = NS_, CHB = CHB_, MINB = MINB_, GROUP = GROUP_;
+    // PERSIST: a grid of (SMs x MINB) CTAs, each taking tiles from a device
+    // counter until none are left; the producer warp culls and stages the next
+    // tile while the consumer warps finish the current one (the stage ring runs
+    // on across tiles, a terminator stage between them)
+    static constexpr bool PERSIST = PERSIST_;
     // IL = 0: consumer warp w takes rows w QW .. w QW + QW - 1 of the tile (a
     // compact warp box); IL = 1: rows w, w + NCW, ...; IL = 2: row pairs
     // (2w, 2w + 1), (2w + 2 NCW, 2w + 2 NCW + 1), ...; IL = 4: row quads
@@ -144,6 +184,12 @@ struct __align__(16) EvalSmem {
     // per consumer warp: the stage's slots that pass the warp test, by rank
     // (the quad tests of sweep launches)
     int slots[C::NCW][32];
+    // persistent shapes: tile indices from the producer to the consumer
+    // warps, two deep (tfull: one arrival by the producer; tempty: one per
+    // consumer warp once it has read the index)
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    int tile_q[2];
 };
 
 template <int PRIM> struct PrimTraits;
@@ -217,6 +263,7 @@ struct Producer {
     int k = 0;       // stage sequence number
     int nslot = 0;   // chunk slots filled in the open stage
     bool failed = false;
+    unsigned *err = nullptr;  // the stream's error word (index checks of CS_DEBUG builds)
     bool early = false;   // flags mode: stop staging once every consumer warp is settled
     bool halted = false;
     int lane;
@@ -255,6 +302,7 @@ struct Producer {
     // each chunk's index and its number of real slots.
     __device__ void emit_run(int c, int len) {
         if (early && !halted) halted = __shfl_sync(0xffffffffu, *(volatile int *)&sm->active == 0, 0);
+        if (!CS_IDX_OK(c >= 0 && len >= 0 && c + len <= sc->nchunks, err)) len = 0;  // stage nothing
         while (len > 0 && !failed && !halted) {
             const int st = k % C::NS;
             const int take = min(len, C::CHB - nslot);
@@ -339,6 +387,21 @@ struct Producer {
         }
         __syncwarp();
     }
+    // Persistent shapes: end the tile with a terminator stage and open the
+    // next stage of the ring (the consumers release terminators too).
+    __device__ void finish_tile() {
+        if (failed) return;
+        if (nslot > 0) close_stage();
+        if (failed) return;
+        const int s = k % C::NS;
+        if (lane == 0) {
+            sm->count[s] = 0;  // terminator
+            mbar_arrive(&sm->full[s]);
+        }
+        __syncwarp();
+        ++k;
+        open_stage();
+    }
     // After a failed wait: close the open stage so its copies can complete,
     // then wait (bounded) for every stage's latest phase.
     __device__ void drain() {
@@ -357,15 +420,17 @@ struct Producer {
     }
 };
 
+// The tile's box of primitive centres and its largest reach parameters
+// (alpha, beta), warp-wide, and its kSub sub-boxes of consecutive rows into
+// shared memory (read by the producer's cull only).
 template <int PRIM, class C, bool EX>
-__device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool early) {
+__device__ __forceinline__ void tile_bounds(const EvalArgs &a, EvalSmem<C> *sm, int tile, int lane, float &lx,
+                                            float &ly, float &lz, float &hx, float &hy, float &hz, float &al,
+                                            float &be) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int TQ = C::NCW * C::QW;
-    const int lane = threadIdx.x & 31;
-    const long long t_start = clock64();
-    const SceneDev &sc = a.sc;
-    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY,
-          hz = -INFINITY, al = 0.f, be = 0.f;
+    lx = INFINITY; ly = INFINITY; lz = INFINITY; hx = -INFINITY; hy = -INFINITY; hz = -INFINITY;
+    al = 0.f; be = 0.f;
     const int q0 = tile * TQ;
     constexpr int RS = TQ / kSub;  // rows per sub-box (4, 8 or 16: within one pass of 32 lanes)
     static_assert(TQ % kSub == 0 && RS <= 32 && 32 % RS == 0, "sub-boxes split the tile's rows evenly");
@@ -375,10 +440,10 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool
         float cx = INFINITY, cy = INFINITY, cz = INFINITY, dx = -INFINITY, dy = -INFINITY, dz = -INFINITY;
         float alpha = 0.f, beta = 0.f;
         if (t < TQ && q < a.Q) {
-            const float4 *rec = a.qrec + (size_t)q * RECS;
+            const float4 *rec = row_rec<RECS>(a, q);
             const float4 r0 = rec[0];
             if (rec_valid(r0)) {
-                prim_reach<PRIM, EX>(rec, a.qns[q], a.k.S_reach, alpha, beta);
+                prim_reach<PRIM, EX>(rec, row_ns(a, q), a.k.S_reach, alpha, beta);
                 cx = dx = r0.x; cy = dy = r0.y; cz = dz = r0.z;
             }
         }
@@ -415,8 +480,18 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool
         al = fmaxf(al, __shfl_xor_sync(0xffffffffu, al, o));
         be = fmaxf(be, __shfl_xor_sync(0xffffffffu, be, o));
     }
+}
+
+template <int PRIM, class C, bool EX>
+__device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool early) {
+    const int lane = threadIdx.x & 31;
+    const long long t_start = clock64();
+    const SceneDev &sc = a.sc;
+    float lx, ly, lz, hx, hy, hz, al, be;
+    tile_bounds<PRIM, C, EX>(a, sm, tile, lane, lx, ly, lz, hx, hy, hz, al, be);
     Producer<PRIM, C, EX> pr{sm, &sc, a.wait_polls, lx, ly, lz, hx, hy, hz, al, be};
     pr.early = early;
+    pr.err = a.err;
     pr.lane = lane;
     pr.t0 = t_start;
     const bool any = lx <= hx;  // at least one valid primitive
@@ -434,6 +509,58 @@ __device__ void producer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, bool
         atomicAdd(a.kstats + 11, pr.n_wait_cycles);
         atomicAdd(a.kstats + 13, pr.t_first);
         atomicAdd(a.kstats + 15, 1ull);
+    }
+}
+
+// Persistent shapes: the producer takes tile after tile from the launch's
+// counter, hands each index to the consumer warps through the two-deep tile
+// queue (tile_q), and culls and stages it; the consumers' terminator releases
+// close each tile.  A final index >= ntiles (or -1 after a failed wait) ends
+// the consumers.
+template <int PRIM, class C, bool EX>
+__device__ void producer_persistent(const EvalArgs &a, EvalSmem<C> *sm) {
+    const int lane = threadIdx.x & 31;
+    const long long t_start = clock64();
+    const SceneDev &sc = a.sc;
+    Producer<PRIM, C, EX> pr{sm, &sc, a.wait_polls, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    pr.err = a.err;
+    pr.lane = lane;
+    pr.t0 = t_start;
+    unsigned long long tiles = 0;
+    for (int i = 0;; ++i) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(a.tile_ctr, 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        const int slot = i & 1;
+        bool ok = true;
+        if (i >= 2 && lane == 0)  // the consumers have read index i - 2 from this slot
+            ok = wait_phase(&sm->tempty[slot], (unsigned)(((i >> 1) - 1) & 1), a.wait_polls) >= 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) pr.failed = true;
+        if (lane == 0) {
+            sm->tile_q[slot] = pr.failed ? -1 : tile;
+            mbar_arrive(&sm->tfull[slot]);  // release: the index is visible to the waiting consumers
+        }
+        __syncwarp();
+        if (pr.failed || tile >= a.ntiles) break;
+        tile_bounds<PRIM, C, EX>(a, sm, tile, lane, pr.lx, pr.ly, pr.lz, pr.hx, pr.hy, pr.hz, pr.al, pr.be);
+        if (pr.lx <= pr.hx && sc.nchunks > 0) pr.descend();
+        pr.finish_tile();
+        ++tiles;
+        if (pr.failed) break;
+    }
+    if (pr.failed) {
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
+        pr.drain();
+    }
+    if (a.kstats && lane == 0) {
+        atomicAdd(a.kstats + 4, pr.n_chunks);
+        atomicAdd(a.kstats + 5, (unsigned long long)pr.k);
+        atomicAdd(a.kstats + 7, pr.n_polls);
+        atomicAdd(a.kstats + 10, (unsigned long long)(clock64() - t_start));
+        atomicAdd(a.kstats + 11, pr.n_wait_cycles);
+        atomicAdd(a.kstats + 13, pr.t_first);
+        atomicAdd(a.kstats + 15, tiles);
     }
 }
 
@@ -837,6 +964,19 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
             if ((SH & kShGeom) && GROUP == 4 && ((same >> j0) & (same >> (j0 + 2)) & (link >> (j0 + 2)) & 1u)) {
                 // rows j0 .. j0 + 3 are one sphere: the geometry once, four tails
                 geom_g2<EX>(g2, wqd[j0], r2, sq);
+                // The quad's highest n_sigma copy first.  st2 does not increase
+                // with n_sigma, in FP32 too (fma is monotone in each operand and
+                // the scale 1/r^2 is positive), so when no lane holds a neighbour
+                // of that copy (st2 <= S_cut), no copy has a neighbour or an
+                // in-collision pair among these Gaussians (st2 < T_in implies
+                // st2 <= S_cut), and the four tails would add exactly nothing.
+                {
+                    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&wqd[j0][1]);  // -cz, 1/r^2
+                    const f32x2 nmax = *reinterpret_cast<const f32x2 *>(&wqd[j0][2].z);       // -2 n_max
+                    float t0, t1;
+                    upk2(mul2(fma2(nmax, sq, r2), pb.y), t0, t1);
+                    if (!__any_sync(0xffffffffu, t0 <= k.S_cut_u || t1 <= k.S_cut_u)) continue;
+                }
 #pragma unroll
                 for (int j = j0; j < j0 + 4; ++j) tail_g2<QW, K0>(A, j, r2, sq, wqd[j], k, nG2, Gs2);
             } else if ((SH & kShGeom) && GROUP == 2 && ((same >> j0) & 1u)) {
@@ -932,8 +1072,12 @@ __device__ __forceinline__ void eval_chunk(Acc<PRIM, QW, MODE, GRAD> &A, const C
     }
 }
 
+// kkp (persistent shapes): the stage sequence number, continued across tiles;
+// the tile's terminator stage is released and *kkp advanced past it.
+// Returns false when a bounded wait gave up.
 template <int PRIM, class C, int MODE, bool GRAD, bool EX, int SH>
-__device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int warp, bool abort) {
+__device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int warp, bool abort,
+                              int *kkp = nullptr) {
     constexpr int RECS = PrimTraits<PRIM>::RECS;
     constexpr int QW = C::QW;
     constexpr int TQ = C::NCW * QW;
@@ -947,10 +1091,10 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         const int q = tile * TQ + C::row(warp, lane);
         float4 d0 = make_float4(0, 0, 0, 0), d1 = d0, d2 = d0, d3 = d0;
         if (q < a.Q) {
-            const float4 *rec = a.qrec + (size_t)q * RECS;
+            const float4 *rec = row_rec<RECS>(a, q);
             const float4 r0 = rec[0];
             if (rec_valid(r0)) {
-                const float ns = a.qns[q];
+                const float ns = row_ns(a, q);
                 float alpha, beta;
                 prim_reach<PRIM, EX>(rec, ns, k.S_reach, alpha, beta);
                 if (PRIM == 0) {
@@ -980,7 +1124,8 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     int mygrp = -1;
     if (MODE == 3 && a.gflags && k.group_size > 0 && lane < QW && ((wvalid >> lane) & 1u)) {
         const int q = tile * TQ + C::row(warp, lane);
-        mygrp = (int)(a.perm[q] / (uint32_t)k.group_size);
+        mygrp = (int)(row_out(a, q) / (uint32_t)k.group_size);
+        if (!CS_IDX_OK(mygrp < (a.Q + k.group_size - 1) / k.group_size, a.err)) mygrp = -1;
     }
     if (MODE == 3 && wlive == 0u && lane == 0) atomicSub(&sm->active, 1);
     __syncwarp();
@@ -990,6 +1135,16 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         wqd[lane][0] = make_float4(-a.x, -a.x, -a.y, -a.y);
         wqd[lane][1] = make_float4(-a.z, -a.z, a.w, a.w);
         wqd[lane][2] = make_float4(-b.x, -b.x, 0.f, 0.f);
+    }
+    __syncwarp();
+    if ((SH & kShGeom) && PRIM == 0 && lane < QW && (lane & 3) == 0) {
+        // row quads of a sweep: -2 n_max of rows lane .. lane + 3 beside row lane's -2 n
+        // (read only when the four rows are one sphere)
+        float m = wqd[lane][2].x;
+#pragma unroll
+        for (int r = 1; r < 4; ++r) m = fminf(m, wqd[lane + r][2].x);
+        wqd[lane][2].z = m;
+        wqd[lane][2].w = m;
     }
     __syncwarp();
     // same, bit j (j even): rows j and j + 1 are the same sphere (centre and
@@ -1078,7 +1233,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     const long long c_start = clock64();
     int group = -1;               // chunk group of the cost partials
     bool ok = !abort;
-    for (int kk = 0; ok; ++kk) {
+    for (int kk = kkp ? *kkp : 0; ok; ++kk) {
         const int s = kk % C::NS;
         bool got = true;
         if (lane == 0) {
@@ -1093,7 +1248,14 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) { ok = false; break; }
         const int nslots = sm->count[s];
-        if (nslots == 0) break;
+        if (nslots == 0) {
+            if (kkp) {  // release the terminator: the ring runs on into the next tile
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->empty[s]);
+                *kkp = kk + 1;
+            }
+            break;
+        }
         ++c_stages;
         c_tested += (unsigned long long)nslots;
         if constexpr (MODE == 3) {
@@ -1249,7 +1411,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             // 1: in collision; 0: free; 2: not finished because its group collides
             const int cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
             if (lane == 0 && q < a.Q && a.out_collide) {
-                const uint32_t row = a.perm[q];
+                const uint32_t row = row_out(a, q);
                 a.out_collide[row] = (vq && ok) ? (cinj > k.k_thr ? 1 : ((wgset >> j) & 1u) ? 2 : 0) : 0;
             }
             continue;
@@ -1276,7 +1438,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 metric = cntj > 0 ? M - k.tau * 0.6931471805599453f * lg2_approx(acc) : INFINITY;
             }
             if (lane == 0 && q < a.Q) {
-                const uint32_t row = a.perm[q];
+                const uint32_t row = row_out(a, q);
                 const bool good = vq && ok;
                 if (a.out_metric) a.out_metric[row] = good ? metric : __int_as_float(0x7fc00000);
                 if (a.out_collide) a.out_collide[row] = (good && cinj > k.k_thr) ? 1 : 0;
@@ -1311,7 +1473,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 const float metric = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? tot * k.d_max / (float)cntj : 0.f)
                                                                      : tot * k.d_max;
                 if (lane == 0 && q < a.Q) {
-                    const uint32_t row = a.perm[q];
+                    const uint32_t row = row_out(a, q);
                     const bool good = vq && ok;
                     if (a.out_metric) a.out_metric[row] = good ? metric : __int_as_float(0x7fc00000);
                     if (a.out_collide) a.out_collide[row] = (good && cinj > k.k_thr) ? 1 : 0;
@@ -1319,9 +1481,12 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 }
             }
             if (lane == 0 && q < a.Q) {
-                const uint32_t row = a.perm[q];
+                const uint32_t row = row_out(a, q);
                 float up = 1.f;
-                if (a.grad_out) up = a.grad_out[k.group_size > 0 ? row / (uint32_t)k.group_size : row];
+                if (a.grad_out) {
+                    const uint32_t gi = k.group_size > 0 ? row / (uint32_t)k.group_size : row;
+                    up = a.grad_out[CS_IDX_OK(gi < (uint32_t)a.Q, a.err) ? gi : 0u];
+                }
                 const bool good = vq && ok;
                 const float nanv = __int_as_float(0x7fc00000);
                 a.grad_centres[3 * (size_t)row + 0] = good ? gx * f * up : nanv;
@@ -1348,6 +1513,7 @@ __device__ void consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         atomicAdd(a.kstats + 12, c_first);
         atomicAdd(a.kstats + 14, (unsigned long long)(c_end - c_loop_end));
     }
+    return ok;
 }
 
 template <int PRIM, class C, int MODE, bool GRAD, bool EX = false, int SH = 0>
@@ -1360,17 +1526,65 @@ __global__ void __launch_bounds__((C::NCW + 1) * 32, C::MINB) k_eval(const EvalA
             mbar_init(&sm->full[s], 1);
             mbar_init(&sm->empty[s], C::NCW);
         }
+        if (C::PERSIST) {
+            for (int s = 0; s < 2; ++s) {
+                mbar_init(&sm->tfull[s], 1);
+                mbar_init(&sm->tempty[s], C::NCW);
+            }
+        }
         fence_mbar_init();
         sm->abort = (*(volatile unsigned *)a.err & kErrTimeout) ? 1 : 0;
         sm->active = C::NCW;
     }
     __syncthreads();
-    const int tile = blockIdx.x;
     const bool abort = sm->abort != 0;
-    if (warp == C::NCW) {
-        if (!abort) producer_warp<PRIM, C, EX>(a, sm, tile, MODE == 3);
+    if constexpr (C::PERSIST) {
+        static_assert(MODE != 3, "the flags mode's early exit runs one tile per CTA");
+        const int lane = threadIdx.x & 31;
+        if (warp == C::NCW) {
+            if (!abort) producer_persistent<PRIM, C, EX>(a, sm);
+        } else if (abort) {
+            // an earlier launch on this stream timed out: mark every row as
+            // the one-tile-per-CTA shapes do (NaN metric and gradient, flag and
+            // count 0), with no waits
+            for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x)
+                if (lane < C::QW) {
+                    const int q = t * C::NCW * C::QW + C::row(warp, lane);
+                    if (q < a.Q) {
+                        const uint32_t row = row_out(a, q);
+                        const float nanv = __int_as_float(0x7fc00000);
+                        if (a.out_metric) a.out_metric[row] = nanv;
+                        if (a.out_collide) a.out_collide[row] = 0;
+                        if (a.out_count) a.out_count[row] = 0;
+                        if (GRAD && a.grad_centres) {
+                            a.grad_centres[3 * (size_t)row + 0] = nanv;
+                            a.grad_centres[3 * (size_t)row + 1] = nanv;
+                            a.grad_centres[3 * (size_t)row + 2] = nanv;
+                        }
+                    }
+                }
+        } else {
+            int kk = 0;
+            for (int i = 0;; ++i) {
+                const int slot = i & 1;
+                bool got = true;
+                if (lane == 0) got = wait_phase(&sm->tfull[slot], (unsigned)((i >> 1) & 1), a.wait_polls) >= 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                const int t = got ? *(volatile int *)&sm->tile_q[slot] : -1;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->tempty[slot]);
+                if (!got && lane == 0) atomicOr(a.err, kErrTimeout);
+                if (t < 0 || t >= a.ntiles) break;
+                if (!consumer_warp<PRIM, C, MODE, GRAD, EX, SH>(a, sm, t, warp, false, &kk)) break;
+            }
+        }
     } else {
-        consumer_warp<PRIM, C, MODE, GRAD, EX, SH>(a, sm, tile, warp, abort);
+        const int tile = blockIdx.x;
+        if (warp == C::NCW) {
+            if (!abort) producer_warp<PRIM, C, EX>(a, sm, tile, MODE == 3);
+        } else {
+            consumer_warp<PRIM, C, MODE, GRAD, EX, SH>(a, sm, tile, warp, abort);
+        }
     }
 }
 
@@ -1491,7 +1705,7 @@ __global__ void k_prep_recs(const float *__restrict__ prims, int prim_type, int 
 // Section II-D/E group outputs: metric summed, flag OR-ed over runs of G rows
 // (a warp per group from kGroupWarpMin rows, else a thread per group).
 __global__ void k_group(const float *__restrict__ metric, const uint8_t *__restrict__ collide,
-                        int Q, int G, float *__restrict__ gm, uint8_t *__restrict__ gc) {
+                        int Q, int G, float *__restrict__ gm, uint8_t *__restrict__ gc, unsigned *err) {
     const int ng = (Q + G - 1) / G;
     float sum;
     unsigned c;
@@ -1499,6 +1713,7 @@ __global__ void k_group(const float *__restrict__ metric, const uint8_t *__restr
         const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
         if (g >= ng) return;  // whole warps leave together
         const int b = g * G, e = min(Q, b + G);
+        if (kDebugBuild && err && !CS_IDX_OK(b >= 0 && b < e && e <= Q, err)) return;
         group_rows_warp(metric, collide, b, e, threadIdx.x & 31, sum, c);
         if ((threadIdx.x & 31) != 0) return;
         if (gm) gm[g] = sum;
@@ -1507,6 +1722,7 @@ __global__ void k_group(const float *__restrict__ metric, const uint8_t *__restr
         const int g = blockIdx.x * blockDim.x + threadIdx.x;
         if (g >= ng) return;
         const int b = g * G, e = min(Q, b + G);
+        if (kDebugBuild && err && !CS_IDX_OK(b >= 0 && b < e && e <= Q, err)) return;
         group_rows_serial(metric, collide, b, e, sum, c);
         if (gm) gm[g] = sum;
         if (gc) gc[g] = (uint8_t)c;
@@ -1562,6 +1778,9 @@ QueryConsts make_consts(const cs_params &p) {
 //   25: shape 24 evaluating sphere primitives in groups of 4 (a quad)
 //   26: shape 19 with row quads evaluated in groups of 4
 //   27: 4 x 16, 2 stages x 24 chunks, 3 CTAs/SM, row quads in groups of 4
+//   28: shape 27 as a persistent kernel (SMs x 3 CTAs taking tiles from a
+//       counter; the producer stages the next tile while the consumers end
+//       the current one); the flags mode runs its own shapes
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1589,6 +1808,7 @@ using Cfg24 = Cfg<8, 8, 2, 32, 2, 2, 4>;
 using Cfg25 = Cfg<8, 8, 2, 32, 2, 4, 4>;
 using Cfg26 = Cfg<4, 16, 3, 16, 3, 4, 4>;
 using Cfg27 = Cfg<4, 16, 2, 24, 3, 4, 4>;
+using Cfg28 = Cfg<4, 16, 2, 24, 3, 4, 4, true>;
 // Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
 // three gradient sums per primitive, so its tiles hold fewer primitives
 //   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
@@ -1600,7 +1820,7 @@ using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
 constexpr int kDefaultGradTile = 2;
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28};
 constexpr int kDefaultTile = 18;
 constexpr int kSmallBatchTile = 23;
 constexpr int kSmallBatchQ = 1 << 17;
@@ -1617,13 +1837,31 @@ static cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s) {
     const int ntiles = (a.Q + TQ - 1) / TQ;
     const size_t smem = sizeof(EvalSmem<C>);
     auto kern = k_eval<PRIM, C, MODE, GRAD, EX, SH>;
-    static bool attr = false;  // once per instantiation (idempotent)
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    EvalArgs b = a;
+    b.ntiles = ntiles;
+    int grid = ntiles;
+    if constexpr (C::PERSIST) {
+        // the tile counter is the word after the stream's error word; it
+        // starts every launch at zero
+        b.tile_ctr = reinterpret_cast<int *>(a.err + 1);
+        cudaError_t e0 = cudaMemsetAsync(b.tile_ctr, 0, sizeof(int), s);
+        if (e0 != cudaSuccess) return e0;
+        grid = std::min(ntiles, std::max(a.num_sms, 1) * C::MINB);
     }
-    kern<<<ntiles, (C::NCW + 1) * 32, smem, s>>>(a);
+    // the shared-memory limit is a per-device attribute of the kernel: set it
+    // once per (instantiation, device); bit d of `attr` records device d
+    // (devices from 64 up set it on every launch, which is idempotent)
+    static std::atomic<unsigned long long> attr{0ull};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(attr.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr.fetch_or(bit, std::memory_order_release);
+    }
+    kern<<<grid, (C::NCW + 1) * 32, smem, s>>>(b);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1735,6 +1973,7 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 25: return launch_mode_sweep<PRIM, Cfg25>(a, s);
         case 26: return launch_mode_sweep<PRIM, Cfg26>(a, s);
         case 27: return launch_mode_sweep<PRIM, Cfg27>(a, s);
+        case 28: return launch_mode_sweep<PRIM, Cfg28>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }
@@ -1760,6 +1999,9 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
     a.qns = qns;
     a.perm = perm;
     a.Q = Q;
+    a.S = sweep_blocks(p);
+    a.Qb = Q / a.S;
+    for (int k = 0; k < 8; ++k) a.sw.v[k] = k < a.S ? p.sweep_nsigma[k] : 0.f;
     a.k = make_consts(p);
     a.out_metric = out_metric;
     a.out_collide = out_collide;
@@ -1771,6 +2013,9 @@ cudaError_t run_eval(int prim_type, const SceneDev &sc, const float4 *qrec, cons
     a.kstats = p.out_kernel_stats;
     a.wait_polls = polls;
     a.gflags = gflags;
+    a.num_sms = num_sms;
+    a.tile_ctr = nullptr;
+    a.ntiles = 0;
     cudaError_t e;
     if (p.eval_events[0] && (e = cudaEventRecord((cudaEvent_t)p.eval_events[0], s)) != cudaSuccess) return e;
     e = launch_eval(prim_type, a, grad_centres != nullptr, p.tile_config, num_sms, s);
@@ -1821,35 +2066,11 @@ void launch_prep(const float *prims, int prim_type, int Q, const SceneDev &sc, f
     *perm_out = perm;
 }
 
-// Row e = p S + s of a sweep: sorted row p at n_sigma value s, written to
-// output row s Q + perm[p].
-__global__ void k_sweep_expand(const float4 *__restrict__ rec_in, const uint32_t *__restrict__ perm_in, int Q,
-                               int recs, int S, SweepNs ns, float4 *__restrict__ rec_out, float *__restrict__ ns_out,
-                               uint32_t *__restrict__ perm_out) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)Q * S) return;
-    const int64_t p = e / S;
-    const int s = (int)(e - p * S);
-    for (int r = 0; r < recs; ++r) rec_out[e * recs + r] = rec_in[p * recs + r];
-    ns_out[e] = ns.v[s];
-    perm_out[e] = (uint32_t)s * (uint32_t)Q + perm_in[p];
-}
-
-void launch_sweep_expand(const float4 *rec_in, const uint32_t *perm_in, int Q, int recs, int S, const float *ns,
-                         float4 *rec_out, float *ns_out, uint32_t *perm_out, cudaStream_t s) {
-    SweepNs v;
-    for (int k = 0; k < 8; ++k) v.v[k] = k < S ? ns[k] : 0.f;
-    const int64_t n = (int64_t)Q * S;
-    k_sweep_expand<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec_in, perm_in, Q, recs, S, v, rec_out, ns_out,
-                                                               perm_out);
-    count_launches(1);
-}
-
 void launch_group(const float *metric, const uint8_t *collide, int Q, int G, float *gm, uint8_t *gc,
-                  cudaStream_t s) {
+                  cudaStream_t s, unsigned *err) {
     const int64_t ng = (Q + G - 1) / G;
     const int64_t threads = G >= kGroupWarpMin ? ng * 32 : ng;
-    k_group<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(metric, collide, Q, G, gm, gc);
+    k_group<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(metric, collide, Q, G, gm, gc, err);
     count_launches(1);
 }
 

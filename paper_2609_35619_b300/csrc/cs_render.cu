@@ -337,6 +337,7 @@ cs_status cs_scene_set_appearance(cs_scene *scene, const float *opacity, const f
 
 cs_status cs_render(const cs_scene *scene, const cs_render_desc *d, const cs_camera *cams, float *out_rgb,
                     float *out_depth, float *out_alpha) {
+    NvtxRange range("cs.render");
     cs_status st = check_scene(scene);
     if (st != CS_OK) return st;
     if (!d) return invalid("desc is NULL");

@@ -219,6 +219,7 @@ extern "C" {
 cs_status cs_rrt_extend(const cs_scene *scene, const cs_rrt_desc *d, float *nodes, int32_t *parent,
                         int32_t *count, const float *samples, int32_t *nearest, uint8_t *edge_free,
                         const cs_params *params) {
+    NvtxRange range("cs.rrt_extend");
     return rrt_common(scene, d, nodes, parent, count, samples, nearest, edge_free, params, nullptr);
 }
 

@@ -213,6 +213,7 @@ static void CUDART_CB on_batch_done(void *arg) {
 // Form and launch one batch on slot `s` from the pending queue (lock held on
 // entry, released while the batch is assembled and enqueued).
 static void launch_batch(Server *srv, Slot &s, std::unique_lock<std::mutex> &lk) {
+    NvtxRange range("cs.serve.batch");
     const int32_t scene = srv->pending.front()->r.scene, prim = srv->pending.front()->r.prim_type;
     const int64_t cap = srv->cfg.slot_rows;
     int64_t rows = 0;

@@ -10,7 +10,7 @@ import pytest
 
 import cs_synth as S
 import oracle
-from _parity import compare, to_np
+from _parity import compare, compare_groups, cutoff_interval, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def test_tiny_scene_all_modes(cs, nsigma, mode):
     assert rep["checked"] > 0.9 * rep["Q"]
 
 
-@pytest.mark.parametrize("cfg", list(range(1, 24)))
+@pytest.mark.parametrize("cfg", list(range(1, 29)))
 @pytest.mark.parametrize("Q", [1, 37, 1000, 5000])
 def test_tile_configs_and_ragged_batches(cs, cfg, Q):
     """Every tile shape, batch sizes spanning one to many tiles with a ragged tail."""
@@ -93,9 +93,13 @@ def test_ellipsoids(cs, mode, axes):
     band = max(1e-5, 24 * 2.0 ** -24 * kappa.max() * max(cond.max(), 4.0))
     orc = oracle.query(sc, e, 1, 1.0, oracle.Params(band=band))
     scene = _scene(cs, sc)
+    # thin ellipsoids against 2 cm Gaussians cancel strongly in Eq. 8, and the
+    # widened band puts more pairs near s_min under cond_cost: 66 of the 600
+    # rows (11 %) take the widened bound with semi-axes from 8 mm
+    cap = 0.05 if axes[0] >= 0.03 else 0.15
     for cfg in (1, 2, 3, 4, 18, 23):
         out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode, tile_config=cfg)
-        rep = compare(out, orc, mode, oracle.Params(), f"ellipsoid mode={mode}", kappa=kappa)
+        rep = compare(out, orc, mode, oracle.Params(), f"ellipsoid mode={mode}", kappa=kappa, max_cancel=cap)
         assert rep["checked"] > 0.5 * rep["Q"], rep
 
 
@@ -132,22 +136,30 @@ def test_negative_s_min(cs, s_min):
 
 
 def test_group_outputs(cs):
+    """Section II-D group sums and Section II-E group flags against the
+    oracle's rows, with the bound derived in compare_groups: the rows' own
+    parity bounds plus the rounding of the FP32 group sum (warp sums for
+    G >= 32, in-order sums below), rows in the cutoff band taking the
+    oracle's range over the band's memberships."""
     sc = S.tiny_scene()
     q = S.tiny_queries(q=1000)
     scene = _scene(cs, sc)
-    for G in (32, 64, 7):
+    P = oracle.Params()
+    orc = oracle.query(sc, q, 0, 1.0, P)
+    band = np.flatnonzero(orc["band_cut"] > 0)
+    lo, hi = cutoff_interval(sc, q, 0, 1.0, P, band, oracle.MODE_MEAN)
+    for G in (32, 64, 7, 1000):
         params = cs.QueryParams(group_size=G)
-        out = to_np(scene.query(torch.as_tensor(q), 1.0, params=params))
-        orc = oracle.query(sc, q, 0, 1.0)
-        gm, gc = oracle.group_reduce(orc["mean_cost"], orc["collide"], G)
-        assert out["group_metric"].shape == gm.shape
-        np.testing.assert_allclose(out["group_metric"], gm, rtol=2e-5, atol=1e-30)
-        band = np.add.reduceat(orc["band_in"], np.arange(0, q.shape[0], G)) > 0
-        assert (out["group_collide"][~band] == gc[~band]).all()
-        # the per-row sums reproduce the group sums
-        per_row = out["metric"].astype(np.float64)
-        np.testing.assert_allclose(np.add.reduceat(per_row, np.arange(0, q.shape[0], G)),
-                                   out["group_metric"], rtol=1e-5)
+        out = to_np(scene.query(torch.as_tensor(q), 1.0, params=params, want_count=True))
+        assert out["group_metric"].shape == ((q.shape[0] + G - 1) // G,)
+        rep = compare(out, orc, 0, P, f"groups G={G} rows")
+        n = compare_groups(out["group_metric"], out["group_collide"], out["metric"], orc, rep, G, oracle.MODE_MEAN,
+                           f"groups G={G}", interval=(band, lo, hi))
+        assert n == out["group_metric"].shape[0]
+        # the group flag is the OR of the rows' flags, exactly
+        ng = out["group_collide"].shape[0]
+        rows_or = np.array([out["collide"][k * G:(k + 1) * G].max() for k in range(ng)])
+        np.testing.assert_array_equal(out["group_collide"], rows_or)
 
 
 # --------------------------------------------------------------- edge cases
@@ -480,3 +492,25 @@ def test_sweep_parameter_equals_separate_calls(cs, prim_type, tile, sweep, k_thr
     with pytest.raises(cs.CsError):  # no flags mode for a sweep
         scene.query(torch.as_tensor(q), 0.0, prim_type=prim_type,
                     params=cs.QueryParams(mode=cs.CS_METRIC_FLAGS, sweep=sweep))
+
+
+def test_persistent_shape_equals_its_one_tile_per_cta_shape(cs):
+    """Shape 28 runs shape 27 as a persistent kernel (SMs x 3 CTAs taking
+    tiles from a counter).  On a batch of far more tiles than the grid holds,
+    with a ragged last tile, every output has the bits of shape 27: each row's
+    reductions do not depend on which CTA or in which order its tile ran.
+    Also as a conservatism sweep with groups, and twice in a row on one stream
+    (the tile counter starts every launch at zero)."""
+    sc = _TABLE["scene"]
+    scene = _TABLE.get("gpu") or _scene(cs, sc)
+    _TABLE["gpu"] = scene
+    q = torch.as_tensor(S.edge_queries(edges=600)[:-13].copy())  # 153,587 rows: ~2,400 tiles of 64
+    for params in ({}, {"group_size": 64, "sweep": (0.0, 0.5, 1.0, 2.0)}):
+        ref = to_np(scene.query(q, 1.0, want_count=True, params=cs.QueryParams(tile_config=27, **params)))
+        for rep in range(2):
+            got = to_np(scene.query(q, 1.0, want_count=True, params=cs.QueryParams(tile_config=28, **params)))
+            torch.cuda.synchronize()
+            for k in ref:
+                np.testing.assert_array_equal(got[k].view(np.uint8), ref[k].view(np.uint8), err_msg=f"{k} {params}")
+        assert (ref["count"] > 0).any()
+    scene.sync()
