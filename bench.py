@@ -61,6 +61,8 @@ def parse():
                     help="requests of the serving measurement in the default run")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests-sweep", type=int, default=10_000, help="requests per load in --case serve")
+    ap.add_argument("--serve-eager", action="store_true",
+                    help="--case serve: launch the query path's kernels one by one instead of replaying graphs")
     ap.add_argument("--serve-slots", type=int, default=3, help="server batch slots in --case serve")
     ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
     ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
@@ -567,13 +569,18 @@ def one_query_per_call(cs, torch, scene, n=2000):
     return n / (time.perf_counter() - t0)
 
 
-def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True, slots=3, slot_rows=1 << 19):
+def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True, slots=3, slot_rows=1 << 19,
+               use_graphs=True):
     import cs_synth as S
     scenes_h, scenes, tiles = serve_setup(torch, cs, dev)
     reqs = S.serving_requests(seed=1007, count=n_requests)
     warm = S.serving_requests(seed=1008, count=16, q_lo=16, q_hi=65536)
-    srv = cs.Server(scenes, slots=slots, slot_rows=slot_rows, tile_config=cs.abi.CS_TILE_TUNED)
+    srv = cs.Server(scenes, slots=slots, slot_rows=slot_rows, tile_config=cs.abi.CS_TILE_TUNED,
+                    use_graphs=use_graphs)
     served_burst(cs, srv, warm)
+    if use_graphs:  # capture every (scene, size bucket) graph before timing
+        served_burst(cs, srv, [dict(r, scene=s) for s in range(len(scenes))
+                               for r in S.serving_requests(seed=1009, count=12, q_lo=512, q_hi=1 << 19)])
     cap, cap_s = served_burst(cs, srv, reqs)
     runs = [served_poisson(cs, srv, reqs, f * cap) for f in loads]
     st = srv.stats()
@@ -581,7 +588,7 @@ def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True, sl
     out = {"workload": SERVE_WORKLOAD, "requests": n_requests,
            "rows": int(sum(r["spheres"].shape[0] for r in reqs)),
            "served_capacity_queries_per_s": cap, "loads": [dict(r, load=f) for f, r in zip(loads, runs)],
-           "server": {"slots": slots, "slot_rows": slot_rows, "tiles": tiles,
+           "server": {"slots": slots, "slot_rows": slot_rows, "tiles": tiles, "graphs": bool(use_graphs),
                       "mean_batch_requests": st["requests"] / max(st["batches"], 1),
                       "max_batch_requests": st["max_batch_requests"]}}
     if with_per_call:
@@ -602,7 +609,8 @@ def run_serve_case(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     res = run_served(torch, cs, dev, args.serve_requests_sweep, loads=(0.25, 0.5, 0.75, 0.9),
-                     with_per_call=not args.no_per_call, slots=args.serve_slots, slot_rows=args.serve_rows)
+                     with_per_call=not args.no_per_call, slots=args.serve_slots, slot_rows=args.serve_rows,
+                     use_graphs=not args.serve_eager)
     print(json.dumps({"case": "serve", **res}))
 
 

@@ -496,6 +496,12 @@ typedef struct cs_server_config {
     int32_t tile_config;  /* as cs_params.tile_config (default CS_TILE_TUNED) */
     cs_params params;     /* metric parameters of every request: gamma, d_max, s_min, eps, tau,
                              k_thr, mode (the pointer, stream and group members are ignored) */
+    int32_t use_graphs;   /* 1 (default): a batch of R rows runs the query path as a replay of
+                             a CUDA graph the slot captured for (scene, primitive type, counts
+                             wanted, bucket), bucket = the next power of two >= max(R, 1024)
+                             capped at slot_rows, the rows past R padded with primitives far
+                             outside every scene (they reach nothing and change no result);
+                             0: the query path's kernels are launched one by one */
 } cs_server_config;
 
 /* One request.  Every pointer is a host pointer; `prims` is read when the

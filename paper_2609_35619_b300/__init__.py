@@ -351,12 +351,13 @@ class Server:
     requests, wait() for their results and timeline."""
 
     def __init__(self, scenes, *, slots=3, slot_rows=1 << 19, max_requests=4096, tile_config=abi.CS_TILE_TUNED,
-                 params: QueryParams | None = None):
+                 params: QueryParams | None = None, use_graphs: bool = True):
         params = params or QueryParams()
         self.scenes = list(scenes)
         cfg = abi.cs_server_config()
         check(abi.cs_server_config_init(cfg))
         cfg.slots, cfg.slot_rows, cfg.max_requests, cfg.tile_config = slots, slot_rows, max_requests, tile_config
+        cfg.use_graphs = 1 if use_graphs else 0
         cfg.params = params.to_c()
         self._h = ctypes.c_void_p()
         check(abi.cs_server_create([s.handle for s in self.scenes], len(self.scenes), cfg, self._h))

@@ -92,6 +92,7 @@ class cs_server_config(ctypes.Structure):
         ("max_requests", ctypes.c_int32),
         ("tile_config", ctypes.c_int32),
         ("params", cs_params),
+        ("use_graphs", ctypes.c_int32),
     ]
 
 

@@ -581,9 +581,10 @@ struct Acc {
     float gx[GRAD ? QW : 1], gy[GRAD ? QW : 1], gz[GRAD ? QW : 1];
     int cnt[MODE == 3 ? 1 : QW];
     int cin[(GRAD && PRIM == 1) ? 1 : QW];
-    // sphere cost launches with k_thr = 0: the smallest st2 instead of the
-    // in-collision count (a row collides iff it is below T_in)
-    float mst[(MODE == 0 && !GRAD && PRIM == 0) ? QW : 1];
+    // sphere cost launches with k_thr = 0: bit j is set once a pair of row j
+    // has st2 < T_in (the row collides iff a lane set it), in place of the
+    // in-collision count
+    unsigned fin;
 };
 
 // Lane-local Gaussian of the current chunk slot (f: tr(Sigma^2)/2, set for
@@ -837,7 +838,7 @@ __device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2
     const bool nb0 = s0 <= k.S_cut_u, nb1 = s1 <= k.S_cut_u;
     A.cnt[j] += (nb0 ? 1 : 0) + (nb1 ? 1 : 0);
     if constexpr (K0) {
-        A.mst[j] = fminf(A.mst[j], fminf(s0, s1));
+        A.fin |= (s0 < k.T_in_u || s1 < k.T_in_u) ? (1u << j) : 0u;
     } else {
         A.cin[j] += ((s0 < k.T_in_u) ? 1 : 0) + ((s1 < k.T_in_u) ? 1 : 0);
     }
@@ -1216,13 +1217,14 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     }
 
     Acc<PRIM, QW, MODE, GRAD> A;
+    A.fin = 0u;
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
         if constexpr (MODE != 3) A.cnt[j] = 0;
         constexpr bool FWD = (SH & kShFwd) != 0;
         if (!GRAD || FWD) A.cin[j] = 0;
         if (MODE == 0 && (!GRAD || FWD)) { A.sum[j] = 0.f; if (PRIM == 1) A.sumb[j] = 0.f; }
-        if (PRIM == 0 && MODE == 0 && !GRAD) A.mst[j] = INFINITY;
+
         if (MODE == 1) A.mn[j] = INFINITY;
         if (MODE == 2) { A.sm_m[j] = k.S_cut; A.sm_acc[j] = 0.f; }
         if (GRAD) { A.gx[j] = 0.f; A.gy[j] = 0.f; A.gz[j] = 0.f; }
@@ -1420,7 +1422,7 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if (!GRAD) {
             int cinj;
             if constexpr ((SH & kShK0) && PRIM == 0 && MODE == 0) {
-                cinj = warp_min(A.mst[j]) < k.T_in_u ? 1 : 0;  // k_thr = 0: any pair in collision
+                cinj = __any_sync(0xffffffffu, (A.fin >> j) & 1u) ? 1 : 0;  // k_thr = 0: any pair in collision
             } else {
                 cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
             }

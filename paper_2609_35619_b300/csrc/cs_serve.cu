@@ -110,6 +110,8 @@ struct Slot {
     std::vector<int64_t> row0, grp0;  // first batch row / group output of each request
     int64_t rows = 0;
     bool want_count = false;
+    // captured query graphs by (scene, primitive type, counts, bucket)
+    std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
 };
 
 struct Server {
@@ -132,6 +134,8 @@ struct Server {
 };
 
 static void free_slot(Slot &s) {
+    for (auto &kv : s.graphs) cudaGraphExecDestroy(kv.second);
+    s.graphs.clear();
     void *dev[] = {s.d_prims, s.d_ns, s.d_metric, s.d_gm, s.d_collide, s.d_gc, s.d_count, s.d_segs};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -210,6 +214,72 @@ static void CUDART_CB on_batch_done(void *arg) {
     srv->cv_launch.notify_all();
 }
 
+// Rows of the graph a batch of `rows` rows replays: the next power of two
+// from 1024, at most the slot's rows.
+static int64_t graph_bucket(int64_t rows, int64_t slot_rows) {
+    int64_t b = 1024;
+    while (b < rows) b <<= 1;
+    return std::min(b, slot_rows);
+}
+
+// The query path of a batch as one graph replay.  The batch's rows are
+// already in pinned memory; rows [rows, bucket) are padded with primitives
+// far outside every scene (valid rows whose reach meets no chunk: count 0,
+// metric 0, flag 0), which sort after the real rows and change none of
+// their results.  The padded rows are copied up with the batch; the graph
+// for (scene, primitive type, counts wanted, bucket) is captured on the
+// slot's stream the first time it is needed.
+static cs_status run_graph(Server *srv, Slot &s, int32_t scene, int32_t prim, int64_t rows, const cs_params &p,
+                           cudaError_t &e) {
+    const int64_t bucket = graph_bucket(rows, srv->cfg.slot_rows);
+    const int stride = stride_of(prim);
+    for (int64_t r = rows; r < bucket; ++r) {
+        float *q = s.h_prims + r * stride;
+        q[0] = q[1] = q[2] = 1e30f;
+        if (stride == 4) {
+            q[3] = 1.f;
+        } else {
+            q[3] = 1.f; q[4] = q[5] = q[6] = 0.f;
+            q[7] = q[8] = q[9] = 1.f;
+        }
+        s.h_ns[r] = 0.f;
+    }
+    cudaStream_t st = s.stream;
+    if (bucket > rows) {
+        e = cudaMemcpyAsync(s.d_prims + rows * stride, s.h_prims + rows * stride,
+                            4 * (size_t)stride * (size_t)(bucket - rows), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.d_ns + rows, s.h_ns + rows, 4 * (size_t)(bucket - rows), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return CS_ERR_CUDA;
+    }
+    const uint64_t key = ((uint64_t)scene << 40) | ((uint64_t)prim << 36) | ((uint64_t)(p.out_count != nullptr) << 35) |
+                         (uint64_t)bucket;
+    auto it = s.graphs.find(key);
+    if (it == s.graphs.end()) {
+        // the slot's stream is idle here (the slot was free); capture the query path once
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return CS_ERR_CUDA;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return CS_ERR_CUDA;
+        const cs_status cst = query_common(reinterpret_cast<cs_scene *>(srv->scenes[scene]), prim, s.d_prims, bucket,
+                                           0.f, &p, false, s.d_metric, s.d_collide, nullptr, nullptr, s.ws);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (cst != CS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return cst;
+        }
+        if (e != cudaSuccess) return CS_ERR_CUDA;
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return CS_ERR_CUDA;
+        it = s.graphs.emplace(key, ex).first;
+    }
+    e = cudaGraphLaunch(it->second, st);
+    return e == cudaSuccess ? CS_OK : CS_ERR_CUDA;
+}
+
 // Form and launch one batch on slot `s` from the pending queue (lock held on
 // entry, released while the batch is assembled and enqueued).
 static void launch_batch(Server *srv, Slot &s, std::unique_lock<std::mutex> &lk) {
@@ -283,9 +353,12 @@ static void launch_batch(Server *srv, Slot &s, std::unique_lock<std::mutex> &lk)
     if (ok()) e = cudaMemcpyAsync(s.d_prims, s.h_prims, 4 * (size_t)stride * (size_t)rows, cudaMemcpyHostToDevice, st);
     if (ok()) e = cudaMemcpyAsync(s.d_ns, s.h_ns, 4 * (size_t)rows, cudaMemcpyHostToDevice, st);
     if (ok() && nseg > 0) e = cudaMemcpyAsync(s.d_segs, s.h_segs, sizeof(GroupSeg) * nseg, cudaMemcpyHostToDevice, st);
-    if (ok())
+    if (ok() && srv->cfg.use_graphs) {
+        cst = run_graph(srv, s, scene, prim, rows, p, e);
+    } else if (ok()) {
         cst = query_common(reinterpret_cast<cs_scene *>(srv->scenes[scene]), prim, s.d_prims, rows, 0.f, &p,
                            false, s.d_metric, s.d_collide, nullptr, nullptr, s.ws);
+    }
     if (ok() && nseg > 0) {
         k_group_segments<<<(unsigned)((g0 * 32 + 255) / 256), 256, 0, st>>>(s.d_metric, s.d_collide, s.d_segs,
                                                                            nseg, (int)g0, s.d_gm, s.d_gc);
@@ -373,6 +446,7 @@ cs_status cs_server_config_init(cs_server_config *c) {
     c->slot_rows = 1 << 19;
     c->max_requests = 4096;
     c->tile_config = CS_TILE_TUNED;
+    c->use_graphs = 1;
     return cs_params_init(&c->params);
 }
 

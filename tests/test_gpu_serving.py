@@ -55,10 +55,14 @@ def _requests(n, seed):
     return reqs
 
 
-def test_results_equal_alone_and_in_the_mix(cs, scenes):
+@pytest.mark.parametrize("use_graphs", [True, False])
+def test_results_equal_alone_and_in_the_mix(cs, scenes, use_graphs):
+    """With graph replay (the default: rows padded to the graph's bucket with
+    primitives far outside the scenes) and with the kernels launched one by
+    one."""
     data, sc = scenes
     reqs = _requests(120, 31)
-    srv = cs.Server(sc, slots=2, slot_rows=1 << 17, max_requests=64, tile_config=0)
+    srv = cs.Server(sc, slots=2, slot_rows=1 << 17, max_requests=64, tile_config=0, use_graphs=use_graphs)
     tickets = [None] * len(reqs)
 
     def client(part):
