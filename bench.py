@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--serve-rows", type=int, default=1 << 19, help="rows per server slot in --case serve")
     ap.add_argument("--no-per-call", action="store_true", help="--case serve: skip the per-call baseline")
     ap.add_argument("--case", default="step",
-                    choices=["step", "eval", "serve", "mppi", "rrt", "variants", "render"],
+                    choices=["step", "eval", "serve", "mppi", "rrt", "variants", "render", "build"],
                     help="eval: the profiling case -- build the tabletop scene, then one warm-up "
                          "and one measured query of the 262,144 arm spheres at n_sigma=1 "
                          "(two fused-kernel launches); prints a short JSON summary. "
@@ -602,6 +602,35 @@ def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True, sl
     return out
 
 
+def run_build_case(args, reps=10):
+    """The scene build alone (cs_scene_create from device arrays: Eq. 2
+    repack, floater filter, Morton order, chunks, tree) on the 1M tabletop,
+    `reps` times after two warm-up builds; CUDA events on the build's stream
+    (the call returns with the scene complete)."""
+    import torch
+
+    import cs_synth as S
+    import paper_2609_35619_b300 as cs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sc = S.tabletop_scene()
+    d = {k: torch.as_tensor(v, device=dev) for k, v in sc.items()}
+    stream = torch.cuda.Stream(dev)
+    ms = []
+    for r in range(reps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        scene = cs.Scene(d["means"], d["scales"], d["quats"], d["opacity"], device=dev, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if r >= 2:
+            ms.append(e0.elapsed_time(e1))
+        scene.close()
+    n = sc["means"].shape[0]
+    print(json.dumps({"case": "build", "gaussians": n, "ms_mean": float(np.mean(ms)), "ms_min": float(np.min(ms)),
+                      "algorithmic_gbs": n * 84 / (np.min(ms) * 1e-3) / 1e9}))
+
+
 def run_serve_case(args):
     import torch
 
@@ -1002,6 +1031,8 @@ def main():
     if args.case == "eval":
         run_eval_case(args)
         return
+    if args.case == "build":
+        return run_build_case(args)
     if args.case == "serve":
         run_serve_case(args)
         return

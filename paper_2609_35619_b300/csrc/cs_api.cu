@@ -82,6 +82,39 @@ Workspace *find_workspace(int device, cudaStream_t stream) {
     return it == g_ws.end() ? nullptr : it->second;
 }
 
+static std::mutex g_pool_mu;
+static std::unordered_map<int, cudaMemPool_t> g_pools;
+
+cudaError_t temp_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it == g_pools.end()) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = 1ull << 30;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        it = g_pools.emplace(dev, pool).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
+}
+
+static void trim_temp_pools() {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto &kv : g_pools) cudaMemPoolTrimTo(kv.second, 0);
+}
+
 cs_status new_workspace(cudaStream_t stream, Workspace **out) {
     Workspace *w = new Workspace();
     w->stream = stream;
@@ -529,9 +562,12 @@ cs_status cs_selftest_wait_timeout(int64_t spins, void *stream) {
 }
 
 cs_status cs_release_scratch(void) {
-    std::lock_guard<std::mutex> lk(g_ws_mu);
-    for (auto &kv : g_ws) free_ws(kv.second);
-    g_ws.clear();
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        for (auto &kv : g_ws) free_ws(kv.second);
+        g_ws.clear();
+    }
+    trim_temp_pools();
     return CS_OK;
 }
 

@@ -315,12 +315,24 @@ __global__ void k_node_level(const NodeBox *__restrict__ child, int nchild, Node
     if (lane == 0) node[k] = NodeBox{make_float4(lx, ly, lz, sg), make_float4(hx, hy, hz, 0.f)};
 }
 
+// A temporary of the build, allocated from the library's stream-ordered pool
+// on the build's stream and returned to it in stream order (no cudaFree, so
+// no device-wide synchronisation per temporary).
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    cudaStream_t s = nullptr;
+    ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+cudaError_t temp_alloc(DevBuf &b, cudaStream_t s, size_t bytes) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = temp_pool(&pool);
+    if (e != cudaSuccess) return e;
+    b.s = s;
+    return cudaMallocFromPoolAsync(&b.p, bytes, pool, s);
+}
 
 }  // namespace
 
@@ -331,9 +343,9 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
         d_stats;
     const float *means = d->means, *scales = d->scales, *quats = d->quats, *op = d->opacity;
     if (n > 0 && !d->on_device) {
-        CS_CUDA(cudaMalloc(&in_means.p, 12 * n));
-        CS_CUDA(cudaMalloc(&in_scales.p, 12 * n));
-        CS_CUDA(cudaMalloc(&in_quats.p, 16 * n));
+        CS_CUDA(temp_alloc(in_means, s, 12 * n));
+        CS_CUDA(temp_alloc(in_scales, s, 12 * n));
+        CS_CUDA(temp_alloc(in_quats, s, 16 * n));
         CS_CUDA(cudaMemcpyAsync(in_means.p, d->means, 12 * n, cudaMemcpyHostToDevice, s));
         CS_CUDA(cudaMemcpyAsync(in_scales.p, d->scales, 12 * n, cudaMemcpyHostToDevice, s));
         CS_CUDA(cudaMemcpyAsync(in_quats.p, d->quats, 16 * n, cudaMemcpyHostToDevice, s));
@@ -341,16 +353,16 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
         scales = (const float *)in_scales.p;
         quats = (const float *)in_quats.p;
         if (op) {
-            CS_CUDA(cudaMalloc(&in_op.p, 4 * n));
+            CS_CUDA(temp_alloc(in_op, s, 4 * n));
             CS_CUDA(cudaMemcpyAsync(in_op.p, d->opacity, 4 * n, cudaMemcpyHostToDevice, s));
             op = (const float *)in_op.p;
         }
     }
     const int64_t nn = n > 0 ? n : 1;
-    CS_CUDA(cudaMalloc(&tmp_rec.p, 48 * nn));
-    CS_CUDA(cudaMalloc(&tmp_code.p, nn));
-    CS_CUDA(cudaMalloc(&tmp_kv.p, 16 * nn));
-    CS_CUDA(cudaMalloc(&d_stats.p, sizeof(BuildStats)));
+    CS_CUDA(temp_alloc(tmp_rec, s, 48 * nn));
+    CS_CUDA(temp_alloc(tmp_code, s, nn));
+    CS_CUDA(temp_alloc(tmp_kv, s, 16 * nn));
+    CS_CUDA(temp_alloc(d_stats, s, sizeof(BuildStats)));
     float4 *upos = (float4 *)tmp_rec.p, *ucovA = upos + nn, *ucovB = ucovA + nn;
     uint8_t *code = (uint8_t *)tmp_code.p;
     BuildStats hs;
@@ -418,8 +430,8 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     size_t hist_n = sort_hist_elems((size_t)nn);
     const int64_t nseg_max = 2 + (nn + kSegment - 1) / kSegment;
     size_t scan_n = scan_tmp_elems(std::max(hist_n, (size_t)nseg_max + 1));
-    CS_CUDA(cudaMalloc(&tmp_hist.p, 4 * std::max(hist_n, (size_t)nseg_max + 1)));
-    CS_CUDA(cudaMalloc(&tmp_scan.p, 4 * scan_n));
+    CS_CUDA(temp_alloc(tmp_hist, s, 4 * std::max(hist_n, (size_t)nseg_max + 1)));
+    CS_CUDA(temp_alloc(tmp_scan, s, 4 * scan_n));
     int res = 0;
     if (n > 0) {
         k_keys<<<blocks_for(n), kThreads, 0, s>>>(upos, code, n, g, keys[0], vals[0], st);
@@ -441,10 +453,10 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     const int seg_main = (int)((n_main + kSegment - 1) / kSegment);
     const int nseg = seg_main + (int)((n_kept - n_main + kSegment - 1) / kSegment);
     DevBuf tmp_spos, tmp_cnt, tmp_base, tmp_slot;
-    CS_CUDA(cudaMalloc(&tmp_spos.p, 16 * (size_t)std::max<int64_t>(n_kept, 1)));
-    CS_CUDA(cudaMalloc(&tmp_cnt.p, 4 * ((size_t)nseg + 1)));
-    CS_CUDA(cudaMalloc(&tmp_base.p, 4 * ((size_t)nseg + 1)));
-    CS_CUDA(cudaMalloc(&tmp_slot.p, 4 * (size_t)std::max<int64_t>(n_kept, 1)));
+    CS_CUDA(temp_alloc(tmp_spos, s, 16 * (size_t)std::max<int64_t>(n_kept, 1)));
+    CS_CUDA(temp_alloc(tmp_cnt, s, 4 * ((size_t)nseg + 1)));
+    CS_CUDA(temp_alloc(tmp_base, s, 4 * ((size_t)nseg + 1)));
+    CS_CUDA(temp_alloc(tmp_slot, s, 4 * (size_t)std::max<int64_t>(n_kept, 1)));
     float4 *spos = (float4 *)tmp_spos.p;
     uint32_t *seg_cnt = (uint32_t *)tmp_cnt.p, *seg_base = (uint32_t *)tmp_base.p, *slot = (uint32_t *)tmp_slot.p;
     const float ext_main = h, ext_large = 4.f * h;
@@ -514,7 +526,7 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
     int32_t *slot_of = (int32_t *)(base + off_slot);
     if (nchunks > 0) {
         DevBuf tmp_ss;
-        CS_CUDA(cudaMalloc(&tmp_ss.p, 4 * (size_t)nchunks * kChunk));
+        CS_CUDA(temp_alloc(tmp_ss, s, 4 * (size_t)nchunks * kChunk));
         float *slot_smax = (float *)tmp_ss.p;
         k_fill_padding<<<(unsigned)(((int64_t)nchunks * kChunk + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             blocks, nchunks, slot_smax);
@@ -534,10 +546,9 @@ cs_status build_scene(const cs_scene_desc *d, cudaStream_t s, Scene *sc) {
             nchild = nnodes[l];
         }
         CS_CUDA(cudaGetLastError());
-        CS_CUDA(cudaStreamSynchronize(s));  // before the temporaries are freed
     }
     CS_CUDA(cudaGetLastError());
-    CS_CUDA(cudaStreamSynchronize(s));
+    CS_CUDA(cudaStreamSynchronize(s));  // the scene is complete when cs_scene_create returns
     if (kDebugBuild) {
         unsigned dbg = 0;
         CS_CUDA(cudaMemcpy(&dbg, &st->dbg_err, sizeof(dbg), cudaMemcpyDeviceToHost));

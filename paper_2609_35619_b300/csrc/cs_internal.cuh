@@ -223,6 +223,11 @@ inline int sweep_blocks(const cs_params &p) { return p.sweep_count >= 2 ? p.swee
 struct SweepNs {
     float v[8];
 };
+// The library's stream-ordered memory pool of the current device, for
+// temporaries that live within one call (the scene build): allocations and
+// frees are enqueued on the caller's stream and never synchronise the
+// device; up to 1 GB stays reserved between calls (cs_release_scratch trims).
+cudaError_t temp_pool(cudaMemPool_t *out);
 // Scratch of a sweep over Q rows: per-row outputs of S Q rows (group-only
 // requests); the Q rows themselves are prepared once and copied in the kernel.
 cs_status sweep_reserve(Workspace *w, int64_t Q, int prim_type, int S);
