@@ -915,11 +915,18 @@ def oracle_sample(target_s: float, seed: int = 0):
         dt = time.perf_counter() - t0
     useful = int(res["count_nbr"].sum())
     n = scene["means"].shape[0]
+    # the parity checks' exclusions and widened bounds on these rows (the
+    # oracle's diagnostics; the contract in tests/_parity.py): rows in the
+    # cutoff band, in the collision band, and cost rows whose Eq. 8 cancels
+    # strongly enough to take the derived bound instead of 1e-5
+    cut = res["band_cut"] > 0
+    parity = {"rows": rows, "cutoff_band_rows": int(cut.sum()), "collision_band_rows": int((res["band_in"] > 0).sum()),
+              "widened_rows": int(((res["cond_cost"] > 50.0) & ~cut).sum())}
     return {"value": useful / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{rows} rows (half arm, half edge spheres) at n_sigma=1 against all {n} Gaussians; "
                       f"{useful} useful pairs, {rows * n} dense pairs in {dt:.2f} s "
                       f"({rows * n / dt:.3g} dense pairs/s)",
-            "seconds": dt}
+            "parity_sample": parity, "seconds": dt}
 
 
 def run_reference(args, rank, world):
