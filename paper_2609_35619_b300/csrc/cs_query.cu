@@ -190,6 +190,10 @@ struct __align__(16) EvalSmem {
     uint64_t tfull[2];
     uint64_t tempty[2];
     int tile_q[2];
+    // per consumer warp, its kernel counters (cs_params.out_kernel_stats), kept
+    // here rather than in registers: stages, slots tested, slots passing the
+    // warp test, polls, wait cycles, first-stage wait, start clock
+    unsigned long long wst[C::NCW][7];
 };
 
 template <int PRIM> struct PrimTraits;
@@ -881,8 +885,13 @@ __device__ __forceinline__ void pair_update_g2_grad(Acc<0, QW, 0, true> &A, int 
     upk2(fma2(nns2, sq, s2), r0, r1);  // Eq. 8 before the clamp
     const f32x2 st = mul2(pk2(fmaxf(r0, 0.f), fmaxf(r1, 0.f)), pb.y);
     float e0, e1, s0, s1;
-    upk2(fma2(st, pk2(-k.G, -k.G), pk2(k.Gsmin, k.Gsmin)), e0, e1);
     upk2(st, s0, s1);
+    // No lane holds a neighbour of this row (st2 <= S_cut) among its two
+    // Gaussians: every term below adds exactly nothing (weight 0 times a
+    // finite gradient term, no count, no in-collision pair since T_in <=
+    // S_cut), so the warp skips them; the outputs keep their bits.
+    if (!__any_sync(0xffffffffu, s0 <= k.S_cut || s1 <= k.S_cut)) return;
+    upk2(fma2(st, pk2(-k.G, -k.G), pk2(k.Gsmin, k.Gsmin)), e0, e1);
     const float dc0 = ex2_approx(fminf(e0, 0.f)), dc1 = ex2_approx(fminf(e1, 0.f));
     const bool nb0 = s0 <= k.S_cut, nb1 = s1 <= k.S_cut;
     A.cnt[j] += (nb0 ? 1 : 0) + (nb1 ? 1 : 0);
@@ -1230,9 +1239,12 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if (GRAD) { A.gx[j] = 0.f; A.gy[j] = 0.f; A.gz[j] = 0.f; }
     }
     unsigned cand = 0, c_hits = 0;  // (primitive, Gaussian) pairs and (primitive, chunk) hits evaluated
-    unsigned long long c_stages = 0, c_tested = 0, c_pass = 0, c_polls = 0;
-    unsigned long long c_wait = 0, c_first = 0;
-    const long long c_start = clock64();
+    unsigned long long *wst = sm->wst[warp];
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) wst[i] = 0ull;
+        wst[6] = (unsigned long long)clock64();
+    }
     int group = -1;               // chunk group of the cost partials
     bool ok = !abort;
     for (int kk = kkp ? *kkp : 0; ok; ++kk) {
@@ -1242,10 +1254,10 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             const long long c0 = clock64();
             const long long w = wait_phase(&sm->full[s], (unsigned)((kk / C::NS) & 1), a.wait_polls);
             const long long c1 = clock64();
-            c_wait += (unsigned long long)(c1 - c0);
-            if (kk == 0) c_first = (unsigned long long)(c1 - c_start);
+            wst[4] += (unsigned long long)(c1 - c0);
+            if (kk == 0) wst[5] = (unsigned long long)c1 - wst[6];
             got = w >= 0;
-            c_polls += got ? (unsigned long long)w : 0ull;
+            wst[3] += got ? (unsigned long long)w : 0ull;
         }
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) { ok = false; break; }
@@ -1258,8 +1270,10 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             }
             break;
         }
-        ++c_stages;
-        c_tested += (unsigned long long)nslots;
+        if (lane == 0) {
+            wst[0] += 1ull;
+            wst[1] += (unsigned long long)nslots;
+        }
         if constexpr (MODE == 3) {
             // settle primitives whose in-count already exceeds k_thr (their
             // flag cannot change) or whose group already collides
@@ -1301,7 +1315,7 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
             }
             unsigned pmask = __ballot_sync(0xffffffffu, wpass);
-            c_pass += (unsigned long long)__popc(pmask);
+            if (lane == 0) wst[2] += (unsigned long long)__popc(pmask);
             // then (primitive, chunk) tests, 32 / QW chunks per round (lane l:
             // primitive l % QW, chunk l / QW of the round); myq of lane t
             // collects slot t's mask of the primitives that reach it
@@ -1401,7 +1415,7 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         if (lane == 0) mbar_arrive(&sm->empty[s]);
     }
     if (!ok && !abort && lane == 0) atomicOr(a.err, kErrTimeout);
-    const long long c_loop_end = clock64();
+    const unsigned long long c_loop_end = (unsigned long long)clock64();
 
     // ---- reductions across lanes (fixed trees) and outputs
     unsigned long long nb_total = 0;
@@ -1504,16 +1518,16 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         atomicAdd(a.stats + 1, nb_total);
     }
     if (a.kstats && lane == 0) {
-        atomicAdd(a.kstats + 0, c_stages);
-        atomicAdd(a.kstats + 1, c_tested);
-        atomicAdd(a.kstats + 2, c_pass);
+        atomicAdd(a.kstats + 0, wst[0]);
+        atomicAdd(a.kstats + 1, wst[1]);
+        atomicAdd(a.kstats + 2, wst[2]);
         atomicAdd(a.kstats + 3, (unsigned long long)c_hits);
-        atomicAdd(a.kstats + 6, c_polls);
-        const long long c_end = clock64();
-        atomicAdd(a.kstats + 8, (unsigned long long)(c_end - c_start));
-        atomicAdd(a.kstats + 9, c_wait);
-        atomicAdd(a.kstats + 12, c_first);
-        atomicAdd(a.kstats + 14, (unsigned long long)(c_end - c_loop_end));
+        atomicAdd(a.kstats + 6, wst[3]);
+        const unsigned long long c_end = (unsigned long long)clock64();
+        atomicAdd(a.kstats + 8, c_end - wst[6]);
+        atomicAdd(a.kstats + 9, wst[4]);
+        atomicAdd(a.kstats + 12, wst[5]);
+        atomicAdd(a.kstats + 14, c_end - c_loop_end);
     }
     return ok;
 }
