@@ -166,6 +166,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     scene_h, arm_h, edge_h, poses_h, offs_h, radius = make_inputs()
+    torch.cuda.synchronize(dev)
+    free_start, _ = torch.cuda.mem_get_info(dev)  # before any of the job's device memory
     with torch.cuda.stream(stream):
         d_scene = {k: torch.as_tensor(v, device=dev) for k, v in scene_h.items()}
         d_arm = torch.as_tensor(arm_h, device=dev)
@@ -256,6 +258,8 @@ def run_ours(args, rank, world):
     build_ms = []
     eval_ms = []  # per forward-sphere launch of the tabletop sweep
     l0 = cs.abi.cs_launch_count()
+    free_min = torch.cuda.mem_get_info(dev)[0]
+    scene_bytes = 0
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
@@ -269,6 +273,8 @@ def run_ours(args, rank, world):
         s, _ = step(events=evs, build_ev=bev)
         t1.record(stream)
         torch.cuda.synchronize(dev)
+        scene_bytes = s.info()["device_bytes"]
+        free_min = min(free_min, torch.cuda.mem_get_info(dev)[0])
         s.close()
         total_ms += t0.elapsed_time(t1)
         build_ms.append(bev[0].elapsed_time(bev[1]))
@@ -338,6 +344,10 @@ def run_ours(args, rank, world):
                    "grid": {"dims": info["dims"], "cell_size": info["cell_size"],
                             "n_large": info["n_large"]}},
         "queries_per_s": qps, "roofline": roofline, "build": build, "tiles": tiles, "e2e": e2e, "clocks": clk,
+        "vram": {"scene_bytes": int(scene_bytes), "job_device_bytes": int(free_start - free_min),
+                 "note": "scene = the resident 1M-Gaussian scene (chunk blocks, tree, export arrays); job = device "
+                         "memory in use at the end of a timed step minus that before the job's first allocation "
+                         "(inputs, outputs, 256 MB L2 flush buffer, scene, the library's query scratch)"},
         "gpu_launches": int(launches // args.steps) if args.steps else 0,
         "gpu_launches_total": int(launches), "served": None,
     }

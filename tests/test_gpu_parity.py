@@ -97,7 +97,7 @@ def test_ellipsoids(cs, mode, axes):
     # widened band puts more pairs near s_min under cond_cost: 66 of the 600
     # rows (11 %) take the widened bound with semi-axes from 8 mm
     cap = 0.05 if axes[0] >= 0.03 else 0.15
-    for cfg in (1, 2, 3, 4, 18, 23):
+    for cfg in (1, 2, 3, 4, 18, 23, 27, 28):
         out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode, tile_config=cfg)
         rep = compare(out, orc, mode, oracle.Params(), f"ellipsoid mode={mode}", kappa=kappa, max_cancel=cap)
         assert rep["checked"] > 0.5 * rep["Q"], rep
