@@ -67,7 +67,8 @@ typedef enum cs_status {
     CS_ERR_BAD_HANDLE = -5,  /* NULL or destroyed scene handle */
     CS_ERR_UNSUPPORTED = -6, /* valid request the library does not implement */
     CS_ERR_BOUNDS = -7       /* a device-side index check failed (builds compiled with
-                                CS_DEBUG only; the access was skipped, no trap) */
+                                CS_DEBUG only): the access was skipped or redirected to an
+                                in-range element, no trap; the call's outputs are not valid */
 } cs_status;
 
 typedef enum cs_prim_type {

@@ -527,7 +527,8 @@ cs_status cs_sync(const cs_scene *s, void *stream) {
         return CS_ERR_TIMEOUT;
     }
     if (e & kErrBounds) {
-        g_err = "a device-side index check failed (CS_DEBUG build); the access was skipped";
+        g_err = "a device-side index check failed (CS_DEBUG build); the access was kept in bounds and the outputs "
+                "are not valid";
         return CS_ERR_BOUNDS;
     }
     if (e & kErrInvalidQuery) {

@@ -42,9 +42,10 @@ constexpr unsigned kErrBounds = 4u;    // an index check of a CS_DEBUG build fai
 
 // CS_IDX_OK(cond, err): in a CS_DEBUG build, evaluates the index condition
 // `cond`; when it is false, records kErrBounds in the error word `err` and
-// yields false so that the caller skips the access (no trap: the context
-// stays usable and cs_sync reports CS_ERR_BOUNDS).  In a normal build it is
-// `true` and the condition is not evaluated.
+// yields false, and the caller keeps the access in bounds: it skips it, or
+// redirects it to element 0 (no trap: the context stays usable, cs_sync
+// reports CS_ERR_BOUNDS, and that call's outputs are not valid).  In a
+// normal build it is `true` and the condition is not evaluated.
 #ifdef CS_DEBUG
 #define CS_IDX_OK(cond, err) ((cond) ? true : (atomicOr((err), ::cs::kErrBounds), false))
 constexpr bool kDebugBuild = true;
