@@ -35,6 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NSIGMAS = (0.0, 0.5, 1.0, 2.0)
+# the counters of cs_params.out_kernel_stats, in order
+KSTAT_NAMES = ["stages", "chunks_tested", "chunks_pass_warp", "hits", "chunks_staged", "stages_filled",
+               "consumer_polls", "producer_polls", "consumer_cycles", "consumer_wait_cycles",
+               "producer_cycles", "producer_wait_cycles", "consumer_first_cycles", "producer_first_cycles",
+               "consumer_tail_cycles", "tiles"]
 OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes)
 # DRAM bytes (read + write) per forward launch of the fused kernel: the mean of
 # the step's two sweep launches from the ncu captures summarised under
@@ -1006,7 +1011,8 @@ def run_eval_case(args):
         print(json.dumps({"case": "eval", "sweep": True, "batch": args.batch, "tile": args.tile,
                           "queries": 4 * Q, "one_launch_ms": ev1[0].elapsed_time(ev1[1]),
                           "four_launches_ms": sep_ms, "bitwise_equal": bool(same),
-                          "consumer_wait_frac": ks[9] / max(ks[8], 1), "producer_wait_frac": ks[11] / max(ks[10], 1)}))
+                          "consumer_wait_frac": ks[9] / max(ks[8], 1), "producer_wait_frac": ks[11] / max(ks[10], 1),
+                          "kernel_stats": dict(zip(KSTAT_NAMES, ks))}))
         return
     if args.grad:
         up = torch.ones(arm.shape[0] // G + (arm.shape[0] % G > 0), device=dev)
@@ -1033,10 +1039,7 @@ def run_eval_case(args):
     torch.cuda.synchronize()
     scene.sync()
     cand, useful = stats.cpu().tolist()
-    names = ["stages", "chunks_tested", "chunks_pass_warp", "hits", "chunks_staged", "stages_filled",
-             "consumer_polls", "producer_polls", "consumer_cycles", "consumer_wait_cycles",
-             "producer_cycles", "producer_wait_cycles", "consumer_first_cycles", "producer_first_cycles",
-             "consumer_tail_cycles", "tiles"]
+    names = KSTAT_NAMES
     print(json.dumps({"case": "eval", "batch": args.batch, "tile": args.tile, "nsigma": ns,
                       "exact": args.exact, "flags": args.flags, "queries": arm.shape[0], "useful_pairs": useful,
                       "candidate_pairs": cand, "eval_ms": ms,

@@ -217,6 +217,25 @@ CS_API cs_status cs_scene_info_get(const cs_scene *scene, cs_scene_info *info);
 CS_API cs_status cs_scene_export(const cs_scene *scene, float *pos, float *cov, int32_t *index,
                           void *stream);
 
+/* Checkpoint of a built scene (resume without a rebuild).  cs_scene_save
+ * writes the scene -- its counts and layout parameters, its one device
+ * allocation byte for byte (chunk blocks, chunk tree, export arrays) and the
+ * appearance of cs_scene_set_appearance when set -- to the host file `path`
+ * (created or truncated), copying on `stream` and synchronising it.  The
+ * scene must live on the current device.  Tile shapes chosen by cs_autotune
+ * are not saved.  The file is in this library's format (host byte order,
+ * format version 1), not portable across byte orders.
+ * cs_scene_load reads such a file into a new scene on the current device
+ * (*out, owned by the caller until cs_scene_destroy), uploading on `stream`
+ * and synchronising it.  A loaded scene answers every query exactly as the
+ * saved one did (same layout, same bits).  Errors: CS_ERR_INVALID_ARG for an
+ * empty path, a file that cannot be opened, read or written, a wrong magic or
+ * format version, a truncated file or a layout that is not self-consistent
+ * (region bounds, tree level sizes, slot indices out of range);
+ * CS_ERR_NO_MEMORY when the device allocation fails.  *out is NULL on error. */
+CS_API cs_status cs_scene_save(const cs_scene *scene, const char *path, void *stream);
+CS_API cs_status cs_scene_load(const char *path, void *stream, cs_scene **out);
+
 /* The metric for Q primitives (rows of `prims`, layout per cs_prim_type)
  * against the scene, with conservatism n_sigma = `conservatism` (Eq. 8, >= 0)
  * unless params->nsigma_per_query is given.

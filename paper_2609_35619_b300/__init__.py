@@ -21,6 +21,7 @@ The raw one-to-one binding is `paper_2609_35619_b300.abi`.
 from __future__ import annotations
 
 import ctypes
+import os
 from dataclasses import dataclass
 
 from . import abi
@@ -118,6 +119,20 @@ class Scene:
                 "n_large": inf.n_large, "n_invalid": inf.n_invalid, "dims": list(inf.dims),
                 "cell_size": inf.cell_size, "sigma_tier": inf.sigma_tier, "lo": list(inf.lo),
                 "hi": list(inf.hi), "device_bytes": inf.device_bytes}
+
+    def save(self, path, stream=None):
+        """Write the built scene to a file (cs_scene_save)."""
+        check(abi.cs_scene_save(self._h, os.fspath(path), stream))
+
+    @classmethod
+    def load(cls, path, *, device="cuda", stream=None) -> "Scene":
+        """A scene read from a file of save() on the current device, without a rebuild (cs_scene_load)."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p()
+        check(abi.cs_scene_load(os.fspath(path), stream, self._h))
+        self.device = torch.device(device)
+        return self
 
     def export(self, stream=None):
         torch = _torch()

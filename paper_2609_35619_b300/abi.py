@@ -197,6 +197,8 @@ _SIGNATURES = {
     "cs_scene_destroy": (ctypes.c_int, [_P]),
     "cs_scene_info_get": (ctypes.c_int, [_P, ctypes.POINTER(cs_scene_info)]),
     "cs_scene_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "cs_scene_save": (ctypes.c_int, [_P, ctypes.c_char_p, _P]),
+    "cs_scene_load": (ctypes.c_int, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "cs_query": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P,
                                 ctypes.POINTER(cs_params)]),
     "cs_query_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_float, _P, _P,
@@ -329,6 +331,15 @@ def cs_scene_info_get(scene, info: cs_scene_info) -> int:
 
 def cs_scene_export(scene, pos, cov, index, stream) -> int:
     return load().cs_scene_export(scene, ptr(pos), ptr(cov), ptr(index), stream_handle(stream))
+
+
+def cs_scene_save(scene, path, stream) -> int:
+    return load().cs_scene_save(scene, None if path is None else os.fsencode(path), stream_handle(stream))
+
+
+def cs_scene_load(path, stream, out: "ctypes.c_void_p") -> int:
+    return load().cs_scene_load(None if path is None else os.fsencode(path), stream_handle(stream),
+                                ctypes.byref(out))
 
 
 def cs_query(scene, prim_type, prims, Q, conservatism, out_metric, out_collide, params) -> int:

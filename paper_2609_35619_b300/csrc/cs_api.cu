@@ -215,8 +215,8 @@ cs_status check_params(const cs_params &p) {
         if (!(p.sweep_nsigma[k] >= 0.f) || !isfinite(p.sweep_nsigma[k]))
             return invalid("sweep_nsigma values must be finite and >= 0");
     if (p.tile_config != 0 && p.tile_config != CS_TILE_TUNED) {
-        int32_t ids[32];
-        int n = tile_configs(ids, 32);
+        int32_t ids[64];
+        int n = tile_configs(ids, 64);
         bool found = false;
         for (int i = 0; i < n; ++i) found |= ids[i] == p.tile_config;
         if (!found) return invalid("unknown tile_config");
@@ -576,6 +576,6 @@ int64_t cs_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 
 const char *cs_last_error(void) { return g_err.c_str(); }
 
-const char *cs_version(void) { return kDebugBuild ? "cs_b300 1.2 (sm_103a, CS_DEBUG)" : "cs_b300 1.2 (sm_103a)"; }
+const char *cs_version(void) { return kDebugBuild ? "cs_b300 1.3 (sm_103a, CS_DEBUG)" : "cs_b300 1.3 (sm_103a)"; }
 
 }  // extern "C"

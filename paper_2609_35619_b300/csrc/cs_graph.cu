@@ -276,9 +276,9 @@ cs_status cs_autotune(cs_scene *scene, int32_t prim_type, const float *prims, in
         cudaEventDestroy(ev[0]);
         return cuda_fail(cudaErrorUnknown, "cudaEventCreate");
     }
-    int32_t ids[32];
-    float times[32];
-    const int n = tile_configs(ids, 32);
+    int32_t ids[64];
+    float times[64];
+    const int n = tile_configs(ids, 64);
     float best_ms = INFINITY;
     int32_t best_id = 0;
     for (int i = 0; i < n && st == CS_OK; ++i) {

@@ -184,6 +184,12 @@ struct __align__(16) EvalSmem {
     // per consumer warp: the stage's slots that pass the warp test, by rank
     // (the quad tests of sweep launches)
     int slots[C::NCW][32];
+    // per consumer warp: its box of primitive centres with the largest reach
+    // parameters, (lo, alpha) (hi, beta), and on the sweep quad shapes each
+    // quad as one sphere record (read by the per-stage tests; kept here rather
+    // than in registers)
+    float4 wbox[C::NCW][2];
+    float4 wquad[C::NCW][4][2];
     // persistent shapes: tile indices from the producer to the consumer
     // warps, two deep (tfull: one arrival by the producer; tempty: one per
     // consumer warp once it has read the index)
@@ -830,11 +836,9 @@ __device__ __forceinline__ void geom_g2(const LaneG2 &g, const float4 *qd, f32x2
 //   - st2 <= S_cut_u and st2 < T_in_u hold exactly when 0 <= S_cut and
 //     0 < T_in, as for the clamped value.
 template <int QW, bool K0>
-__device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2, f32x2 sq, const float4 *qd,
-                                        const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
-    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
-    const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
-    const f32x2 st = mul2(fma2(nns2, sq, r2), pb.y);
+__device__ __forceinline__ void tail_g2v(Acc<0, QW, 0, false> &A, int j, f32x2 r2, f32x2 sq, f32x2 ir2,
+                                         f32x2 nns2, const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
+    const f32x2 st = mul2(fma2(nns2, sq, r2), ir2);
     float e0, e1, s0, s1;
     upk2(fma2(st, nG2, Gs2), e0, e1);
     upk2(st, s0, s1);
@@ -848,6 +852,15 @@ __device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2
     }
     A.sum[j] += nb0 ? dc0 : 0.f;
     A.sum[j] += nb1 ? dc1 : 0.f;
+}
+
+// The same for row j's record in shared memory: scale (qd[1]) and n_sigma (qd[2]).
+template <int QW, bool K0>
+__device__ __forceinline__ void tail_g2(Acc<0, QW, 0, false> &A, int j, f32x2 r2, f32x2 sq, const float4 *qd,
+                                        const QueryConsts &k, f32x2 nG2, f32x2 Gs2) {
+    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&qd[1]);  // -cz, 1/r^2
+    const f32x2 nns2 = *reinterpret_cast<const f32x2 *>(&qd[2]);          // -2n
+    tail_g2v<QW, K0>(A, j, r2, sq, pb.y, nns2, k, nG2, Gs2);
 }
 
 template <int QW, bool EX, bool K0>
@@ -980,15 +993,18 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
                 // of that copy (st2 <= S_cut), no copy has a neighbour or an
                 // in-collision pair among these Gaussians (st2 < T_in implies
                 // st2 <= S_cut), and the four tails would add exactly nothing.
+                // The four rows are one sphere: its scale 1/r^2 (row j0's) serves
+                // every tail; each row keeps its own n_sigma.
+                const f32x2 ir2 = reinterpret_cast<const ulonglong2 *>(&wqd[j0][1])->y;  // 1/r^2
                 {
-                    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&wqd[j0][1]);  // -cz, 1/r^2
-                    const f32x2 nmax = *reinterpret_cast<const f32x2 *>(&wqd[j0][2].z);       // -2 n_max
+                    const f32x2 nmax = *reinterpret_cast<const f32x2 *>(&wqd[j0][2].z);  // -2 n_max
                     float t0, t1;
-                    upk2(mul2(fma2(nmax, sq, r2), pb.y), t0, t1);
+                    upk2(mul2(fma2(nmax, sq, r2), ir2), t0, t1);
                     if (!__any_sync(0xffffffffu, t0 <= k.S_cut_u || t1 <= k.S_cut_u)) continue;
                 }
 #pragma unroll
-                for (int j = j0; j < j0 + 4; ++j) tail_g2<QW, K0>(A, j, r2, sq, wqd[j], k, nG2, Gs2);
+                for (int j = j0; j < j0 + 4; ++j)
+                    tail_g2v<QW, K0>(A, j, r2, sq, ir2, *reinterpret_cast<const f32x2 *>(&wqd[j][2]), k, nG2, Gs2);
             } else if ((SH & kShGeom) && GROUP == 2 && ((same >> j0) & 1u)) {
                 // rows j0 and j0 + 1 are the same sphere (n_sigma copies of a
                 // sweep): the geometry once, then each row's own n_sigma; the
@@ -1180,18 +1196,19 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     // chunk adds nothing, so the outputs do not change.
     constexpr bool QT = (SH & kShGeom) && PRIM == 0 && C::GROUP == 4 && C::IL == 4 && MODE == 0 && !GRAD;
     constexpr int NQ = QW / 4;  // quads per warp
-    float4 qrec[2];             // lane l: quad l % NQ as one record
     bool quadok = false;
     if constexpr (QT) {
-        const int qi = lane % NQ;
-        qrec[0] = wq[4 * qi][0];
-        qrec[1] = wq[4 * qi][1];
+        if (lane < NQ) {  // quad `lane` as one record
+            float4 r0 = wq[4 * lane][0], r1 = wq[4 * lane][1];
 #pragma unroll
-        for (int m = 1; m < 4; ++m) {
-            const float4 b = wq[4 * qi + m][1];
-            qrec[1].y = fmaxf(qrec[1].y, b.y);
-            qrec[1].z = fmaxf(qrec[1].z, b.z);
-            qrec[1].w = fmaxf(qrec[1].w, b.w);
+            for (int m = 1; m < 4; ++m) {
+                const float4 b = wq[4 * lane + m][1];
+                r1.y = fmaxf(r1.y, b.y);
+                r1.z = fmaxf(r1.z, b.z);
+                r1.w = fmaxf(r1.w, b.w);
+            }
+            sm->wquad[warp][lane][0] = r0;
+            sm->wquad[warp][lane][1] = r1;
         }
         unsigned whole = 0u;
 #pragma unroll
@@ -1224,6 +1241,11 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
         wal = fmaxf(wal, __shfl_xor_sync(0xffffffffu, wal, o));
         wbe = fmaxf(wbe, __shfl_xor_sync(0xffffffffu, wbe, o));
     }
+    if (lane == 0) {
+        sm->wbox[warp][0] = make_float4(wlx, wly, wlz, wal);
+        sm->wbox[warp][1] = make_float4(whx, why, whz, wbe);
+    }
+    __syncwarp();
 
     Acc<PRIM, QW, MODE, GRAD> A;
     A.fin = 0u;
@@ -1311,8 +1333,9 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             bool wpass = false;
             if (lane < nslots) {
                 const float4 blo = sm->blk[s][lane].lo, bhi = sm->blk[s][lane].hi;
-                const float R = reach<EX && PRIM == 0>(wal, wbe, blo.w, sc.pad_abs);
-                wpass = box_gap2(wlx, wly, wlz, whx, why, whz, blo, bhi) <= R * R;
+                const float4 wl = sm->wbox[warp][0], wh = sm->wbox[warp][1];
+                const float R = reach<EX && PRIM == 0>(wl.w, wh.w, blo.w, sc.pad_abs);
+                wpass = box_gap2(wl.x, wl.y, wl.z, wh.x, wh.y, wh.z, blo, bhi) <= R * R;
             }
             unsigned pmask = __ballot_sync(0xffffffffu, wpass);
             if (lane == 0) wst[2] += (unsigned long long)__popc(pmask);
@@ -1336,7 +1359,8 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                     bool qp = false;
                     if (kq < npass) {
                         const int my = sm->slots[warp][kq];
-                        qp = reaches<0, EX>(qrec, sm->blk[s][my].lo, sm->blk[s][my].hi, sc.pad_abs, k.S_reach);
+                        qp = reaches<0, EX>(sm->wquad[warp][lane % NQ], sm->blk[s][my].lo, sm->blk[s][my].hi,
+                                            sc.pad_abs, k.S_reach);
                     }
                     const unsigned hits = __ballot_sync(0xffffffffu, qp);
                     if (mine && rank >= base && rank < base + CPRQ) {
@@ -1797,6 +1821,10 @@ QueryConsts make_consts(const cs_params &p) {
 //   28: shape 27 as a persistent kernel (SMs x 3 CTAs taking tiles from a
 //       counter; the producer stages the next tile while the consumers end
 //       the current one); the flags mode runs its own shapes
+//   29: 4 x 16, 2 stages x 16 chunks, 4 CTAs/SM, row quads in groups of 4
+//       (at most 96 registers: the warp box and quad records live in shared
+//       memory; four CTAs of five warps fill the register file)
+//   30: shape 29 as a persistent kernel
 using Cfg1 = Cfg<8, 8, 4, 16, 2>;
 using Cfg2 = Cfg<8, 16, 4, 16, 1>;
 using Cfg3 = Cfg<4, 8, 3, 8, 4>;
@@ -1825,6 +1853,8 @@ using Cfg25 = Cfg<8, 8, 2, 32, 2, 4, 4>;
 using Cfg26 = Cfg<4, 16, 3, 16, 3, 4, 4>;
 using Cfg27 = Cfg<4, 16, 2, 24, 3, 4, 4>;
 using Cfg28 = Cfg<4, 16, 2, 24, 3, 4, 4, true>;
+using Cfg29 = Cfg<4, 16, 2, 16, 4, 4, 4>;
+using Cfg30 = Cfg<4, 16, 2, 16, 4, 4, 4, true>;
 // Adjoint shapes (cs_query_grad; tile_config 1-4, 0 = 2): the adjoint keeps
 // three gradient sums per primitive, so its tiles hold fewer primitives
 //   1: 4 x 8, 3 stages x 8 chunks, 3 CTAs/SM
@@ -1836,7 +1866,8 @@ using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
 constexpr int kDefaultGradTile = 2;
-static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28};
+static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30};
+static_assert(sizeof(kTileIds) / sizeof(kTileIds[0]) <= 64, "callers hold up to 64 shape ids");
 constexpr int kDefaultTile = 18;
 constexpr int kSmallBatchTile = 23;
 constexpr int kSmallBatchQ = 1 << 17;
@@ -1990,6 +2021,8 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
         case 26: return launch_mode_sweep<PRIM, Cfg26>(a, s);
         case 27: return launch_mode_sweep<PRIM, Cfg27>(a, s);
         case 28: return launch_mode_sweep<PRIM, Cfg28>(a, s);
+        case 29: return launch_mode_sweep<PRIM, Cfg29>(a, s);
+        case 30: return launch_mode_sweep<PRIM, Cfg30>(a, s);
         default: return launch_mode<PRIM, Cfg1>(a, s);
     }
 }

@@ -84,3 +84,48 @@ def test_binding_marshals_numpy_and_rejects_strided():
     with pytest.raises(ValueError):
         abi.ptr(a[:, ::2])
     assert abi.ptr(None) is None
+
+
+def _scene_file_header(**kw):
+    """A scene file header (magic, version, counts, layout, blob offsets) in
+    the 192-byte layout cs_scene_load reads; one chunk, one Gaussian."""
+    f = dict(magic=b"CSB300SC", version=1, header_bytes=192, n_input=1, n_kept=1, n_grid=1, n_large=0,
+             n_invalid=0, blob_bytes=2820, app_bytes=0, nchunks=1, large_chunk0=1, n_gauss=1,
+             nnodes=(1, 1, 1), floats=(0.1, 0.0, 1e-6, 0, 0, 0, 1, 1, 1),
+             off_chead=1280, off_nodes=(1536, 1792, 2048), off_smax=2304, off_index=2560, off_slot=2816)
+    f.update(kw)
+    import struct
+    return struct.pack("<8sII7q6i9f4x7q", f["magic"], f["version"], f["header_bytes"], f["n_input"], f["n_kept"],
+                       f["n_grid"], f["n_large"], f["n_invalid"], f["blob_bytes"], f["app_bytes"], f["nchunks"],
+                       f["large_chunk0"], f["n_gauss"], *f["nnodes"], *f["floats"], f["off_chead"], *f["off_nodes"],
+                       f["off_smax"], f["off_index"], f["off_slot"])
+
+
+def test_scene_file_checks_without_device(tmp_path):
+    """cs_scene_load validates a file before it touches the device: missing
+    file, wrong magic or version, an inconsistent layout, a truncated blob and
+    a slot index out of range are CS_ERR_INVALID_ARG with *out NULL."""
+    assert len(_scene_file_header()) == 192
+    out = ctypes.c_void_p()
+    assert abi.cs_scene_save(None, str(tmp_path / "x"), None) == abi.CS_ERR_BAD_HANDLE
+    assert abi.cs_scene_load(None, None, out) == abi.CS_ERR_INVALID_ARG
+    assert abi.cs_scene_load(str(tmp_path / "missing"), None, out) == abi.CS_ERR_INVALID_ARG
+    blob = bytearray(2820)
+    cases = {
+        "magic": _scene_file_header(magic=b"CSB300XX") + bytes(blob),
+        "another format version": _scene_file_header(version=2) + bytes(blob),
+        "short header": _scene_file_header()[:100],
+        "inconsistent layout": _scene_file_header(nnodes=(2, 1, 1)) + bytes(blob),
+        "inconsistent layout ": _scene_file_header(off_slot=2817) + bytes(blob),
+        "inconsistent layout  ": _scene_file_header(n_grid=0) + bytes(blob),
+        "truncated": _scene_file_header() + bytes(blob[:-1]),
+    }
+    slot_bad = bytearray(blob)
+    slot_bad[2816:2820] = (32).to_bytes(4, "little")  # one chunk has slots 0..31
+    cases["slot index"] = _scene_file_header() + bytes(slot_bad)
+    for why, data in cases.items():
+        p = tmp_path / "f.csscene"
+        p.write_bytes(data)
+        assert abi.cs_scene_load(str(p), None, out) == abi.CS_ERR_INVALID_ARG, why
+        assert not out
+        assert why.strip() in abi.cs_last_error(), (why, abi.cs_last_error())

@@ -2,8 +2,9 @@
 size: the 1M-Gaussian tabletop with the 262,144 arm spheres (groups of 64, one
 per configuration) and the 2,097,152 RRT edge spheres (groups of 1,024, one per
 edge), each as one conservatism-sweep call over n_sigma = 0, 0.5, 1, 2 on tile
-shape 27 (the shape the benchmark times: row quads, the sweep copies sharing
-their geometry, the k_thr = 0 running minimum).
+shape 29 (the shape the autotuner picks for the benchmark: row quads, the sweep
+copies sharing their geometry, k_thr = 0 flags as one bit per row, four CTAs
+per SM); the other quad shapes (27, 28, 30) give the same bits at full size.
 
 Per n_sigma block: a seeded sample of at least 192 rows (half uniform, half
 among rows that touch the scene) element by element, and whole groups (two
@@ -23,7 +24,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 NSIGMAS = (0.0, 0.5, 1.0, 2.0)
-TILE = 27
+TILE = 29
 
 
 @pytest.fixture(scope="module")
@@ -74,3 +75,23 @@ def test_benchmark_sweep_launch_full_size(tabletop, batch):
                                out["group_collide"][b * ng + g: b * ng + g + 1], grows["metric"], og, grep, G,
                                oracle.MODE_MEAN, f"{batch} ns={ns} group {g}", interval=interval)
             assert n == 1
+
+
+@pytest.mark.parametrize("batch", ["arm", "edge"])
+def test_quad_shapes_agree_at_full_size(tabletop, batch):
+    """Shapes 27, 28 (persistent), 29 and 30 (persistent) run the same
+    per-lane accumulation order, so the benchmark's sweep launches give the
+    same bits on each of them."""
+    cs, sc, scene = tabletop
+    q = torch.as_tensor(S.arm_queries() if batch == "arm" else S.edge_queries())
+    G = 64 if batch == "arm" else 1024
+    outs = {}
+    for tile in (27, 28, 29, 30):
+        outs[tile] = to_np(scene.query(q, 0.0, want_count=True,
+                                       params=cs.QueryParams(group_size=G, tile_config=tile, sweep=NSIGMAS)))
+        torch.cuda.synchronize()
+    for tile in (27, 28, 30):
+        for k in outs[TILE]:
+            np.testing.assert_array_equal(outs[tile][k].view(np.uint8), outs[TILE][k].view(np.uint8),
+                                          err_msg=f"{batch} tile {tile} {k}")
+    scene.sync()

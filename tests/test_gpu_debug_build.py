@@ -1,7 +1,7 @@
 """The CS_DEBUG build (device index checks that record CS_ERR_BOUNDS and skip
 the access, no trap) runs the parity cases clean: every check holds on the
 tiny scene in the cost mode, a conservatism sweep with groups, the persistent
-tile shape, the flags mode with groups, the adjoint and ellipsoids, and the results still match the FP64
+tile shapes, the four-CTA quad shapes, the flags mode with groups, the adjoint and ellipsoids, and the results still match the FP64
 oracle.  It runs in a child process that loads libcs_b300_debug.so through
 CS_B300_LIBRARY.  Also: the autotuner's JSON log."""
 import json
@@ -39,9 +39,16 @@ scene.sync()
 for b, ns in enumerate((0.0, 1.0, 2.0)):
     blk = {{k: v[b * 1000:(b + 1) * 1000] for k, v in sw.items() if v.shape[0] == 3000}}
     compare(blk, oracle.query(sc, q, 0, ns, P), 0, P, f"debug sweep ns={{ns}}")
-pe = to_np(scene.query(torch.as_tensor(q), 1.0, want_count=True, params=cs.QueryParams(group_size=32, tile_config=28)))
+for t in (28, 29, 30):
+    pe = to_np(scene.query(torch.as_tensor(q), 1.0, want_count=True, params=cs.QueryParams(group_size=32, tile_config=t)))
+    scene.sync()
+    compare(pe, oracle.query(sc, q, 0, 1.0, P), 0, P, f"debug shape {{t}}")
+sw = to_np(scene.query(torch.as_tensor(q), 0.0, want_count=True,
+                       params=cs.QueryParams(group_size=64, sweep=(0.0, 1.0, 2.0, 0.5), tile_config=30)))
 scene.sync()
-compare(pe, oracle.query(sc, q, 0, 1.0, P), 0, P, "debug persistent shape")
+for b, ns in enumerate((0.0, 1.0, 2.0, 0.5)):
+    blk = {{k: v[b * 1000:(b + 1) * 1000] for k, v in sw.items() if v.shape[0] == 4000}}
+    compare(blk, oracle.query(sc, q, 0, ns, P), 0, P, f"debug persistent sweep ns={{ns}}")
 fl = to_np(scene.query(torch.as_tensor(q), 1.0, params=cs.QueryParams(group_size=16, mode=cs.CS_METRIC_FLAGS)))
 scene.sync()
 g = scene.query_grad(torch.as_tensor(q), 1.0, params=cs.QueryParams(group_size=32))

@@ -52,7 +52,7 @@ def test_tiny_scene_all_modes(cs, nsigma, mode):
     assert rep["checked"] > 0.9 * rep["Q"]
 
 
-@pytest.mark.parametrize("cfg", list(range(1, 29)))
+@pytest.mark.parametrize("cfg", list(range(1, 31)))
 @pytest.mark.parametrize("Q", [1, 37, 1000, 5000])
 def test_tile_configs_and_ragged_batches(cs, cfg, Q):
     """Every tile shape, batch sizes spanning one to many tiles with a ragged tail."""
@@ -97,7 +97,7 @@ def test_ellipsoids(cs, mode, axes):
     # widened band puts more pairs near s_min under cond_cost: 66 of the 600
     # rows (11 %) take the widened bound with semi-axes from 8 mm
     cap = 0.05 if axes[0] >= 0.03 else 0.15
-    for cfg in (1, 2, 3, 4, 18, 23, 27, 28):
+    for cfg in (1, 2, 3, 4, 18, 23, 27, 28, 29, 30):
         out = _run(cs, scene, e, 1.0, prim_type=1, mode=mode, tile_config=cfg)
         rep = compare(out, orc, mode, oracle.Params(), f"ellipsoid mode={mode}", kappa=kappa, max_cancel=cap)
         assert rep["checked"] > 0.5 * rep["Q"], rep
@@ -452,9 +452,11 @@ def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
     (0, 15, (0.0, 0.5, 1.0, 2.0), 0), (0, 18, (0.0, 0.5, 1.0, 2.0), 0), (0, 24, (0.0, 0.5, 1.0, 2.0), 0),
     (0, 24, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 24, (2.0, 0.0, 1.0), 0), (0, 23, (0.0, 0.5, 1.0, 2.0), 0),
     (0, 22, (0.0, 0.5, 1.0, 2.0), 0), (0, 15, (1.0, 0.5, 0.0), 0),
-    # quads evaluated as one group of four, with one reach test per quad (25-27)
+    # quads evaluated as one group of four, with one reach test per quad (25-30)
     (0, 26, (0.0, 0.5, 1.0, 2.0), 0), (0, 26, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 26, (2.0, 0.0, 1.0), 0),
     (0, 27, (0.0, 0.5, 1.0, 2.0), 0), (0, 27, (1.0, 0.5, 0.0), 0), (0, 26, (0.0, 0.5, 1.0, 2.0), 2),
+    (0, 29, (0.0, 0.5, 1.0, 2.0), 0), (0, 29, (2.0, 0.0, 1.0), 0), (0, 29, (0.0, 0.5, 1.0, 2.0, 1.25), 2),
+    (0, 30, (0.0, 0.5, 1.0, 2.0), 0),
     (0, 25, (0.0, 0.5, 1.0, 2.0), 0), (0, 25, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 25, (2.0, 0.0, 1.0), 0),
     # k_thr > 0: in-collision counts instead of the smallest st^2
     (0, 25, (0.0, 0.5, 1.0, 2.0), 2), (0, 24, (0.0, 0.5, 1.0, 2.0), 1), (0, 0, (0.0, 1.0, 2.0), 3)])
@@ -494,10 +496,11 @@ def test_sweep_parameter_equals_separate_calls(cs, prim_type, tile, sweep, k_thr
                     params=cs.QueryParams(mode=cs.CS_METRIC_FLAGS, sweep=sweep))
 
 
-def test_persistent_shape_equals_its_one_tile_per_cta_shape(cs):
-    """Shape 28 runs shape 27 as a persistent kernel (SMs x 3 CTAs taking
-    tiles from a counter).  On a batch of far more tiles than the grid holds,
-    with a ragged last tile, every output has the bits of shape 27: each row's
+@pytest.mark.parametrize("base,persistent", [(27, 28), (29, 30)])
+def test_persistent_shape_equals_its_one_tile_per_cta_shape(cs, base, persistent):
+    """Shapes 28 and 30 run shapes 27 and 29 as persistent kernels (SMs x 3
+    or 4 CTAs taking tiles from a counter).  On a batch of far more tiles than the grid holds,
+    with a ragged last tile, every output has the bits of its base shape: each row's
     reductions do not depend on which CTA or in which order its tile ran.
     Also as a conservatism sweep with groups, and twice in a row on one stream
     (the tile counter starts every launch at zero)."""
@@ -506,9 +509,9 @@ def test_persistent_shape_equals_its_one_tile_per_cta_shape(cs):
     _TABLE["gpu"] = scene
     q = torch.as_tensor(S.edge_queries(edges=600)[:-13].copy())  # 153,587 rows: ~2,400 tiles of 64
     for params in ({}, {"group_size": 64, "sweep": (0.0, 0.5, 1.0, 2.0)}):
-        ref = to_np(scene.query(q, 1.0, want_count=True, params=cs.QueryParams(tile_config=27, **params)))
+        ref = to_np(scene.query(q, 1.0, want_count=True, params=cs.QueryParams(tile_config=base, **params)))
         for rep in range(2):
-            got = to_np(scene.query(q, 1.0, want_count=True, params=cs.QueryParams(tile_config=28, **params)))
+            got = to_np(scene.query(q, 1.0, want_count=True, params=cs.QueryParams(tile_config=persistent, **params)))
             torch.cuda.synchronize()
             for k in ref:
                 np.testing.assert_array_equal(got[k].view(np.uint8), ref[k].view(np.uint8), err_msg=f"{k} {params}")
