@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <float.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
@@ -320,6 +321,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // One poll; true when the phase with the given parity has completed.
+// try_wait with a suspend-time hint: the thread may sleep up to `ns`
+// nanoseconds for the phase (it resumes when the phase completes), so a long
+// wait takes few polls and leaves the issue slots to other warps.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, unsigned parity, unsigned ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -399,14 +414,19 @@ __device__ __forceinline__ float lg2_approx(float x) {
 //   x^2 <= beta + 2 a^2 + 2 a sqrt(beta + a^2 + 1.5 sigma^2),  a = alpha sigma,
 // which reduces to R(sigma)^2 without the 1.5 sigma^2.  Both grow with alpha
 // and beta, so the largest of a group bound the whole group.
+// The roots are the hardware approximation (one MUFU operation, relative
+// error below 2^-22); the relative padding kReachPadRel = 1e-4 covers it
+// many times over, so the radius stays an upper bound.  Its input is held at
+// FLT_MIN or above (the approximation flushes subnormals to zero, which would
+// make a tiny radius smaller than it is).
 template <bool EX = false>
 __device__ __forceinline__ float reach(float alpha, float beta, float sigma, float pad_abs) {
     float a = alpha * sigma;
     if constexpr (EX) {
-        const float inner = sqrtf(fmaf(a, a, fmaf(1.5f * sigma, sigma, beta)));
-        return sqrtf(fmaf(2.f * a, a + inner, beta)) * (1.f + kReachPadRel) + pad_abs;
+        const float inner = sqrt_approx(fmaxf(fmaf(a, a, fmaf(1.5f * sigma, sigma, beta)), FLT_MIN));
+        return sqrt_approx(fmaxf(fmaf(2.f * a, a + inner, beta), FLT_MIN)) * (1.f + kReachPadRel) + pad_abs;
     }
-    return (a + sqrtf(fmaf(a, a, beta))) * (1.f + kReachPadRel) + pad_abs;
+    return (a + sqrt_approx(fmaxf(fmaf(a, a, beta), FLT_MIN))) * (1.f + kReachPadRel) + pad_abs;
 }
 
 }  // namespace cs

@@ -157,6 +157,14 @@ constexpr int kShK0 = 2;
 // kShFwd (adjoint launches, spheres, cost modes): the same launch also writes
 // the forward outputs (metric, flag, count) from the pairs it evaluates.
 constexpr int kShFwd = 4;
+// kShQuad (with kShGeom, on the row-quad shapes that evaluate groups of four):
+// the sweep has a multiple of four n_sigma values, so every row quad of a
+// tile is four copies of one prepared sphere (launch rows 4m .. 4m + 3 are
+// p S + s .. p S + s + 3), or four dead rows (beyond the batch, or a sphere
+// whose record is invalid).  Only the quad evaluation is compiled: no
+// per-row fallback, fewer registers.  A dead quad's record has live = 0,
+// so its reach test never passes and it is never evaluated.
+constexpr int kShQuad = 8;
 
 // Per-primitive data in shared memory, 4 float4 (QREC) per primitive:
 //   sphere:    (c, 1/r^2) (2n, alpha, beta, live) - -
@@ -251,12 +259,13 @@ __device__ __forceinline__ long long globaltimer_ns() {
 }
 
 // Bounded wait by poll count and wall time (1 s; a healthy wait is a few
-// microseconds).
+// microseconds).  Each poll may sleep up to kWaitHintNs for the phase.
 // Returns the number of polls the wait took, or -1 when it gave up.
+constexpr unsigned kWaitHintNs = 20000;
 __device__ __noinline__ long long wait_phase(uint64_t *bar, unsigned parity, long long polls) {
     long long t0 = globaltimer_ns();
     for (long long i = 0; i < polls; ++i) {
-        if (mbar_try_wait(bar, parity)) return i + 1;
+        if (mbar_try_wait_hint(bar, parity, kWaitHintNs)) return i + 1;
         if ((i & 255) == 255 && globaltimer_ns() - t0 > 1000000000ll) break;
     }
     return -1;
@@ -984,7 +993,8 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 #pragma unroll
     for (int j0 = 0; j0 < QW; j0 += GROUP) {
         if ((gm >> j0) & 1u) {
-            if ((SH & kShGeom) && GROUP == 4 && ((same >> j0) & (same >> (j0 + 2)) & (link >> (j0 + 2)) & 1u)) {
+            if ((SH & kShQuad) ||
+                ((SH & kShGeom) && GROUP == 4 && ((same >> j0) & (same >> (j0 + 2)) & (link >> (j0 + 2)) & 1u))) {
                 // rows j0 .. j0 + 3 are one sphere: the geometry once, four tails
                 geom_g2<EX>(g2, wqd[j0], r2, sq);
                 // The quad's highest n_sigma copy first.  st2 does not increase
@@ -1005,6 +1015,8 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
 #pragma unroll
                 for (int j = j0; j < j0 + 4; ++j)
                     tail_g2v<QW, K0>(A, j, r2, sq, ir2, *reinterpret_cast<const f32x2 *>(&wqd[j][2]), k, nG2, Gs2);
+            } else if constexpr ((SH & kShQuad) != 0) {
+                // not reached: every group is a quad
             } else if ((SH & kShGeom) && GROUP == 2 && ((same >> j0) & 1u)) {
                 // rows j0 and j0 + 1 are the same sphere (n_sigma copies of a
                 // sweep): the geometry once, then each row's own n_sigma; the
@@ -1024,6 +1036,104 @@ __device__ __forceinline__ void eval_chunk_pair(Acc<0, QW, 0, false> &A, const C
             have = false;
         }
     }
+}
+
+// Sweep launches with whole quads (kShQuad): one chunk pair against the
+// warp's quads of `qm` (bit qq: quad qq, rows 4 qq .. 4 qq + 3, reaches
+// either chunk).  The operations, and their order per lane and row, are those
+// of eval_chunk_pair's quad branch, hence the same bits.  n1 == 0: no second
+// chunk (its half holds the padding point, which meets no primitive).
+template <int QW, bool EX, int SH>
+__device__ __forceinline__ void eval_pair_quads(Acc<0, QW, 0, false> &A, const ChunkBlock &B0, int n0,
+                                                const ChunkBlock &B1, int n1, unsigned qm, float4 (*wqd)[3],
+                                                const QueryConsts &k, int lane, unsigned &cand, unsigned &c_hits) {
+    constexpr bool K0 = (SH & kShK0) != 0;
+    constexpr int NQ = QW / 4;
+    LaneG2 g2;
+    g2.x = pk2(B0.x[lane], B1.x[lane]); g2.y = pk2(B0.y[lane], B1.y[lane]); g2.z = pk2(B0.z[lane], B1.z[lane]);
+    g2.sxx = pk2(B0.sxx[lane], B1.sxx[lane]); g2.syy = pk2(B0.syy[lane], B1.syy[lane]);
+    g2.szz = pk2(B0.szz[lane], B1.szz[lane]); g2.sxy2 = pk2(B0.sxy2[lane], B1.sxy2[lane]);
+    g2.sxz2 = pk2(B0.sxz2[lane], B1.sxz2[lane]); g2.syz2 = pk2(B0.syz2[lane], B1.syz2[lane]);
+    if (n1 == 0) {  // the padding point in half 1
+        float a, b;
+        upk2(g2.x, a, b); g2.x = pk2(a, 1e18f);
+        upk2(g2.y, a, b); g2.y = pk2(a, 1e18f);
+        upk2(g2.z, a, b); g2.z = pk2(a, 1e18f);
+        upk2(g2.sxx, a, b); g2.sxx = pk2(a, 0.f);
+        upk2(g2.syy, a, b); g2.syy = pk2(a, 0.f);
+        upk2(g2.szz, a, b); g2.szz = pk2(a, 0.f);
+        upk2(g2.sxy2, a, b); g2.sxy2 = pk2(a, 0.f);
+        upk2(g2.sxz2, a, b); g2.sxz2 = pk2(a, 0.f);
+        upk2(g2.syz2, a, b); g2.syz2 = pk2(a, 0.f);
+    }
+    if constexpr (EX) {
+        LaneG h0, h1;
+        upk2(g2.sxx, h0.sxx, h1.sxx); upk2(g2.syy, h0.syy, h1.syy); upk2(g2.szz, h0.szz, h1.szz);
+        upk2(g2.sxy2, h0.sxy2, h1.sxy2); upk2(g2.sxz2, h0.sxz2, h1.sxz2); upk2(g2.syz2, h0.syz2, h1.syz2);
+        g2.f = pk2(half_tr_ss(h0), half_tr_ss(h1));
+    }
+    const unsigned nq = (unsigned)__popc(qm);
+    c_hits += 4u * nq;
+    cand += 4u * nq * (unsigned)(n0 + n1);
+    const f32x2 nG2 = pk2(-k.G, -k.G), Gs2 = pk2(k.Gsmin, k.Gsmin);
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) {
+        if (!((qm >> qq) & 1u)) continue;
+        const int j0 = 4 * qq;
+        f32x2 r2, sq;
+        geom_g2<EX>(g2, wqd[j0], r2, sq);
+        const f32x2 ir2 = reinterpret_cast<const ulonglong2 *>(&wqd[j0][1])->y;  // 1/r^2
+        {
+            // the quad's highest n_sigma copy first (see eval_chunk_pair)
+            const f32x2 nmax = *reinterpret_cast<const f32x2 *>(&wqd[j0][2].z);  // -2 n_max
+            float t0, t1;
+            upk2(mul2(fma2(nmax, sq, r2), ir2), t0, t1);
+            if (!__any_sync(0xffffffffu, t0 <= k.S_cut_u || t1 <= k.S_cut_u)) continue;
+        }
+#pragma unroll
+        for (int j = j0; j < j0 + 4; ++j)
+            tail_g2v<QW, K0>(A, j, r2, sq, ir2, *reinterpret_cast<const f32x2 *>(&wqd[j][2]), k, nG2, Gs2);
+    }
+}
+
+// One stage of a kShQuad consumer warp: lane l tests quad l % NQ against
+// slot base + l / NQ (one reach test per quad and staged chunk, the same test
+// as the quad test of the general path; no warp-box test first), then the
+// chunks some quad reaches are evaluated two at a time in slot order.
+// Returns the number of slots some quad reaches.
+template <int QW, bool EX, int SH, class C>
+__device__ __forceinline__ int quad_stage(Acc<0, QW, 0, false> &A, EvalSmem<C> *sm, int s, int nslots, int warp,
+                                          int lane, float4 (*wqd)[3], const QueryConsts &k, float pad_abs,
+                                          unsigned &cand, unsigned &c_hits) {
+    constexpr int NQ = QW / 4;
+    constexpr int SPR = 32 / NQ;  // slots per round
+    unsigned myq = 0u;            // lane t: the quads reaching slot t
+#pragma unroll 1
+    for (int base = 0; base < nslots; base += SPR) {
+        const int sl = base + lane / NQ;
+        bool qp = false;
+        if (sl < nslots) qp = reaches<0, EX>(sm->wquad[warp][lane % NQ], sm->blk[s][sl].lo, sm->blk[s][sl].hi,
+                                             pad_abs, k.S_reach);
+        const unsigned hits = __ballot_sync(0xffffffffu, qp);
+        const int r = lane - base;
+        if (r >= 0 && r < SPR) myq = (hits >> (r * NQ)) & ((1u << NQ) - 1u);
+    }
+    unsigned cmask = __ballot_sync(0xffffffffu, myq != 0u);
+    const int npass = __popc(cmask);
+    while (cmask) {
+        const int sa = __ffs(cmask) - 1;
+        cmask &= cmask - 1;
+        int sb = sa, n1 = 0;
+        if (cmask) {
+            sb = __ffs(cmask) - 1;
+            cmask &= cmask - 1;
+            n1 = sm->meta[s][sb].hi;
+        }
+        const unsigned qm = __shfl_sync(0xffffffffu, myq, sa) | __shfl_sync(0xffffffffu, myq, sb);
+        eval_pair_quads<QW, EX, SH>(A, sm->blk[s][sa], sm->meta[s][sa].hi, sm->blk[s][sb], n1, qm, wqd, k, lane,
+                                    cand, c_hits);
+    }
+    return npass;
 }
 
 // The adjoint counterpart of eval_chunk_pair (spheres, mean or sum cost).
@@ -1328,7 +1438,12 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 }
             }
         }
-        if ((MODE == 3) ? (wlive != 0u) : (nvalid > 0)) {
+        if constexpr (QT && (SH & kShQuad) != 0) {
+            if (nvalid > 0) {
+                const int npass = quad_stage<QW, EX, SH>(A, sm, s, nslots, warp, lane, wqd, k, sc.pad_abs, cand, c_hits);
+                if (lane == 0) wst[2] += (unsigned long long)npass;
+            }
+        } else if ((MODE == 3) ? (wlive != 0u) : (nvalid > 0)) {
             // lane t tests chunk slot t against the warp's box + reach
             bool wpass = false;
             if (lane < nslots) {
@@ -1345,7 +1460,7 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             constexpr int CPR = 32 / QW;
             constexpr unsigned QMASK = (1u << QW) - 1u;
             unsigned myq = 0u;
-            if (QT && quadok) {
+            if (QT && (quadok || (SH & kShQuad))) {
                 // lane l: quad l % NQ against the passing slot of rank
                 // base + l / NQ; slot t's quad bits become its row bits
                 constexpr int CPRQ = 32 / NQ;
@@ -1932,6 +2047,12 @@ static cudaError_t launch_mode(const EvalArgs &a, cudaStream_t s) {
 // in-collision count; every other launch keeps the plain evaluation.
 template <int PRIM, class C>
 static cudaError_t launch_mode_sweep(const EvalArgs &a, cudaStream_t s) {
+    if constexpr (PRIM == 0 && C::GROUP == 4 && C::IL == 4) {
+        const bool cost = a.k.mode == CS_METRIC_MEAN_COST || a.k.mode == CS_METRIC_SUM_COST;
+        if (a.k.sweep > 1 && a.k.sweep % 4 == 0 && cost)
+            return a.k.k_thr == 0 ? launch_eval_t<PRIM, C, 0, false, false, kShGeom | kShK0 | kShQuad>(a, s)
+                                  : launch_eval_t<PRIM, C, 0, false, false, kShGeom | kShQuad>(a, s);
+    }
     if constexpr (PRIM == 0 && (C::GROUP == 2 || (C::GROUP == 4 && C::IL == 4)) && C::IL != 1) {
         const bool cost = a.k.mode == CS_METRIC_MEAN_COST || a.k.mode == CS_METRIC_SUM_COST;
         if (a.k.sweep > 1 && cost)

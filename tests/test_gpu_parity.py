@@ -457,6 +457,8 @@ def test_nsigma_sweep_in_one_launch_equals_separate_launches(cs):
     (0, 27, (0.0, 0.5, 1.0, 2.0), 0), (0, 27, (1.0, 0.5, 0.0), 0), (0, 26, (0.0, 0.5, 1.0, 2.0), 2),
     (0, 29, (0.0, 0.5, 1.0, 2.0), 0), (0, 29, (2.0, 0.0, 1.0), 0), (0, 29, (0.0, 0.5, 1.0, 2.0, 1.25), 2),
     (0, 30, (0.0, 0.5, 1.0, 2.0), 0),
+    # eight values: two whole quads per primitive (the quad-only evaluation)
+    (0, 29, (0.0, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0), 0), (0, 28, (2.0, 1.0, 0.0, 0.5, 3.0, 0.1, 1.5, 0.7), 1),
     (0, 25, (0.0, 0.5, 1.0, 2.0), 0), (0, 25, (0.0, 0.5, 1.0, 2.0, 1.25), 0), (0, 25, (2.0, 0.0, 1.0), 0),
     # k_thr > 0: in-collision counts instead of the smallest st^2
     (0, 25, (0.0, 0.5, 1.0, 2.0), 2), (0, 24, (0.0, 0.5, 1.0, 2.0), 1), (0, 0, (0.0, 1.0, 2.0), 3)])
