@@ -576,6 +576,6 @@ int64_t cs_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 
 const char *cs_last_error(void) { return g_err.c_str(); }
 
-const char *cs_version(void) { return kDebugBuild ? "cs_b300 1.4 (sm_103a, CS_DEBUG)" : "cs_b300 1.4 (sm_103a)"; }
+const char *cs_version(void) { return kDebugBuild ? "cs_b300 1.5 (sm_103a, CS_DEBUG)" : "cs_b300 1.5 (sm_103a)"; }
 
 }  // extern "C"

@@ -18,7 +18,7 @@ namespace cs {
 // ---------------------------------------------------------------- constants
 constexpr int kChunk = 32;             // Gaussians per chunk record (warp-level cull unit)
 constexpr int kMortonBits = 8;         // bits per axis of the query sort key
-constexpr int kSceneMortonBits = 10;   // bits per axis of the scene order
+constexpr int kSceneOrderBits = 10;    // bits per axis of the scene order (Hilbert index)
 constexpr int kSegment = 1024;         // Gaussians per greedy chunking segment
 constexpr int kSigmaBins = 512;        // log2 histogram of the largest scale
 constexpr float kSigmaLog2Lo = -32.f;  // histogram covers 2^-32 .. 2^32 in 1/8 octaves

@@ -1328,35 +1328,37 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     }
     // the warp's box of primitive centres and its largest reach parameters:
     // a chunk outside box + reach is out of reach of every primitive here
-    float wlx = INFINITY, wly = INFINITY, wlz = INFINITY, whx = -INFINITY, why = -INFINITY, whz = -INFINITY;
-    float wal = 0.f, wbe = 0.f;
-    if (lane < QW) {
-        const float4 q0 = wq[lane][0];
-        float alpha, beta, live;
-        if (PRIM == 0) { const float4 q1 = wq[lane][1]; alpha = q1.y; beta = q1.z; live = q1.w; }
-        else { const float4 q2 = wq[lane][2]; alpha = q2.z; beta = q2.w; live = wq[lane][3].x; }
-        if (live != 0.f) {
-            wlx = whx = q0.x; wly = why = q0.y; wlz = whz = q0.z;
-            wal = alpha; wbe = beta;
+    // (the whole-quad sweep path tests its quads directly and needs none)
+    if constexpr (!(QT && (SH & kShQuad) != 0)) {
+        float wlx = INFINITY, wly = INFINITY, wlz = INFINITY, whx = -INFINITY, why = -INFINITY, whz = -INFINITY;
+        float wal = 0.f, wbe = 0.f;
+        if (lane < QW) {
+            const float4 q0 = wq[lane][0];
+            float alpha, beta, live;
+            if (PRIM == 0) { const float4 q1 = wq[lane][1]; alpha = q1.y; beta = q1.z; live = q1.w; }
+            else { const float4 q2 = wq[lane][2]; alpha = q2.z; beta = q2.w; live = wq[lane][3].x; }
+            if (live != 0.f) {
+                wlx = whx = q0.x; wly = why = q0.y; wlz = whz = q0.z;
+                wal = alpha; wbe = beta;
+            }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        wlx = fminf(wlx, __shfl_xor_sync(0xffffffffu, wlx, o));
-        wly = fminf(wly, __shfl_xor_sync(0xffffffffu, wly, o));
-        wlz = fminf(wlz, __shfl_xor_sync(0xffffffffu, wlz, o));
-        whx = fmaxf(whx, __shfl_xor_sync(0xffffffffu, whx, o));
-        why = fmaxf(why, __shfl_xor_sync(0xffffffffu, why, o));
-        whz = fmaxf(whz, __shfl_xor_sync(0xffffffffu, whz, o));
-        wal = fmaxf(wal, __shfl_xor_sync(0xffffffffu, wal, o));
-        wbe = fmaxf(wbe, __shfl_xor_sync(0xffffffffu, wbe, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            wlx = fminf(wlx, __shfl_xor_sync(0xffffffffu, wlx, o));
+            wly = fminf(wly, __shfl_xor_sync(0xffffffffu, wly, o));
+            wlz = fminf(wlz, __shfl_xor_sync(0xffffffffu, wlz, o));
+            whx = fmaxf(whx, __shfl_xor_sync(0xffffffffu, whx, o));
+            why = fmaxf(why, __shfl_xor_sync(0xffffffffu, why, o));
+            whz = fmaxf(whz, __shfl_xor_sync(0xffffffffu, whz, o));
+            wal = fmaxf(wal, __shfl_xor_sync(0xffffffffu, wal, o));
+            wbe = fmaxf(wbe, __shfl_xor_sync(0xffffffffu, wbe, o));
+        }
+        if (lane == 0) {
+            sm->wbox[warp][0] = make_float4(wlx, wly, wlz, wal);
+            sm->wbox[warp][1] = make_float4(whx, why, whz, wbe);
+        }
+        __syncwarp();
     }
-    if (lane == 0) {
-        sm->wbox[warp][0] = make_float4(wlx, wly, wlz, wal);
-        sm->wbox[warp][1] = make_float4(whx, why, whz, wbe);
-    }
-    __syncwarp();
-
     Acc<PRIM, QW, MODE, GRAD> A;
     A.fin = 0u;
 #pragma unroll
@@ -1557,18 +1559,25 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
     const unsigned long long c_loop_end = (unsigned long long)clock64();
 
     // ---- reductions across lanes (fixed trees) and outputs
+    // Each row's reductions run over the warp (fixed trees, the results on
+    // every lane); lane j keeps row j's results and, after the loop, the
+    // first QW lanes write their rows' outputs at once (output row, upstream
+    // gradient and the divisions computed per lane in parallel rather than
+    // one row after another).
+    const bool mine = lane < QW;
+    const int my_q = tile * TQ + C::row(warp, mine ? lane : 0);
+    const bool my_in = mine && my_q < a.Q;
+    const bool my_good = my_in && ((wvalid >> lane) & 1u) && ok;
+    float my_tot = 0.f, my_gx = 0.f, my_gy = 0.f, my_gz = 0.f, my_f = 0.f;
+    int my_cnt = 0, my_cin = 0;
     unsigned long long nb_total = 0;
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
-        const int q = tile * TQ + C::row(warp, j);
         const bool vq = (wvalid >> j) & 1u;
         if constexpr (MODE == 3) {
             // 1: in collision; 0: free; 2: not finished because its group collides
             const int cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
-            if (lane == 0 && q < a.Q && a.out_collide) {
-                const uint32_t row = row_out(a, q);
-                a.out_collide[row] = (vq && ok) ? (cinj > k.k_thr ? 1 : ((wgset >> j) & 1u) ? 2 : 0) : 0;
-            }
+            if (lane == j) my_cin = cinj > k.k_thr ? 1 : ((wgset >> j) & 1u) ? 2 : 0;
             continue;
         } else {
         const int cntj = __reduce_add_sync(0xffffffffu, (unsigned)A.cnt[j]);
@@ -1579,11 +1588,9 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
             } else {
                 cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
             }
-            float metric = 0.f;
+            float metric = 0.f;  // mode 0: the sum, scaled after the loop
             if (MODE == 0) {
-                const float tot = warp_sum(PRIM == 1 ? A.sum[j] + A.sumb[j] : A.sum[j]);
-                metric = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? tot * k.d_max / (float)cntj : 0.f)
-                                                         : tot * k.d_max;
+                metric = warp_sum(PRIM == 1 ? A.sum[j] + A.sumb[j] : A.sum[j]);
             } else if (MODE == 1) {
                 const float m = warp_min(A.mn[j]);
                 metric = cntj > 0 ? m : INFINITY;
@@ -1592,19 +1599,11 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 const float acc = warp_sum(A.sm_acc[j] * ex2_approx((M - A.sm_m[j]) * k.K));
                 metric = cntj > 0 ? M - k.tau * 0.6931471805599453f * lg2_approx(acc) : INFINITY;
             }
-            if (lane == 0 && q < a.Q) {
-                const uint32_t row = row_out(a, q);
-                const bool good = vq && ok;
-                if (a.out_metric) a.out_metric[row] = good ? metric : __int_as_float(0x7fc00000);
-                if (a.out_collide) a.out_collide[row] = (good && cinj > k.k_thr) ? 1 : 0;
-                if (a.out_count) a.out_count[row] = good ? cntj : 0;
-            }
+            if (lane == j) { my_tot = metric; my_cnt = cntj; my_cin = cinj; }
         } else {
             float gx, gy, gz, f = 0.f;
             if (MODE == 0) {
                 gx = warp_sum(A.gx[j]); gy = warp_sum(A.gy[j]); gz = warp_sum(A.gz[j]);
-                f = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? -k.gamma * k.d_max / (float)cntj : 0.f)
-                                                    : -k.gamma * k.d_max;
             } else if (MODE == 1) {
                 // the arg-min pair: the lane holding the smallest st2 (lowest lane on ties)
                 const float m = warp_min(A.mn[j]);
@@ -1621,36 +1620,52 @@ __device__ bool consumer_warp(const EvalArgs &a, EvalSmem<C> *sm, int tile, int 
                 gx = warp_sum(A.gx[j] * sc_); gy = warp_sum(A.gy[j] * sc_); gz = warp_sum(A.gz[j] * sc_);
                 f = cntj > 0 ? 1.f / acc : 0.f;
             }
+            if (lane == j) { my_gx = gx; my_gy = gy; my_gz = gz; my_f = f; my_cnt = cntj; }
             if constexpr ((SH & kShFwd) != 0 && MODE == 0 && PRIM == 0) {
                 // the forward outputs of the same launch (as in the forward epilogue)
                 const int cinj = (int)__reduce_add_sync(0xffffffffu, (unsigned)A.cin[j]);
                 const float tot = warp_sum(A.sum[j]);
-                const float metric = (k.mode == CS_METRIC_MEAN_COST) ? (cntj > 0 ? tot * k.d_max / (float)cntj : 0.f)
-                                                                     : tot * k.d_max;
-                if (lane == 0 && q < a.Q) {
-                    const uint32_t row = row_out(a, q);
-                    const bool good = vq && ok;
-                    if (a.out_metric) a.out_metric[row] = good ? metric : __int_as_float(0x7fc00000);
-                    if (a.out_collide) a.out_collide[row] = (good && cinj > k.k_thr) ? 1 : 0;
-                    if (a.out_count) a.out_count[row] = good ? cntj : 0;
-                }
-            }
-            if (lane == 0 && q < a.Q) {
-                const uint32_t row = row_out(a, q);
-                float up = 1.f;
-                if (a.grad_out) {
-                    const uint32_t gi = k.group_size > 0 ? row / (uint32_t)k.group_size : row;
-                    up = a.grad_out[CS_IDX_OK(gi < (uint32_t)a.Q, a.err) ? gi : 0u];
-                }
-                const bool good = vq && ok;
-                const float nanv = __int_as_float(0x7fc00000);
-                a.grad_centres[3 * (size_t)row + 0] = good ? gx * f * up : nanv;
-                a.grad_centres[3 * (size_t)row + 1] = good ? gy * f * up : nanv;
-                a.grad_centres[3 * (size_t)row + 2] = good ? gz * f * up : nanv;
+                if (lane == j) { my_tot = tot; my_cin = cinj; }
             }
         }
         if (vq) nb_total += (unsigned long long)cntj;
         }  // MODE != 3
+    }
+    if (my_in) {
+        const uint32_t row = row_out(a, my_q);
+        const float nanv = __int_as_float(0x7fc00000);
+        if constexpr (MODE == 3) {
+            if (a.out_collide) a.out_collide[row] = my_good ? (uint8_t)my_cin : (uint8_t)0;
+        } else if constexpr (!GRAD) {
+            float metric = my_tot;
+            if (MODE == 0)
+                metric = (k.mode == CS_METRIC_MEAN_COST) ? (my_cnt > 0 ? my_tot * k.d_max / (float)my_cnt : 0.f)
+                                                         : my_tot * k.d_max;
+            if (a.out_metric) a.out_metric[row] = my_good ? metric : nanv;
+            if (a.out_collide) a.out_collide[row] = (my_good && my_cin > k.k_thr) ? 1 : 0;
+            if (a.out_count) a.out_count[row] = my_good ? my_cnt : 0;
+        } else {
+            float f = my_f;
+            if (MODE == 0)
+                f = (k.mode == CS_METRIC_MEAN_COST) ? (my_cnt > 0 ? -k.gamma * k.d_max / (float)my_cnt : 0.f)
+                                                    : -k.gamma * k.d_max;
+            if constexpr ((SH & kShFwd) != 0 && MODE == 0 && PRIM == 0) {
+                const float metric = (k.mode == CS_METRIC_MEAN_COST)
+                                         ? (my_cnt > 0 ? my_tot * k.d_max / (float)my_cnt : 0.f)
+                                         : my_tot * k.d_max;
+                if (a.out_metric) a.out_metric[row] = my_good ? metric : nanv;
+                if (a.out_collide) a.out_collide[row] = (my_good && my_cin > k.k_thr) ? 1 : 0;
+                if (a.out_count) a.out_count[row] = my_good ? my_cnt : 0;
+            }
+            float up = 1.f;
+            if (a.grad_out) {
+                const uint32_t gi = k.group_size > 0 ? row / (uint32_t)k.group_size : row;
+                up = a.grad_out[CS_IDX_OK(gi < (uint32_t)a.Q, a.err) ? gi : 0u];
+            }
+            a.grad_centres[3 * (size_t)row + 0] = my_good ? my_gx * f * up : nanv;
+            a.grad_centres[3 * (size_t)row + 1] = my_good ? my_gy * f * up : nanv;
+            a.grad_centres[3 * (size_t)row + 2] = my_good ? my_gz * f * up : nanv;
+        }
     }
     if (a.stats && lane == 0) {
         atomicAdd(a.stats + 0, (unsigned long long)cand);
