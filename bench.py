@@ -43,11 +43,11 @@ KSTAT_NAMES = ["stages", "chunks_tested", "chunks_pass_warp", "hits", "chunks_st
 OPS_PER_PAIR = 26  # canonical FP32 ops of one sphere pair (see the design notes)
 # DRAM bytes (read + write) per forward launch of the fused kernel: the mean of
 # the step's two sweep launches from the ncu captures summarised under
-# profiles/ (arm 41.74 MB, edge 122.05 MB), valid for the library version they
+# profiles/ (arm 41.21 MB, edge 124.02 MB), valid for the library version they
 # were taken with (reported as null otherwise)
-TRAFFIC = {"version": "cs_b300 1.4 (sm_103a)", "bytes": (41.727232e6 + 0.01024e6 + 96.088832e6 + 25.961472e6) / 2,
-           "case": "mean of the step's two forward sweep launches, tile 30 (arm 262,144 x 4 rows: 41.7 MB; "
-                   "edge 2,097,152 x 4 rows: 122.1 MB)"}
+TRAFFIC = {"version": "cs_b300 1.5 (sm_103a)", "bytes": (41.13024e6 + 0.076544e6 + 97.350912e6 + 26.670592e6) / 2,
+           "case": "mean of the step's two forward sweep launches, tile 30 (arm 262,144 x 4 rows: 41.2 MB; "
+                   "edge 2,097,152 x 4 rows: 124.0 MB)"}
 WORKLOAD = ("tabletop-1M: 262,144 arm + 2,097,152 edge spheres x n_sigma{0,0.5,1,2} + 262,144 pose spheres "
             "fwd+adjoint (each batch's conservatism sweep as one launch; the pose forward and adjoint as one fused launch)")
 

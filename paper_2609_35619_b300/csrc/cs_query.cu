@@ -1995,6 +1995,10 @@ using CfgGrad1 = Cfg<4, 8, 3, 8, 3>;
 using CfgGrad2 = Cfg<4, 8, 3, 16, 3, 2, 2>;
 using CfgGrad3 = Cfg<4, 8, 2, 24, 3, 2, 2>;
 using CfgGrad4 = Cfg<8, 8, 2, 16, 2, 2, 2>;
+// the fused forward + adjoint launch of sphere cost queries (cs_query_fwd_grad):
+// 4 x 8, 2 x 24, 3 CTAs/SM, row pairs, persistent (SMs x 3 CTAs take tiles
+// from a counter)
+using CfgGradF = Cfg<4, 8, 2, 24, 3, 2, 2, true>;
 constexpr int kDefaultGradTile = 2;
 static const int kTileIds[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30};
 static_assert(sizeof(kTileIds) / sizeof(kTileIds[0]) <= 64, "callers hold up to 64 shape ids");
@@ -2120,8 +2124,8 @@ static cudaError_t launch_prim(const EvalArgs &a, bool grad, int tile, cudaStrea
     if (grad) {
         const int mode = a.k.mode == CS_METRIC_MIN_S2 ? 1 : a.k.mode == CS_METRIC_SOFTMIN_S2 ? 2 : 0;
         if constexpr (PRIM == 0) {
-            // forward outputs in the same launch: the default adjoint shape
-            if (mode == 0 && fused_forward(a)) return launch_eval_t<PRIM, CfgGrad2, 0, true, false, kShFwd>(a, s);
+            // forward outputs in the same launch: its own persistent shape
+            if (mode == 0 && fused_forward(a)) return launch_eval_t<PRIM, CfgGradF, 0, true, false, kShFwd>(a, s);
         }
         const int gt = (tile >= 1 && tile <= 4) ? tile : kDefaultGradTile;
         if (gt == 1) return launch_grad<PRIM, CfgGrad1>(a, mode, s);
