@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--tiles", default="",
                     help="ARM,EDGE tile ids for the step (default: chosen by the autotuner before timing)")
     ap.add_argument("--serve-requests", type=int, default=1500,
-                    help="requests of the serving measurement in the default run")
+                    help="requests per load (25, 50, 75 and 90 %% of the served capacity) of the serving "
+                         "measurement in the default run")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests-sweep", type=int, default=10_000, help="requests per load in --case serve")
     ap.add_argument("--serve-eager", action="store_true",
@@ -357,7 +358,7 @@ def run_ours(args, rank, world):
         "gpu_launches_total": int(launches), "served": None,
     }
     if not args.no_serve and world == 1:
-        result["served"] = run_served(torch, cs, dev, args.serve_requests)
+        result["served"] = run_served(torch, cs, dev, args.serve_requests, loads=(0.25, 0.5, 0.75, 0.9))
         result["mppi"] = run_mppi(torch, cs, dev)
         result["rrt"] = run_rrt(torch, cs, dev)
         result["refine"] = run_refine(torch, cs, dev)
