@@ -321,7 +321,7 @@ def run_ours(args, rank, world):
                 "avg_launch_ms": avg_eval_s * 1e3,
                 "candidate_frac": (fwd_cand * OPS_PER_PAIR / n_fwd_launches / avg_eval_s) / peak_ops}
 
-    # scene build (Eq. 2 repack, filter, Morton order, chunks, tree): minimal
+    # scene build (Eq. 2 repack, filter, Hilbert order, chunks, tree): minimal
     # traffic is the 44 input bytes read and the 40-byte record written per
     # Gaussian; the build synchronises the host a few times, so this is a
     # lower bound of the build's own bandwidth
@@ -620,7 +620,7 @@ def run_served(torch, cs, dev, n_requests, loads=(0.75,), with_per_call=True, sl
 
 def run_build_case(args, reps=10):
     """The scene build alone (cs_scene_create from device arrays: Eq. 2
-    repack, floater filter, Morton order, chunks, tree) on the 1M tabletop,
+    repack, floater filter, Hilbert order, chunks, tree) on the 1M tabletop,
     `reps` times after two warm-up builds; CUDA events on the build's stream
     (the call returns with the scene complete)."""
     import torch

@@ -103,7 +103,7 @@ typedef struct cs_scene_desc {
     float opacity_min;      /* default 0.05 */
     float extent_max;       /* default 0.1 (scene units) */
     float cell_size;        /* extent limit of a chunk (up to 32 Gaussians consecutive in
-                               Morton order); 0 = automatic: twice the edge of a box that
+                               Hilbert-curve order); 0 = automatic: twice the edge of a box that
                                holds 32 Gaussians at the mean density of the scene box */
     float tier_quantile;    /* Gaussians whose largest scale exceeds this quantile go to
                                the separately culled large tier; 0 = default 0.99 */
@@ -196,7 +196,7 @@ typedef struct cs_scene_info {
  * for p == NULL. */
 CS_API cs_status cs_params_init(cs_params *p);
 
-/* Build a resident scene (Eq. 2 repack, floater filter, Morton-ordered
+/* Build a resident scene (Eq. 2 repack, floater filter, Hilbert-ordered
  * chunks of the main and large tiers, the chunk tree) on the current device.
  * Synchronises `stream` a few times (the layout depends on the scene's extent
  * and on the chunk count).  On success *out owns device memory
@@ -211,7 +211,7 @@ CS_API cs_status cs_scene_destroy(cs_scene *scene);
 
 CS_API cs_status cs_scene_info_get(const cs_scene *scene, cs_scene_info *info);
 
-/* Copy the repacked, Morton-sorted scene to caller device buffers (any may be
+/* Copy the repacked, Hilbert-sorted scene to caller device buffers (any may be
  * NULL): pos [n_kept,4] = (mu, max scale); cov [n_kept,8] = (Sxx, Syy, Szz,
  * 2Sxy, 2Sxz, 2Syz, 0, 0); index [n_kept] = input row of each entry. */
 CS_API cs_status cs_scene_export(const cs_scene *scene, float *pos, float *cov, int32_t *index,
