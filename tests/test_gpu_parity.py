@@ -214,6 +214,49 @@ def test_invalid_query_rows_reported(cs):
     compare(sub, oracle.query(sc, q[keep], 0, 1.0), 0, oracle.Params(), "valid rows beside invalid")
 
 
+@pytest.mark.parametrize("tile,sweep", [(29, (0.0, 0.5, 1.0, 2.0)), (30, (0.0, 0.5, 1.0, 2.0)),
+                                        (28, (2.0, 1.0, 0.0, 0.5, 3.0, 0.1, 1.5, 0.7))])
+def test_sweep_whole_quads_with_invalid_rows(cs, tile, sweep):
+    """A conservatism sweep with a multiple of four n_sigma values on the quad
+    shapes runs the whole-quad evaluation: every row quad is four copies of one
+    prepared sphere, and the copies of an invalid sphere (NaN centre, negative
+    radius) form dead quads that are never evaluated.  Their rows come out as
+    NaN (metric) and 0 (flag, count), the error word reports them, and every
+    other row of every n_sigma block keeps the bits of its own call; a ragged
+    last tile (1,003 primitives)."""
+    sc = S.tiny_scene(n=3000)
+    scene = _scene(cs, sc)
+    rng = np.random.default_rng(93)
+    Q, G = 1003, 10
+    q = np.c_[rng.uniform(0, 2, (Q, 3)), rng.uniform(0.05, 0.25, Q)].astype(np.float32)
+    bad = np.array([0, 5, 64, 333, 1002])
+    q[bad[::2], 0] = np.nan
+    q[bad[1::2], 3] = -1.0
+    ng = (Q + G - 1) // G
+    one = scene.query(torch.as_tensor(q), 0.0, want_count=True,
+                      params=cs.QueryParams(group_size=G, sweep=sweep, tile_config=tile))
+    torch.cuda.synchronize()
+    with pytest.raises(cs.CsError) as ei:
+        scene.sync()
+    assert ei.value.status == cs.abi.CS_ERR_INVALID_ARG
+    scene.sync()  # cleared
+    for b, ns in enumerate(sweep):
+        blk = {k: one[k][b * Q:(b + 1) * Q].cpu().numpy() for k in ("metric", "collide", "count")}
+        assert np.isnan(blk["metric"][bad]).all() and (blk["collide"][bad] == 0).all() and (blk["count"][bad] == 0).all()
+        sep = scene.query(torch.as_tensor(q), ns, want_count=True, params=cs.QueryParams(group_size=G))
+        torch.cuda.synchronize()
+        with pytest.raises(cs.CsError):
+            scene.sync()
+        scene.sync()
+        for k in ("metric", "collide", "count"):
+            np.testing.assert_array_equal(blk[k].view(np.uint8), sep[k].cpu().numpy().view(np.uint8),
+                                          err_msg=f"{tile} {ns} {k}")
+        for k in ("group_metric", "group_collide"):
+            np.testing.assert_array_equal(one[k][b * ng:(b + 1) * ng].cpu().numpy().view(np.uint8),
+                                          sep[k].cpu().numpy().view(np.uint8), err_msg=f"{tile} {ns} {k}")
+        assert (blk["count"] > 0).any()
+
+
 def test_degenerate_gaussians_and_far_queries(cs):
     """2DGS-style disks (a zero scale), zero-size points, identity-less zero
     quaternions, queries far outside the scene box."""
